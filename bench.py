@@ -1,0 +1,428 @@
+"""Benchmark of the msRep SpMV hot path on one GB300.
+
+Workload (the SpMV workload the headline metric is quoted on): two FP64
+matrices, each in CSR, CSC and COO with int32 indices,
+  * R-MAT 2^20 x 2^20 with 2^24 nonzeros (a,b,c,d = .57/.19/.19/.05,
+    duplicates summed, values N(0,1)),
+  * the 5-point Laplacian of a 2048 x 2048 grid (4,194,304 rows,
+    20,963,328 nonzeros),
+cut into P nnz-balanced partitions (default P = 148 * 16).
+
+One step = msrep_spmv (partitioned SpMV plus the merge of split rows) for
+all six (matrix, format) pairs, inputs resident in HBM.  Partitioning
+(pCSR/pCSC/pCOO conversion, Alg. 2/4/6, with the tile plan) is done once per
+matrix, timed separately and reported as partition time.  Every matrix is
+larger than L2, so no L2 flush is done between steps.
+
+Printed: one JSON line (rank 0) with value = SpMV GFLOP/s (2*nnz per SpMV,
+alpha/beta scaling not counted), the HBM roofline of the dominant kernel,
+the end-to-end figure through the C ABI with host buffers, the oracle timed
+on the host cores, clocks sampled during the timed region, and the
+low-precision form (FP32 / BF16 values) on the R-MAT matrix.
+
+--impl reference times the CPU oracle (plain single-threaded FP64 SpMV of
+the same workload) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2209_07552_gb300 import inputs as I  # noqa: E402
+
+FORMATS = ("csr", "csc", "coo")
+METRIC = "SpMV GFLOP/s (FP64, R-MAT 2^20 / 2^24 nnz + 2D Laplacian 2048^2, CSR+CSC+COO)"
+
+
+def algorithmic_bytes(fmt: str, m: int, n: int, nnz: int, sv: int, sx: int) -> int:
+    """Compulsory bytes of one SpMV (beta = 0): every nonzero's value and
+    index(es), the pointer array, x and y each touched once."""
+    if fmt == "csr":
+        return (sv + 4) * nnz + 4 * (m + 1) + sx * n + sx * m
+    if fmt == "csc":
+        return (sv + 4) * nnz + 4 * (n + 1) + sx * n + sx * m
+    return (sv + 8) * nnz + sx * n + sx * m
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons (every 200 ms)."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_workload():
+    return {"rmat": I.rmat_full(), "laplace": I.laplace_full()}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# --------------------------------------------------------------------------
+
+def cpu_oracle_run(mats, budget_s: float):
+    """Time the oracle's FP64 SpMV over the workload's (matrix, format)
+    pairs, repeating until ~budget_s of CPU work; returns (GFLOP/s, sample)."""
+    import oracle as O
+    pre = []
+    for name, a in mats.items():
+        x = I.vector(a.n, I.SEED_BASE + 1)
+        c = I.csr_to_csc(a)
+        q = I.csr_to_coo(a)
+        pre.append((name, "csr", lambda a=a, x=x: O.spmv_csr(a.m, a.row_ptr, a.col_idx, a.val, x), a.nnz))
+        pre.append((name, "csc", lambda a=a, c=c, x=x: O.spmv_csc(a.m, a.n, c.col_ptr, c.row_idx, c.val, x), a.nnz))
+        pre.append((name, "coo", lambda a=a, q=q, x=x: O.spmv_coo(a.m, q.row_idx, q.col_idx, q.val, x), a.nnz))
+    flops = 0.0
+    spmvs = 0
+    t0 = time.perf_counter()
+    while True:
+        for name, fmt, fn, nnz in pre:
+            fn()
+            flops += 2.0 * nnz
+            spmvs += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return flops / dt / 1e9, f"{spmvs} single-threaded FP64 SpMVs over the 6 (matrix, format) pairs of the workload, {dt:.1f} s"
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    mats = load_workload()
+    budget = max(3.0, min(60.0, 2.0 * args.steps))
+    val, sample = cpu_oracle_run(mats, budget)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "rmat20_16Mnnz+laplace2048", "formats": list(FORMATS)},
+        "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": 1,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P = args.P
+
+    mats = load_workload()
+    pairs = []   # (name, fmt, A, part, x, y, ws, nnz, bytes)
+    part_ms = {}
+    for name, a in mats.items():
+        xh = I.vector(a.n, I.SEED_BASE + 1)
+        x = torch.from_numpy(xh).to(dev)
+        for fmt in FORMATS:
+            A = M.DeviceMatrix.from_host(a, fmt, "f64", device=dev)
+            part = M.DevicePartition(A, P, tile=args.tile, device=dev)
+            # partition time (the pCSR/pCSC/pCOO conversion incl. tile plan)
+            for _ in range(2):
+                M.msrep_partition(A, part)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 10
+            e0.record()
+            for _ in range(reps):
+                M.msrep_partition(A, part)
+            e1.record()
+            torch.cuda.synchronize()
+            part_ms[f"{name}/{fmt}"] = e0.elapsed_time(e1) / reps
+            y = torch.empty(a.m, dtype=torch.float64, device=dev)
+            ws = M.alloc_workspace(A, part, device=dev)
+            nb = algorithmic_bytes(fmt, a.m, a.n, a.nnz, 8, 8)
+            pairs.append((name, fmt, A, part, x, y, ws, a.nnz, nb))
+    del mats
+
+    def step():
+        for (_, _, A, part, x, y, ws, _, _) in pairs:
+            M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+
+    flops_step = sum(2.0 * p[7] for p in pairs)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+        # per-kernel timing of the main SpMV kernels (profiling events)
+        kern = {}
+        reps = max(5, args.steps)
+        for (name, fmt, A, part, x, y, ws, nnz, nb) in pairs:
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            M.native.msrep_profile_events(s0, s1)
+            tot = 0.0
+            for _ in range(reps):
+                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+                s1.synchronize()
+                tot += s0.elapsed_time(s1)
+            M.native.msrep_profile_events(None, None)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            kern[f"{name}/{fmt}"] = {"kernel_us": 1e3 * tot / reps,
+                                     "call_us": 1e3 * e0.elapsed_time(e1) / reps,
+                                     "bytes": nb, "nnz": nnz}
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = flops_step * world / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (largest kernel time in the step)
+    peak, peak_kind = measured_peaks()
+    dom_key = max(kern, key=lambda k: kern[k]["kernel_us"])
+    d = kern[dom_key]
+    achieved = d["bytes"] / (d["kernel_us"] * 1e-6) / 1e9
+    roof = {"bound": "hbm", "kernel": dom_key, "achieved": achieved, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None}
+    for k, v in kern.items():
+        v["gbs"] = v["bytes"] / (v["kernel_us"] * 1e-6) / 1e9
+        v["frac"] = v["gbs"] / peak
+
+    # end to end through the C ABI with host buffers: x up, SpMV, y down
+    e2e = run_e2e(M, pairs, args, dev)
+
+    # low-precision form on the R-MAT matrix (CSR)
+    prec = run_precision(M, args, dev) if not args.skip_precision else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded R-MAT and 2D Laplacian)",
+        "config": {"workload": "rmat20_16Mnnz+laplace2048", "formats": list(FORMATS),
+                   "P": P, "tile": args.tile or 2048, "alpha": 1.0, "beta": 0.0,
+                   "l2": "inputs larger than L2 (each matrix 222-403 MB); no flush",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "per_kernel": kern,
+        "partition_ms": part_ms,
+        "e2e": e2e,
+        # CSR and COO: main kernel + fix-up kernel; CSC (beta = 0): memset + main kernel
+        "gpu_launches": args.steps * sum(2 if p[1] != "csc" else 1 for p in pairs),
+        "clocks": clk.summary(),
+    }
+    if prec:
+        line["precision"] = prec
+    if rank == 0 and not args.no_cpu_baseline:
+        mats = load_workload()
+        v, sample = cpu_oracle_run(mats, args.cpu_budget)
+        line["cpu_baseline"] = {"value": v, "unit": "GFLOP/s", "cores": 1,
+                                "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_e2e(M, pairs, args, dev):
+    import torch
+    hx, hy = {}, {}
+    for (name, fmt, A, part, x, y, ws, nnz, nb) in pairs:
+        hx[(name, fmt)] = torch.empty(x.numel(), dtype=torch.float64).pin_memory()
+        hx[(name, fmt)].copy_(x.cpu())
+        hy[(name, fmt)] = torch.empty(y.numel(), dtype=torch.float64).pin_memory()
+    h2d = sum(x.numel() * 8 for (_, _, _, _, x, _, _, _, _) in pairs)
+    d2h = sum(y.numel() * 8 for (_, _, _, _, _, y, _, _, _) in pairs)
+
+    def step():
+        for (name, fmt, A, part, x, y, ws, _, _) in pairs:
+            x.copy_(hx[(name, fmt)], non_blocking=True)
+            M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+            hy[(name, fmt)].copy_(y, non_blocking=True)
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    steps = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    flops = sum(2.0 * p[7] for p in pairs)
+    return {"value": flops / dt / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3}
+
+
+def run_precision(M, args, dev):
+    """R-MAT CSR with values stored FP64 / FP32 / BF16: kernel GB/s, time,
+    speedup over FP64, and normwise error vs the FP64 inputs (computed by
+    the GPU path itself against the FP64 GPU result)."""
+    import torch
+    a = I.rmat_full()
+    xh = I.vector(a.n, I.SEED_BASE + 1)
+    out = {}
+    base = None
+    y64 = None
+    peak, _ = measured_peaks()
+    for dt in ("f64", "f32", "bf16"):
+        A = M.DeviceMatrix.from_host(a, "csr", dt, device=dev)
+        part = M.DevicePartition(A, args.P, tile=args.tile, device=dev)
+        M.msrep_partition(A, part)
+        xt = torch.float64 if dt == "f64" else torch.float32
+        x = torch.from_numpy(xh).to(dev, xt)
+        y = torch.empty(a.m, dtype=xt, device=dev)
+        ws = M.alloc_workspace(A, part, device=dev)
+        for _ in range(3):
+            M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        M.native.msrep_profile_events(s0, s1)
+        kt = 0.0
+        for _ in range(reps):
+            M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+            s1.synchronize()
+            kt += s0.elapsed_time(s1)
+        M.native.msrep_profile_events(None, None)
+        e0.record()
+        for _ in range(reps):
+            M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+        e1.record()
+        torch.cuda.synchronize()
+        call_us = 1e3 * e0.elapsed_time(e1) / reps
+        sv = {"f64": 8, "f32": 4, "bf16": 2}[dt]
+        nb = algorithmic_bytes("csr", a.m, a.n, a.nnz, sv, 8 if dt == "f64" else 4)
+        kus = 1e3 * kt / reps
+        rec = {"call_us": call_us, "kernel_us": kus, "gbs": nb / (kus * 1e-6) / 1e9,
+               "frac": nb / (kus * 1e-6) / 1e9 / peak,
+               "gflops": 2.0 * a.nnz / (call_us * 1e-6) / 1e9}
+        yv = y.double()
+        if dt == "f64":
+            base, y64 = call_us, yv
+        else:
+            rec["speedup_vs_f64"] = base / call_us
+            rec["normwise_err_vs_f64"] = float(torch.linalg.norm(yv - y64) / torch.linalg.norm(y64))
+        out[dt] = rec
+        del A, part, x, y, ws
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--P", type=int, default=148 * 16)
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-precision", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * msrep.h -- C ABI of the GB300 implementation of the msRep SpMV hot path
+ * (arXiv 2209.07552, "msRep: A Fast yet Light Sparse Matrix Framework for
+ * Multi-GPU Systems").
+ *
+ * The paper cuts the nonzeros of a CSR, CSC or COO matrix into np partitions
+ * of equal nonzero count (pCSR/pCSC/pCOO, Sec. 3.2), runs an SpMV kernel per
+ * partition and merges the partial sums of rows that a partition boundary
+ * splits (Alg. 3, 5, 7; Sec. 4.3).  Here the partitions map to thread blocks
+ * of one GPU instead of to GPUs.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers named "device" must be CUDA device (or managed) memory; the
+ *    library never copies them to the host.  Every buffer is BORROWED: the
+ *    caller owns it and keeps it alive until the work queued on `stream` has
+ *    finished.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls are asynchronous unless their comment says "syncs".
+ *  - Index and pointer arrays are int32 (nnz < 2^31); partition arithmetic
+ *    (i * nnz) is done in 64-bit integers.
+ *  - No entry point allocates device memory, except msrep_serve_* (the server
+ *    owns the memory of the matrices it holds, counted against its budget).
+ *  - On error a call returns a non-zero msrep_status, queues nothing further
+ *    and records a message readable by msrep_last_error() (per host thread).
+ *  - y = alpha*A*x + beta*y (Alg. 1).  beta == 0 means y is write-only (its
+ *    old contents may be NaN).
+ */
+#ifndef MSREP_H
+#define MSREP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MSREP_OK = 0,
+  MSREP_ERR_INVALID_ARG = 1, /* a NULL pointer, bad size or bad enum value */
+  MSREP_ERR_BAD_MATRIX = 2,  /* structural check failed (MSREP_VALIDATE)   */
+  MSREP_ERR_OOM = 3,         /* server-side allocation failed              */
+  MSREP_ERR_CUDA = 4,        /* a CUDA runtime call failed                 */
+  MSREP_ERR_TIMEOUT = 5,     /* a bounded wait expired                     */
+  MSREP_ERR_BUDGET = 6,      /* the server's memory budget is exhausted    */
+  MSREP_ERR_NOT_FOUND = 7,   /* unknown matrix or request id               */
+  MSREP_ERR_SHUTDOWN = 8,    /* the server is shutting down                */
+  MSREP_ERR_WORKSPACE = 9    /* workspace or plan buffer too small         */
+} msrep_status;
+
+typedef enum { MSREP_CSR = 0, MSREP_CSC = 1, MSREP_COO = 2 } msrep_format;
+
+/* Value / vector storage types.  MSREP_BF16 is bfloat16 (8-bit exponent,
+ * 7-bit mantissa) stored as uint16. */
+typedef enum { MSREP_F64 = 0, MSREP_F32 = 1, MSREP_BF16 = 2 } msrep_dtype;
+
+/* A sparse matrix in one of the three formats of Sec. 2.1.  All arrays are
+ * device memory, borrowed.
+ *   CSR (Sec. 2.1.2): ptr = row_ptr[m+1], idx = col_idx[nnz], idx2 = NULL.
+ *   CSC (Sec. 2.1.3): ptr = col_ptr[n+1], idx = row_idx[nnz], idx2 = NULL;
+ *                     row indices ascend within each column.
+ *   COO (Sec. 2.1.1): ptr = NULL, idx = col_idx[nnz], idx2 = row_idx[nnz],
+ *                     sorted by (row, col) as Sec. 3.2.3 assumes.
+ * val has nnz entries of type val_dtype. */
+typedef struct {
+  int32_t fmt;       /* msrep_format */
+  int32_t val_dtype; /* msrep_dtype */
+  int32_t m, n;      /* rows, columns */
+  int64_t nnz;
+  const int32_t *ptr;
+  const int32_t *idx;
+  const int32_t *idx2;
+  const void *val;
+} msrep_matrix;
+
+/* pCSR / pCSC / pCOO metadata (Sec. 3.2) plus the library's tile plan.
+ * Every array is caller-allocated device memory of the stated length.
+ *   start_idx, end_idx  [np]  nonzero range of partition i, end inclusive:
+ *                             floor(i*nnz/np) .. floor((i+1)*nnz/np)-1.
+ *   start_major,        [np]  first / last row (CSR, COO) or column (CSC)
+ *   end_major                 that owns a nonzero of the partition.
+ *   start_flag          [np]  1 if the partition's first row (column) also
+ *                             has nonzeros in an earlier partition.
+ *   local_off  (opt.) [np+1]  offsets of each partition's local pointers.
+ *   local      (opt.)         CSR/CSC: local row_ptr/col_ptr of partition i
+ *                             at local_off[i], end_major-start_major+2
+ *                             entries (0, ptr[start+1]-start_idx, ...,
+ *                             end_idx-start_idx+1); capacity
+ *                             msrep_partition_local_bound().  COO: local row
+ *                             index array, nnz entries, row_idx[k] -
+ *                             start_major of k's partition.
+ *   plan       (opt.)         opaque tile plan used by msrep_spmv for CSR
+ *                             and CSC; plan_bytes >= msrep_plan_size().
+ *   tile                      nonzeros+rows per thread-block tile of the
+ *                             plan, 0 = library default; must be a
+ *                             supported size (msrep_tile_supported()).
+ * An empty partition (np > nnz) has start_major = 0, end_major = -1,
+ * start_flag = 0 and a one-entry local pointer {0}. */
+typedef struct {
+  int32_t np;
+  int32_t tile;
+  int32_t *start_idx;
+  int32_t *end_idx;
+  int32_t *start_major;
+  int32_t *end_major;
+  uint8_t *start_flag;
+  int64_t *local_off;
+  int32_t *local;
+  void *plan;
+  int64_t plan_bytes;
+} msrep_partition;
+
+/* flags for msrep_partition_* */
+#define MSREP_VALIDATE 0x1u /* check structure on the device first; syncs */
+
+/* Library version string. */
+const char *msrep_version(void);
+
+/* Message of the last failed call on this host thread ("" if none). */
+const char *msrep_last_error(void);
+
+/* Host only, no GPU work.  Capacity that `local` needs for a CSR/CSC
+ * partition with np parts: n_major + 2*np entries (Alg. 2 loop bound plus
+ * the two closing entries per partition); nnz entries for COO. */
+msrep_status msrep_partition_local_bound(const msrep_matrix *A, int32_t np,
+                                         int64_t *entries);
+
+/* Host only.  1 if `tile` is a tile size msrep_spmv supports, else 0. */
+int msrep_tile_supported(int32_t tile);
+
+/* Host only.  Bytes of the tile plan for (A, np, tile); tile 0 = default. */
+msrep_status msrep_plan_size(const msrep_matrix *A, int32_t np, int32_t tile,
+                             int64_t *bytes);
+
+/* CSR -> pCSR, Alg. 2 (Sec. 3.2.1).  Fills the metadata arrays, and the
+ * local row pointers / tile plan when those pointers are non-NULL.  All
+ * results are integers and exactly reproducible.  The binary search of
+ * Alg. 2 owns nonzero k by row(k) = max{r < m : row_ptr[r] <= k}.
+ * Errors: INVALID_ARG (np < 1, NULL array, wrong format), WORKSPACE (plan
+ * too small), BAD_MATRIX (with MSREP_VALIDATE: row_ptr not monotone,
+ * row_ptr[0] != 0, row_ptr[m] != nnz, column out of range). */
+msrep_status msrep_partition_csr(const msrep_matrix *A, msrep_partition *part,
+                                 unsigned flags, void *stream);
+
+/* CSC -> pCSC, Alg. 4 (Sec. 3.2.2): Alg. 2 over col_ptr. */
+msrep_status msrep_partition_csc(const msrep_matrix *A, msrep_partition *part,
+                                 unsigned flags, void *stream);
+
+/* Row-sorted COO -> pCOO, Alg. 6 (Sec. 3.2.3).  Alg. 6 searches a row_ptr
+ * that COO does not carry; here start_major = row_idx[start_idx], end_major
+ * = row_idx[end_idx], start_flag = row_idx[start_idx-1] == row_idx[start_idx].
+ * The result equals msrep_partition_csr on the CSR of the same matrix.
+ * Validation also checks the (row, col) order. */
+msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *part,
+                                 unsigned flags, void *stream);
+
+/* Host only.  Device workspace bytes msrep_spmv needs for (A, part). */
+msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
+                                       const msrep_partition *part,
+                                       size_t *bytes);
+
+/* flags for msrep_spmv */
+#define MSREP_COMP_ALL 0x10u  /* low precision: compensate every row      */
+#define MSREP_COMP_NONE 0x20u /* low precision: plain FP32 accumulation   */
+
+/* y = alpha*A*x + beta*y over the partitions of `part` (Alg. 3 for CSR,
+ * Alg. 5 for CSC, Alg. 7 for COO).  `part` must come from the matching
+ * msrep_partition_* call on the same matrix; CSR and CSC also need its plan.
+ *
+ * Types: val_dtype F64 with xy_dtype F64 (the plain path), or val_dtype F32
+ * or BF16 with xy_dtype F32 (the low-precision form: FP32 products, FP32
+ * accumulation with TwoSum compensation on rows longer than 256 nonzeros
+ * and on rows split between thread-block tiles, partial sums of split rows
+ * merged in FP64).  x has n entries, y has m entries, device memory.
+ *
+ * Merge: every row split by a partition (or tile) boundary gets
+ * alpha * (sum of its partials, in partition order) + beta * y_in, beta
+ * applied once (Sec. 3.2.1, Sec. 4.3).  CSR and COO merge without atomics;
+ * CSC scatters into y with atomic adds (the column merge of Alg. 5), so its
+ * rounding order varies from run to run.
+ * `workspace` must hold msrep_spmv_workspace_size() bytes, 256-byte
+ * aligned.  Errors: INVALID_ARG, WORKSPACE, CUDA. */
+msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
+                        double alpha, const void *x, double beta, void *y,
+                        int32_t xy_dtype, unsigned flags, void *workspace,
+                        void *stream);
+
+/* Profiling aid (no counterpart in the paper).  While set, every msrep_spmv
+ * call made on this host thread records `start` (a cudaEvent_t passed as
+ * void*) on its stream just before its main SpMV kernel and `stop` just
+ * after it, so the caller can time that kernel alone with
+ * cudaEventElapsedTime.  Pass NULL, NULL to stop recording. */
+msrep_status msrep_profile_events(void *start, void *stop);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSREP_H */

@@ -1,0 +1,499 @@
+// Device partitioner: CSR -> pCSR (Alg. 2), CSC -> pCSC (Alg. 4),
+// row-sorted COO -> pCOO (Alg. 6), the optional local pointers computed on
+// the GPU (Sec. 4.1), and the merge-path tile plan that msrep_spmv runs on.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <mutex>
+#include <string>
+
+#include "common.cuh"
+
+namespace msrep {
+
+// ---------------------------------------------------------------------------
+// status plumbing (declared in common.cuh)
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_last_error;
+
+msrep_status fail(msrep_status st, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+msrep_status ok() {
+  g_last_error.clear();
+  return MSREP_OK;
+}
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+            cudaSuccess ||
+        n <= 0)
+      n = 148;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+// ---------------------------------------------------------------------------
+// searches over a compressed pointer array
+// ---------------------------------------------------------------------------
+
+// Largest r in [lo, hi] with ptr[r] <= k.  Requires ptr[lo] <= k.
+__device__ __forceinline__ int32_t last_le(const int32_t *__restrict__ ptr,
+                                           int32_t lo, int32_t hi, int64_t k) {
+  while (lo < hi) {
+    int32_t mid = lo + (hi - lo + 1) / 2;
+    if (static_cast<int64_t>(__ldg(ptr + mid)) <= k)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// Merge-path coordinate of diagonal d: largest r in [lo, hi] with
+// ptr[r] + r <= d (rows 0..r-1 have ended; ties consume the row end first).
+__device__ __forceinline__ int32_t path_row(const int32_t *__restrict__ ptr,
+                                            int32_t lo, int32_t hi, int64_t d) {
+  while (lo < hi) {
+    int32_t mid = lo + (hi - lo + 1) / 2;
+    if (static_cast<int64_t>(__ldg(ptr + mid)) + mid <= d)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Alg. 2 / Alg. 4: metadata, one thread per partition
+// ---------------------------------------------------------------------------
+
+__global__ void part_meta_compressed(const int32_t *__restrict__ ptr,
+                                     int32_t n_major, int64_t nnz, int32_t np,
+                                     int32_t *start_idx, int32_t *end_idx,
+                                     int32_t *start_major, int32_t *end_major,
+                                     uint8_t *start_flag, int64_t *plan_D,
+                                     int32_t *plan_R) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i > np) return;
+  int64_t s = (i * nnz) / np;
+  if (plan_D) {
+    // level-1 cut of the tile plan: (R(s_i), s_i) with R over [0, n_major]
+    int32_t R;
+    if (i == 0)
+      R = 0;
+    else if (i == np)
+      R = n_major;
+    else
+      R = last_le(ptr, 0, n_major, s);
+    plan_R[i] = R;
+    plan_D[i] = (i == 0) ? 0 : s + R;
+  }
+  if (i == np) return;
+  int64_t e = ((i + 1) * nnz) / np - 1;
+  start_idx[i] = static_cast<int32_t>(s);
+  end_idx[i] = static_cast<int32_t>(e);
+  if (e < s) {
+    start_major[i] = 0;
+    end_major[i] = -1;
+    start_flag[i] = 0;
+    return;
+  }
+  int32_t sr = last_le(ptr, 0, n_major - 1, s);
+  int32_t er = last_le(ptr, sr, n_major - 1, e);
+  start_major[i] = sr;
+  end_major[i] = er;
+  start_flag[i] = (s > static_cast<int64_t>(__ldg(ptr + sr))) ? 1 : 0;
+}
+
+// Alg. 6 (reading for sorted COO): metadata from row_idx directly.
+__global__ void part_meta_coo(const int32_t *__restrict__ row_idx, int64_t nnz,
+                              int32_t np, int32_t *start_idx, int32_t *end_idx,
+                              int32_t *start_major, int32_t *end_major,
+                              uint8_t *start_flag) {
+  int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= np) return;
+  int64_t s = (i * nnz) / np;
+  int64_t e = ((i + 1) * nnz) / np - 1;
+  start_idx[i] = static_cast<int32_t>(s);
+  end_idx[i] = static_cast<int32_t>(e);
+  if (e < s) {
+    start_major[i] = 0;
+    end_major[i] = -1;
+    start_flag[i] = 0;
+    return;
+  }
+  int32_t rs = __ldg(row_idx + s);
+  start_major[i] = rs;
+  end_major[i] = __ldg(row_idx + e);
+  start_flag[i] = (s > 0 && __ldg(row_idx + s - 1) == rs) ? 1 : 0;
+}
+
+// ---------------------------------------------------------------------------
+// single-block exclusive scan (np is at most a few hundred thousand)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__device__ T block_exclusive_scan(T v, T &total) {
+  __shared__ T warp_sums[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_sums[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    T w = lane < nw ? warp_sums[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    warp_sums[lane] = w;  // inclusive over warps
+  }
+  __syncthreads();
+  T base = wid > 0 ? warp_sums[wid - 1] : T(0);
+  total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return base + inc - v;
+}
+
+// local_off[i] = sum_{j<i} (end_major[j] - start_major[j] + 2) (CSR/CSC).
+__global__ void __launch_bounds__(1024)
+    local_off_scan(const int32_t *start_major, const int32_t *end_major,
+                   int32_t np, int64_t *local_off) {
+  int64_t carry = 0;
+  for (int32_t base = 0; base < np; base += blockDim.x) {
+    int32_t i = base + threadIdx.x;
+    int64_t len = (i < np) ? int64_t(end_major[i]) - start_major[i] + 2 : 0;
+    int64_t total;
+    int64_t ex = block_exclusive_scan<int64_t>(len, total);
+    if (i < np) local_off[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) local_off[np] = carry;
+}
+
+// Local row_ptr / col_ptr (Alg. 2/4 inner loop, computed on the GPU as in
+// Sec. 4.1): one block per partition.
+__global__ void local_fill_compressed(const int32_t *__restrict__ ptr,
+                                      const int32_t *start_idx,
+                                      const int32_t *end_idx,
+                                      const int32_t *start_major,
+                                      const int32_t *end_major,
+                                      const int64_t *local_off,
+                                      int32_t *local) {
+  const int32_t i = blockIdx.x;
+  const int32_t sm = start_major[i], em = end_major[i];
+  const int32_t s = start_idx[i], e = end_idx[i];
+  int32_t *out = local + local_off[i];
+  const int32_t span = em - sm;  // -1 for an empty partition
+  for (int32_t j = threadIdx.x; j <= span + 1; j += blockDim.x) {
+    int32_t v;
+    if (j == 0)
+      v = 0;
+    else if (j == span + 1)
+      v = e - s + 1;
+    else
+      v = __ldg(ptr + sm + j) - s;
+    out[j] = v;
+  }
+}
+
+// pCOO local row-index array: lrow[k] = row_idx[k] - start_row(partition).
+__global__ void local_fill_coo(const int32_t *__restrict__ row_idx,
+                               const int32_t *start_idx, const int32_t *end_idx,
+                               const int32_t *start_major, int32_t *local) {
+  const int32_t i = blockIdx.x;
+  const int32_t s = start_idx[i], e = end_idx[i], r0 = start_major[i];
+  for (int64_t k = s + threadIdx.x; k <= e; k += blockDim.x)
+    local[k] = __ldcs(row_idx + k) - r0;
+}
+
+// ---------------------------------------------------------------------------
+// tile plan (CSR/CSC): each partition's stretch of the merge path
+// [D_i, D_{i+1}) is split into ceil(len / tile) equal pieces
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024)
+    plan_scan(const int64_t *D, int32_t np, int32_t tile, int32_t *tile_off) {
+  int64_t carry = 0;
+  for (int32_t base = 0; base < np; base += blockDim.x) {
+    int32_t i = base + threadIdx.x;
+    int64_t g = 0;
+    if (i < np) g = (D[i + 1] - D[i] + tile - 1) / tile;
+    int64_t total;
+    int64_t ex = block_exclusive_scan<int64_t>(g, total);
+    if (i < np) tile_off[i] = static_cast<int32_t>(carry + ex);
+    carry += total;
+  }
+  if (threadIdx.x == 0) tile_off[np] = static_cast<int32_t>(carry);
+}
+
+__global__ void plan_tiles(const int32_t *__restrict__ ptr, int32_t n_major,
+                           int64_t nnz, int32_t np, const int64_t *D,
+                           const int32_t *R, const int32_t *tile_off,
+                           int32_t *tile_row, int32_t *tile_k) {
+  const int32_t i = blockIdx.x;
+  const int32_t t0 = tile_off[i], G = tile_off[i + 1] - t0;
+  const int64_t d0 = D[i], len = D[i + 1] - d0;
+  const int32_t lo = R[i], hi = R[i + 1];
+  for (int32_t g = threadIdx.x; g < G; g += blockDim.x) {
+    int64_t d = d0 + (static_cast<int64_t>(g) * len) / G;
+    int32_t r = path_row(ptr, lo, hi, d);
+    tile_row[t0 + g] = r;
+    tile_k[t0 + g] = static_cast<int32_t>(d - r);
+  }
+  if (i == np - 1 && threadIdx.x == 0) {
+    const int32_t T = tile_off[np];
+    tile_row[T] = n_major;
+    tile_k[T] = static_cast<int32_t>(nnz);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// structural validation (MSREP_VALIDATE)
+// ---------------------------------------------------------------------------
+
+__device__ unsigned int g_validate_err;
+
+__global__ void validate_compressed(const int32_t *__restrict__ ptr,
+                                    int32_t n_major, int64_t nnz,
+                                    const int32_t *__restrict__ idx,
+                                    int32_t n_minor) {
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  if (t == 0 && (ptr[0] != 0 || ptr[n_major] != nnz)) atomicOr(&g_validate_err, 1u);
+  for (int64_t r = t; r < n_major; r += stride)
+    if (ptr[r] > ptr[r + 1]) atomicOr(&g_validate_err, 2u);
+  for (int64_t k = t; k < nnz; k += stride) {
+    int32_t c = idx[k];
+    if (c < 0 || c >= n_minor) atomicOr(&g_validate_err, 4u);
+  }
+}
+
+__global__ void validate_coo(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
+                             int64_t nnz, int32_t m, int32_t n) {
+  int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  int64_t stride = int64_t(gridDim.x) * blockDim.x;
+  for (int64_t k = t; k < nnz; k += stride) {
+    int32_t r = row[k], c = col[k];
+    if (r < 0 || r >= m || c < 0 || c >= n) atomicOr(&g_validate_err, 4u);
+    if (k + 1 < nnz) {
+      int32_t r2 = row[k + 1], c2 = col[k + 1];
+      if (r2 < r || (r2 == r && c2 <= c)) atomicOr(&g_validate_err, 8u);
+    }
+  }
+}
+
+static std::mutex g_validate_mu;
+
+static msrep_status run_validation(const msrep_matrix *A, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_validate_mu);
+  unsigned int zero = 0, err = 0;
+  MSREP_CUDA_TRY(cudaMemcpyToSymbolAsync(g_validate_err, &zero, sizeof zero, 0,
+                                         cudaMemcpyHostToDevice, st));
+  const int blocks = 4 * sm_count();
+  if (A->fmt == MSREP_COO) {
+    validate_coo<<<blocks, 256, 0, st>>>(A->idx2, A->idx, A->nnz, A->m, A->n);
+  } else {
+    const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
+    const int32_t n_minor = A->fmt == MSREP_CSR ? A->n : A->m;
+    validate_compressed<<<blocks, 256, 0, st>>>(A->ptr, n_major, A->nnz, A->idx,
+                                                n_minor);
+  }
+  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_CUDA_TRY(cudaMemcpyFromSymbolAsync(&err, g_validate_err, sizeof err, 0,
+                                           cudaMemcpyDeviceToHost, st));
+  MSREP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (err)
+    return fail(MSREP_ERR_BAD_MATRIX,
+                "matrix failed validation (code 0x%x: 1=ptr ends, 2=ptr not "
+                "monotone, 4=index out of range, 8=COO not sorted by (row, col))",
+                err);
+  return MSREP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// argument checks shared by the entry points
+// ---------------------------------------------------------------------------
+
+msrep_status check_matrix(const msrep_matrix *A) {
+  if (!A) return fail(MSREP_ERR_INVALID_ARG, "matrix is NULL");
+  if (A->m < 0 || A->n < 0 || A->nnz < 0 || A->nnz > INT32_MAX)
+    return fail(MSREP_ERR_INVALID_ARG, "bad sizes m=%d n=%d nnz=%lld", A->m,
+                A->n, (long long)A->nnz);
+  if (A->val_dtype < MSREP_F64 || A->val_dtype > MSREP_BF16)
+    return fail(MSREP_ERR_INVALID_ARG, "bad val_dtype %d", A->val_dtype);
+  switch (A->fmt) {
+    case MSREP_CSR:
+    case MSREP_CSC:
+      if (!A->ptr) return fail(MSREP_ERR_INVALID_ARG, "ptr is NULL");
+      break;
+    case MSREP_COO:
+      if (!A->idx2 && A->nnz > 0)
+        return fail(MSREP_ERR_INVALID_ARG, "COO row_idx (idx2) is NULL");
+      break;
+    default:
+      return fail(MSREP_ERR_INVALID_ARG, "bad format %d", A->fmt);
+  }
+  if (A->nnz > 0 && (!A->idx || !A->val))
+    return fail(MSREP_ERR_INVALID_ARG, "idx or val is NULL");
+  return MSREP_OK;
+}
+
+int32_t effective_tile(int32_t tile) { return tile == 0 ? kDefaultTile : tile; }
+
+static msrep_status check_partition(const msrep_partition *p) {
+  if (!p) return fail(MSREP_ERR_INVALID_ARG, "partition is NULL");
+  if (p->np < 1) return fail(MSREP_ERR_INVALID_ARG, "np must be >= 1 (got %d)", p->np);
+  if (!p->start_idx || !p->end_idx || !p->start_major || !p->end_major ||
+      !p->start_flag)
+    return fail(MSREP_ERR_INVALID_ARG, "a partition metadata array is NULL");
+  if (!tile_supported(effective_tile(p->tile)))
+    return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", p->tile);
+  return MSREP_OK;
+}
+
+static msrep_status partition_compressed(const msrep_matrix *A,
+                                         msrep_partition *p, unsigned flags,
+                                         void *stream, int expect_fmt) {
+  MSREP_TRY(check_matrix(A));
+  if (A->fmt != expect_fmt)
+    return fail(MSREP_ERR_INVALID_ARG, "matrix format %d does not match call",
+                A->fmt);
+  MSREP_TRY(check_partition(p));
+  if (p->local && !p->local_off)
+    return fail(MSREP_ERR_INVALID_ARG, "local pointers need local_off");
+  cudaStream_t st = as_stream(stream);
+  if (flags & MSREP_VALIDATE) MSREP_TRY(run_validation(A, st));
+  const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
+  const int32_t tile = effective_tile(p->tile);
+  PlanLayout L = plan_layout(n_major, A->nnz, p->np, tile);
+  if (p->plan && p->plan_bytes < static_cast<int64_t>(L.bytes))
+    return fail(MSREP_ERR_WORKSPACE, "plan buffer has %lld bytes, needs %zu",
+                (long long)p->plan_bytes, L.bytes);
+  if (p->plan && (reinterpret_cast<uintptr_t>(p->plan) & 255))
+    return fail(MSREP_ERR_INVALID_ARG, "plan must be 256-byte aligned");
+  char *plan = static_cast<char *>(p->plan);
+  int64_t *D = plan ? reinterpret_cast<int64_t *>(plan + L.off_D) : nullptr;
+  int32_t *R = plan ? reinterpret_cast<int32_t *>(plan + L.off_R) : nullptr;
+  const int threads = 256;
+  const int blocks = static_cast<int>(ceil_div(p->np + 1, threads));
+  part_meta_compressed<<<blocks, threads, 0, st>>>(
+      A->ptr, n_major, A->nnz, p->np, p->start_idx, p->end_idx,
+      p->start_major, p->end_major, p->start_flag, D, R);
+  MSREP_CUDA_TRY(cudaGetLastError());
+  if (p->local_off) {
+    local_off_scan<<<1, 1024, 0, st>>>(p->start_major, p->end_major, p->np,
+                                       p->local_off);
+    MSREP_CUDA_TRY(cudaGetLastError());
+    if (p->local) {
+      local_fill_compressed<<<p->np, 128, 0, st>>>(
+          A->ptr, p->start_idx, p->end_idx, p->start_major, p->end_major,
+          p->local_off, p->local);
+      MSREP_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  if (plan) {
+    int32_t *toff = reinterpret_cast<int32_t *>(plan + L.off_toff);
+    int32_t *trow = reinterpret_cast<int32_t *>(plan + L.off_row);
+    int32_t *tk = reinterpret_cast<int32_t *>(plan + L.off_k);
+    plan_scan<<<1, 1024, 0, st>>>(D, p->np, tile, toff);
+    MSREP_CUDA_TRY(cudaGetLastError());
+    plan_tiles<<<p->np, 128, 0, st>>>(A->ptr, n_major, A->nnz, p->np, D, R,
+                                      toff, trow, tk);
+    MSREP_CUDA_TRY(cudaGetLastError());
+  }
+  return ok();
+}
+
+}  // namespace msrep
+
+using namespace msrep;
+
+extern "C" {
+
+const char *msrep_version(void) { return "msrep-gb300 0.1 (sm_103a)"; }
+
+const char *msrep_last_error(void) { return g_last_error.c_str(); }
+
+int msrep_tile_supported(int32_t tile) { return tile_supported(tile) ? 1 : 0; }
+
+msrep_status msrep_partition_local_bound(const msrep_matrix *A, int32_t np,
+                                         int64_t *entries) {
+  MSREP_TRY(check_matrix(A));
+  if (np < 1 || !entries) return fail(MSREP_ERR_INVALID_ARG, "bad np or entries");
+  if (A->fmt == MSREP_COO)
+    *entries = A->nnz;
+  else
+    *entries = int64_t(A->fmt == MSREP_CSR ? A->m : A->n) + 2 * int64_t(np);
+  return ok();
+}
+
+msrep_status msrep_plan_size(const msrep_matrix *A, int32_t np, int32_t tile,
+                             int64_t *bytes) {
+  MSREP_TRY(check_matrix(A));
+  if (np < 1 || !bytes) return fail(MSREP_ERR_INVALID_ARG, "bad np or bytes");
+  const int32_t t = effective_tile(tile);
+  if (!tile_supported(t)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", tile);
+  if (A->fmt == MSREP_COO) {
+    *bytes = 0;
+    return ok();
+  }
+  const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
+  *bytes = static_cast<int64_t>(plan_layout(n_major, A->nnz, np, t).bytes);
+  return ok();
+}
+
+msrep_status msrep_partition_csr(const msrep_matrix *A, msrep_partition *part,
+                                 unsigned flags, void *stream) {
+  return partition_compressed(A, part, flags, stream, MSREP_CSR);
+}
+
+msrep_status msrep_partition_csc(const msrep_matrix *A, msrep_partition *part,
+                                 unsigned flags, void *stream) {
+  return partition_compressed(A, part, flags, stream, MSREP_CSC);
+}
+
+msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
+                                 unsigned flags, void *stream) {
+  MSREP_TRY(check_matrix(A));
+  if (A->fmt != MSREP_COO)
+    return fail(MSREP_ERR_INVALID_ARG, "matrix format %d is not COO", A->fmt);
+  MSREP_TRY(check_partition(p));
+  cudaStream_t st = as_stream(stream);
+  if (flags & MSREP_VALIDATE) MSREP_TRY(run_validation(A, st));
+  const int threads = 256;
+  part_meta_coo<<<static_cast<int>(ceil_div(p->np, threads)), threads, 0, st>>>(
+      A->idx2, A->nnz, p->np, p->start_idx, p->end_idx, p->start_major,
+      p->end_major, p->start_flag);
+  MSREP_CUDA_TRY(cudaGetLastError());
+  if (p->local) {
+    local_fill_coo<<<p->np, 256, 0, st>>>(A->idx2, p->start_idx, p->end_idx,
+                                          p->start_major, p->local);
+    MSREP_CUDA_TRY(cudaGetLastError());
+  }
+  return ok();
+}
+
+}  // extern "C"

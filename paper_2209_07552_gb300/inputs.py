@@ -19,6 +19,7 @@ degree structure (Sec. 5.2 selects matrices with power-law exponent R in
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -351,3 +352,43 @@ def poisson_arrivals(rate_hz: float, duration_s: float, seed: int):
     n = int(rate_hz * duration_s * 1.2) + 16
     t = np.cumsum(g.exponential(1.0 / rate_hz, n))
     return t[t < duration_s]
+
+
+# --------------------------------------------------------------------------
+# on-disk cache of the large generated matrices (regenerated when absent)
+# --------------------------------------------------------------------------
+
+def _cache_dir() -> str:
+    d = os.environ.get("MSREP_INPUT_CACHE")
+    if not d:
+        d = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                         ".input_cache")
+    return d
+
+
+def cached_csr(key: str, make) -> CSR:
+    """make() once, then reload from an .npz under the cache directory."""
+    path = os.path.join(_cache_dir(), key + ".npz")
+    if os.path.exists(path):
+        z = np.load(path, allow_pickle=False)
+        return CSR(int(z["m"]), int(z["n"]), z["row_ptr"], z["col_idx"], z["val"],
+                   meta={"cached": key})
+    a = make()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}.npz"
+        np.savez(tmp, m=a.m, n=a.n, row_ptr=a.row_ptr, col_idx=a.col_idx, val=a.val)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+    return a
+
+
+def rmat_full(seed: int = SEED_BASE + 1) -> CSR:
+    """The 2^20 x 2^20, 2^24-nonzero R-MAT matrix (a,b,c,d = .57/.19/.19/.05)."""
+    return cached_csr(f"rmat20_{seed}", lambda: rmat(seed=seed))
+
+
+def laplace_full() -> CSR:
+    """The 2048 x 2048 grid 5-point Laplacian (4,194,304 rows)."""
+    return cached_csr("laplace2048", lambda: laplace5(2048))

@@ -1,0 +1,304 @@
+"""Python binding of libmsrep.so (the C ABI declared in include/msrep.h).
+
+Argument marshalling only: every step of the SpMV path runs in the CUDA
+kernels of libmsrep.so.  PyTorch supplies device memory and streams.  The
+functions keep the C names (msrep_partition_csr, msrep_spmv, ...); the small
+classes DeviceMatrix / DevicePartition own the torch tensors that back the
+C structs.  If libmsrep.so has not been built, every call raises: there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmsrep.so")
+_LOCK = threading.Lock()
+_LIB = None
+
+MSREP_CSR, MSREP_CSC, MSREP_COO = 0, 1, 2
+MSREP_F64, MSREP_F32, MSREP_BF16 = 0, 1, 2
+MSREP_VALIDATE = 0x1
+MSREP_COMP_ALL = 0x10
+MSREP_COMP_NONE = 0x20
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_MATRIX", 3: "OOM", 4: "CUDA",
+          5: "TIMEOUT", 6: "BUDGET", 7: "NOT_FOUND", 8: "SHUTDOWN",
+          9: "WORKSPACE"}
+
+_DTYPE_CODES = {"f64": MSREP_F64, "f32": MSREP_F32, "bf16": MSREP_BF16}
+
+
+class MsrepError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"msrep {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class msrep_matrix(ctypes.Structure):
+    _fields_ = [("fmt", ctypes.c_int32), ("val_dtype", ctypes.c_int32),
+                ("m", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("nnz", ctypes.c_int64), ("ptr", ctypes.c_void_p),
+                ("idx", ctypes.c_void_p), ("idx2", ctypes.c_void_p),
+                ("val", ctypes.c_void_p)]
+
+
+class msrep_partition(ctypes.Structure):
+    _fields_ = [("np", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("start_idx", ctypes.c_void_p), ("end_idx", ctypes.c_void_p),
+                ("start_major", ctypes.c_void_p), ("end_major", ctypes.c_void_p),
+                ("start_flag", ctypes.c_void_p), ("local_off", ctypes.c_void_p),
+                ("local", ctypes.c_void_p), ("plan", ctypes.c_void_p),
+                ("plan_bytes", ctypes.c_int64)]
+
+
+_M = ctypes.POINTER(msrep_matrix)
+_P = ctypes.POINTER(msrep_partition)
+_vp = ctypes.c_void_p
+
+# name -> (restype, argtypes); mirrors include/msrep.h
+SIGNATURES = {
+    "msrep_version": (ctypes.c_char_p, []),
+    "msrep_last_error": (ctypes.c_char_p, []),
+    "msrep_partition_local_bound": (ctypes.c_int, [_M, ctypes.c_int32,
+                                                   ctypes.POINTER(ctypes.c_int64)]),
+    "msrep_tile_supported": (ctypes.c_int, [ctypes.c_int32]),
+    "msrep_plan_size": (ctypes.c_int, [_M, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    "msrep_partition_csr": (ctypes.c_int, [_M, _P, ctypes.c_uint, _vp]),
+    "msrep_partition_csc": (ctypes.c_int, [_M, _P, ctypes.c_uint, _vp]),
+    "msrep_partition_coo": (ctypes.c_int, [_M, _P, ctypes.c_uint, _vp]),
+    "msrep_spmv_workspace_size": (ctypes.c_int, [_M, _P,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "msrep_spmv": (ctypes.c_int, [_M, _P, ctypes.c_double, _vp, ctypes.c_double,
+                                  _vp, ctypes.c_int32, ctypes.c_uint, _vp, _vp]),
+    "msrep_profile_events": (ctypes.c_int, [_vp, _vp]),
+}
+
+
+def lib(path: str | None = None):
+    """Load libmsrep.so (raises if it has not been built)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(
+                    "libmsrep.so is not built: run "
+                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+            so = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(so, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = so
+    return _LIB
+
+
+def _check(status: int):
+    if status != 0:
+        msg = lib().msrep_last_error()
+        raise MsrepError(status, msg.decode() if msg else "")
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream")
+                           else int(stream))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+# --------------------------------------------------------------------------
+# device-side containers
+# --------------------------------------------------------------------------
+
+def _val_tensor(val: np.ndarray, val_dtype: str, device):
+    import torch
+
+    from . import inputs as I
+    if val_dtype == "f64":
+        return torch.from_numpy(np.ascontiguousarray(val, np.float64)).to(device)
+    if val_dtype == "f32":
+        return torch.from_numpy(I.to_f32(val)).to(device)
+    if val_dtype == "bf16":
+        bits = I.bf16_bits(val).view(np.int16)
+        return torch.from_numpy(bits).to(device).view(torch.bfloat16)
+    raise ValueError(val_dtype)
+
+
+class DeviceMatrix:
+    """A matrix resident in device memory plus its msrep_matrix struct."""
+
+    def __init__(self, fmt, m, n, nnz, ptr, idx, idx2, val, val_dtype: str):
+        self.fmt, self.m, self.n, self.nnz = fmt, int(m), int(n), int(nnz)
+        self.ptr, self.idx, self.idx2, self.val = ptr, idx, idx2, val
+        self.val_dtype = val_dtype
+        self.c = msrep_matrix(fmt, _DTYPE_CODES[val_dtype], self.m, self.n,
+                              self.nnz, _ptr(ptr), _ptr(idx), _ptr(idx2),
+                              _ptr(val))
+
+    @property
+    def format_name(self):
+        return {MSREP_CSR: "csr", MSREP_CSC: "csc", MSREP_COO: "coo"}[self.fmt]
+
+    @classmethod
+    def from_host(cls, a, fmt: str = "csr", val_dtype: str = "f64",
+                  device="cuda"):
+        """Upload an inputs.CSR (converted to `fmt`) to the device."""
+        import torch
+
+        from . import inputs as I
+
+        def t32(v):
+            return torch.from_numpy(np.ascontiguousarray(v, np.int32)).to(device)
+        if fmt == "csr":
+            return cls(MSREP_CSR, a.m, a.n, a.nnz, t32(a.row_ptr), t32(a.col_idx),
+                       None, _val_tensor(a.val, val_dtype, device), val_dtype)
+        if fmt == "csc":
+            c = I.csr_to_csc(a)
+            return cls(MSREP_CSC, a.m, a.n, a.nnz, t32(c.col_ptr), t32(c.row_idx),
+                       None, _val_tensor(c.val, val_dtype, device), val_dtype)
+        if fmt == "coo":
+            q = I.csr_to_coo(a)
+            return cls(MSREP_COO, a.m, a.n, a.nnz, None, t32(q.col_idx),
+                       t32(q.row_idx), _val_tensor(q.val, val_dtype, device),
+                       val_dtype)
+        raise ValueError(fmt)
+
+    def nbytes(self) -> int:
+        return sum(t.numel() * t.element_size()
+                   for t in (self.ptr, self.idx, self.idx2, self.val)
+                   if t is not None)
+
+
+class DevicePartition:
+    """Caller-allocated pCSR/pCSC/pCOO metadata (+ optional local pointers
+    and tile plan) for one matrix, plus its msrep_partition struct."""
+
+    def __init__(self, A: DeviceMatrix, np_: int, tile: int = 0,
+                 local: bool = False, plan: bool = True, device="cuda"):
+        import torch
+        self.np, self.tile = int(np_), int(tile)
+        i32 = dict(dtype=torch.int32, device=device)
+        self.start_idx = torch.empty(self.np, **i32)
+        self.end_idx = torch.empty(self.np, **i32)
+        self.start_major = torch.empty(self.np, **i32)
+        self.end_major = torch.empty(self.np, **i32)
+        self.start_flag = torch.empty(self.np, dtype=torch.uint8, device=device)
+        self.local_off = self.local = None
+        if local:
+            if A.fmt != MSREP_COO:
+                self.local_off = torch.empty(self.np + 1, dtype=torch.int64,
+                                             device=device)
+            self.local = torch.empty(max(1, msrep_partition_local_bound(A, self.np)),
+                                     **i32)
+        self.plan = None
+        pb = 0
+        if plan and A.fmt != MSREP_COO:
+            pb = msrep_plan_size(A, self.np, self.tile)
+            self.plan = torch.empty(max(pb, 256), dtype=torch.uint8, device=device)
+        self.c = msrep_partition(
+            self.np, self.tile, _ptr(self.start_idx), _ptr(self.end_idx),
+            _ptr(self.start_major), _ptr(self.end_major), _ptr(self.start_flag),
+            _ptr(self.local_off), _ptr(self.local), _ptr(self.plan), pb)
+
+    def to_host(self) -> dict:
+        out = {k: getattr(self, k).cpu().numpy() for k in
+               ("start_idx", "end_idx", "start_major", "end_major", "start_flag")}
+        if self.local_off is not None:
+            out["local_off"] = self.local_off.cpu().numpy()
+            out["local"] = self.local.cpu().numpy()[: int(out["local_off"][-1])]
+        elif self.local is not None:
+            out["local"] = self.local.cpu().numpy()
+        return out
+
+
+# --------------------------------------------------------------------------
+# the C entry points
+# --------------------------------------------------------------------------
+
+def msrep_version() -> str:
+    return lib().msrep_version().decode()
+
+
+def msrep_partition_local_bound(A: DeviceMatrix, np_: int) -> int:
+    out = ctypes.c_int64()
+    _check(lib().msrep_partition_local_bound(ctypes.byref(A.c), np_,
+                                             ctypes.byref(out)))
+    return out.value
+
+
+def msrep_tile_supported(tile: int) -> bool:
+    return bool(lib().msrep_tile_supported(tile))
+
+
+def msrep_plan_size(A: DeviceMatrix, np_: int, tile: int = 0) -> int:
+    out = ctypes.c_int64()
+    _check(lib().msrep_plan_size(ctypes.byref(A.c), np_, tile, ctypes.byref(out)))
+    return out.value
+
+
+def msrep_partition_csr(A: DeviceMatrix, part: DevicePartition, flags: int = 0,
+                        stream=None):
+    _check(lib().msrep_partition_csr(ctypes.byref(A.c), ctypes.byref(part.c),
+                                     flags, _stream(stream)))
+
+
+def msrep_partition_csc(A: DeviceMatrix, part: DevicePartition, flags: int = 0,
+                        stream=None):
+    _check(lib().msrep_partition_csc(ctypes.byref(A.c), ctypes.byref(part.c),
+                                     flags, _stream(stream)))
+
+
+def msrep_partition_coo(A: DeviceMatrix, part: DevicePartition, flags: int = 0,
+                        stream=None):
+    _check(lib().msrep_partition_coo(ctypes.byref(A.c), ctypes.byref(part.c),
+                                     flags, _stream(stream)))
+
+
+def msrep_partition(A: DeviceMatrix, part: DevicePartition, flags: int = 0,
+                    stream=None):
+    """Dispatch to msrep_partition_{csr,csc,coo} by the matrix format."""
+    {MSREP_CSR: msrep_partition_csr, MSREP_CSC: msrep_partition_csc,
+     MSREP_COO: msrep_partition_coo}[A.fmt](A, part, flags, stream)
+
+
+def msrep_spmv_workspace_size(A: DeviceMatrix, part: DevicePartition) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().msrep_spmv_workspace_size(ctypes.byref(A.c), ctypes.byref(part.c),
+                                           ctypes.byref(out)))
+    return out.value
+
+
+def alloc_workspace(A: DeviceMatrix, part: DevicePartition, device="cuda"):
+    import torch
+    return torch.empty(max(256, msrep_spmv_workspace_size(A, part)),
+                       dtype=torch.uint8, device=device)
+
+
+def msrep_spmv(A: DeviceMatrix, part: DevicePartition, alpha: float, x,
+               beta: float, y, flags: int = 0, workspace=None, stream=None):
+    """y = alpha*A*x + beta*y.  x, y are device tensors (float64 for an FP64
+    matrix, float32 for FP32/BF16 values)."""
+    import torch
+    xy = MSREP_F64 if y.dtype == torch.float64 else MSREP_F32
+    _check(lib().msrep_spmv(ctypes.byref(A.c), ctypes.byref(part.c),
+                            float(alpha), _ptr(x), float(beta), _ptr(y), xy,
+                            flags, _ptr(workspace), _stream(stream)))
+
+
+def msrep_profile_events(start=None, stop=None):
+    """Record torch.cuda.Event `start`/`stop` around the main kernel of every
+    following msrep_spmv call on this thread (None, None to stop)."""
+    sp = ctypes.c_void_p(start.cuda_event) if start is not None else None
+    ep = ctypes.c_void_p(stop.cuda_event) if stop is not None else None
+    _check(lib().msrep_profile_events(sp, ep))

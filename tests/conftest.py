@@ -28,3 +28,15 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def rmat_full():
+    from paper_2209_07552_gb300 import inputs as I
+    return I.rmat_full()
+
+
+@pytest.fixture(scope="session")
+def laplace_full():
+    from paper_2209_07552_gb300 import inputs as I
+    return I.laplace_full()
