@@ -178,7 +178,7 @@ msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
  * applied once (Sec. 3.2.1, Sec. 4.3).  CSR and COO merge without atomics;
  * CSC scatters into y with atomic adds (the column merge of Alg. 5), so its
  * rounding order varies from run to run.
- * `workspace` must hold msrep_spmv_workspace_size() bytes, 256-byte
+ * `workspace` must hold msrep_spmv_workspace_size() bytes, 16-byte
  * aligned.  Errors: INVALID_ARG, WORKSPACE, CUDA. */
 msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
                         double alpha, const void *x, double beta, void *y,

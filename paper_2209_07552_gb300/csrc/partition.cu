@@ -392,8 +392,8 @@ static msrep_status partition_compressed(const msrep_matrix *A,
   if (p->plan && p->plan_bytes < static_cast<int64_t>(L.bytes))
     return fail(MSREP_ERR_WORKSPACE, "plan buffer has %lld bytes, needs %zu",
                 (long long)p->plan_bytes, L.bytes);
-  if (p->plan && (reinterpret_cast<uintptr_t>(p->plan) & 255))
-    return fail(MSREP_ERR_INVALID_ARG, "plan must be 256-byte aligned");
+  if (p->plan && (reinterpret_cast<uintptr_t>(p->plan) & 15))
+    return fail(MSREP_ERR_INVALID_ARG, "plan must be 16-byte aligned");
   char *plan = static_cast<char *>(p->plan);
   int64_t *D = plan ? reinterpret_cast<int64_t *>(plan + L.off_D) : nullptr;
   int32_t *R = plan ? reinterpret_cast<int32_t *>(plan + L.off_R) : nullptr;

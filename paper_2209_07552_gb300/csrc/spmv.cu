@@ -888,8 +888,8 @@ msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
     return ok();
   }
   if (!workspace) return fail(MSREP_ERR_WORKSPACE, "workspace is NULL");
-  if (reinterpret_cast<uintptr_t>(workspace) & 255)
-    return fail(MSREP_ERR_INVALID_ARG, "workspace must be 256-byte aligned");
+  if (reinterpret_cast<uintptr_t>(workspace) & 15)
+    return fail(MSREP_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
   const int64_t tiles = tiles_for(A, part, tile);
   const int64_t m_acc = (A->fmt == MSREP_CSC && !f64) ? A->m : 0;
   Workspace w;

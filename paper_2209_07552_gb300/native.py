@@ -39,7 +39,7 @@ class MsrepError(RuntimeError):
         self.status = status
 
 
-class msrep_matrix(ctypes.Structure):
+class c_msrep_matrix(ctypes.Structure):
     _fields_ = [("fmt", ctypes.c_int32), ("val_dtype", ctypes.c_int32),
                 ("m", ctypes.c_int32), ("n", ctypes.c_int32),
                 ("nnz", ctypes.c_int64), ("ptr", ctypes.c_void_p),
@@ -47,7 +47,7 @@ class msrep_matrix(ctypes.Structure):
                 ("val", ctypes.c_void_p)]
 
 
-class msrep_partition(ctypes.Structure):
+class c_msrep_partition(ctypes.Structure):
     _fields_ = [("np", ctypes.c_int32), ("tile", ctypes.c_int32),
                 ("start_idx", ctypes.c_void_p), ("end_idx", ctypes.c_void_p),
                 ("start_major", ctypes.c_void_p), ("end_major", ctypes.c_void_p),
@@ -56,8 +56,8 @@ class msrep_partition(ctypes.Structure):
                 ("plan_bytes", ctypes.c_int64)]
 
 
-_M = ctypes.POINTER(msrep_matrix)
-_P = ctypes.POINTER(msrep_partition)
+_M = ctypes.POINTER(c_msrep_matrix)
+_P = ctypes.POINTER(c_msrep_partition)
 _vp = ctypes.c_void_p
 
 # name -> (restype, argtypes); mirrors include/msrep.h
@@ -142,7 +142,7 @@ class DeviceMatrix:
         self.fmt, self.m, self.n, self.nnz = fmt, int(m), int(n), int(nnz)
         self.ptr, self.idx, self.idx2, self.val = ptr, idx, idx2, val
         self.val_dtype = val_dtype
-        self.c = msrep_matrix(fmt, _DTYPE_CODES[val_dtype], self.m, self.n,
+        self.c = c_msrep_matrix(fmt, _DTYPE_CODES[val_dtype], self.m, self.n,
                               self.nnz, _ptr(ptr), _ptr(idx), _ptr(idx2),
                               _ptr(val))
 
@@ -206,7 +206,7 @@ class DevicePartition:
         if plan and A.fmt != MSREP_COO:
             pb = msrep_plan_size(A, self.np, self.tile)
             self.plan = torch.empty(max(pb, 256), dtype=torch.uint8, device=device)
-        self.c = msrep_partition(
+        self.c = c_msrep_partition(
             self.np, self.tile, _ptr(self.start_idx), _ptr(self.end_idx),
             _ptr(self.start_major), _ptr(self.end_major), _ptr(self.start_flag),
             _ptr(self.local_off), _ptr(self.local), _ptr(self.plan), pb)

@@ -42,7 +42,7 @@ def test_host_only_entry_points(so):
     assert N.msrep_version().startswith("msrep")
     assert N.msrep_tile_supported(2048) and not N.msrep_tile_supported(100)
     A = N.DeviceMatrix.__new__(N.DeviceMatrix)
-    A.c = N.msrep_matrix(N.MSREP_CSR, N.MSREP_F64, 1000, 1000, 5000, 1, 1, None, 1)
+    A.c = N.c_msrep_matrix(N.MSREP_CSR, N.MSREP_F64, 1000, 1000, 5000, 1, 1, None, 1)
     A.fmt = N.MSREP_CSR
     assert N.msrep_partition_local_bound(A, 10) == 1000 + 20
     assert N.msrep_plan_size(A, 10, 0) > 0
