@@ -188,6 +188,7 @@ class DevicePartition:
                  local: bool = False, plan: bool = True, device="cuda"):
         import torch
         self.np, self.tile = int(np_), int(tile)
+        self.nnz = A.nnz
         i32 = dict(dtype=torch.int32, device=device)
         self.start_idx = torch.empty(self.np, **i32)
         self.end_idx = torch.empty(self.np, **i32)
@@ -218,7 +219,7 @@ class DevicePartition:
             out["local_off"] = self.local_off.cpu().numpy()
             out["local"] = self.local.cpu().numpy()[: int(out["local_off"][-1])]
         elif self.local is not None:
-            out["local"] = self.local.cpu().numpy()
+            out["local"] = self.local.cpu().numpy()[: self.nnz]
         return out
 
 
@@ -299,6 +300,11 @@ def msrep_spmv(A: DeviceMatrix, part: DevicePartition, alpha: float, x,
 def msrep_profile_events(start=None, stop=None):
     """Record torch.cuda.Event `start`/`stop` around the main kernel of every
     following msrep_spmv call on this thread (None, None to stop)."""
+    if start is not None:
+        # torch only reports elapsed time for events it has seen recorded;
+        # the library re-records the same CUDA events on every call
+        start.record()
+        stop.record()
     sp = ctypes.c_void_p(start.cuda_event) if start is not None else None
     ep = ctypes.c_void_p(stop.cuda_event) if stop is not None else None
     _check(lib().msrep_profile_events(sp, ep))
