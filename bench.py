@@ -404,6 +404,31 @@ def run_precision(M, args, dev):
     return out
 
 
+def run_profile_case(args):
+    """A short fixed case for ncu captures: partition the R-MAT matrix once,
+    then `--reps` calls of msrep_spmv in one format and value type."""
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    a = I.rmat_full() if args.profile_matrix == "rmat" else I.laplace_full()
+    dt = args.profile_dtype
+    A = M.DeviceMatrix.from_host(a, args.profile, dt, device=dev)
+    part = M.DevicePartition(A, args.P, tile=args.tile, device=dev)
+    M.msrep_partition(A, part)
+    xt = torch.float64 if dt == "f64" else torch.float32
+    x = torch.from_numpy(I.vector(a.n, I.SEED_BASE + 1)).to(dev, xt)
+    y = torch.empty(a.m, dtype=xt, device=dev)
+    ws = M.alloc_workspace(A, part, device=dev)
+    for _ in range(args.reps):
+        M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile, "matrix": args.profile_matrix,
+                      "dtype": dt, "reps": args.reps, "P": args.P,
+                      "y_norm": float(torch.linalg.norm(y.double()))}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,7 +440,15 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-precision", action="store_true")
+    ap.add_argument("--profile", choices=FORMATS, default=None,
+                    help="run only a short fixed case (for ncu captures)")
+    ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")
+    ap.add_argument("--profile-dtype", choices=["f64", "f32", "bf16"], default="f64")
+    ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
