@@ -429,6 +429,44 @@ def run_profile_case(args):
                       "y_norm": float(torch.linalg.norm(y.double()))}))
 
 
+def run_sweep(args):
+    """Kernel time of every (matrix, format, tile, P) combination (FP64),
+    one JSON line each; used to choose the defaults."""
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    peak, _ = measured_peaks()
+    mats = load_workload()
+    for name, a in mats.items():
+        x = torch.from_numpy(I.vector(a.n, I.SEED_BASE + 1)).to(dev)
+        y = torch.empty(a.m, dtype=torch.float64, device=dev)
+        for fmt in FORMATS:
+            A = M.DeviceMatrix.from_host(a, fmt, "f64", device=dev)
+            nb = algorithmic_bytes(fmt, a.m, a.n, a.nnz, 8, 8)
+            for tile in (1024, 2048, 4096):
+                for P in (148, 148 * 16, 148 * 64):
+                    part = M.DevicePartition(A, P, tile=tile, device=dev)
+                    M.msrep_partition(A, part)
+                    ws = M.alloc_workspace(A, part, device=dev)
+                    for _ in range(3):
+                        M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+                    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    M.native.msrep_profile_events(s0, s1)
+                    tot = 0.0
+                    for _ in range(10):
+                        M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+                        s1.synchronize()
+                        tot += s0.elapsed_time(s1)
+                    M.native.msrep_profile_events(None, None)
+                    us = 100.0 * tot
+                    print(json.dumps({"matrix": name, "fmt": fmt, "tile": tile, "P": P,
+                                      "kernel_us": us, "gbs": nb / us / 1e3,
+                                      "frac": nb / us / 1e3 / peak}), flush=True)
+            del A
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,7 +483,11 @@ def main():
     ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")
     ap.add_argument("--profile-dtype", choices=["f64", "f32", "bf16"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--sweep", action="store_true", help="time every (format, tile, P)")
     args = ap.parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     if args.profile:
         run_profile_case(args)
         return

@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "spmv_core.cuh"
 
 namespace msrep {
 
@@ -26,275 +27,29 @@ msrep_status check_matrix(const msrep_matrix *A);
 int32_t effective_tile(int32_t tile);
 
 // ---------------------------------------------------------------------------
-// arithmetic policies
+// single-matrix kernels: a grid of (resident blocks x SMs) walks the tiles
 // ---------------------------------------------------------------------------
 
-// Plain FP64: products and sums rounded in binary64.
-struct PolF64 {
-  using V = double;
-  using X = double;
-  using Prod = double;
-  using Acc = double;
-  __device__ static Prod prod(double v, double x) { return __dmul_rn(v, x); }
-  __device__ static Acc zero() { return 0.0; }
-  __device__ static Acc add(Acc a, Prod p, bool) { return __dadd_rn(a, p); }
-  __device__ static Acc combine(Acc a, Acc b) { return __dadd_rn(a, b); }
-  __device__ static double to_f64(Acc a) { return a; }
-  __device__ static X finish(Acc a, double alpha, double beta, X yold) {
-    return beta == 0.0 ? alpha * a : alpha * a + beta * yold;
-  }
-  __device__ static Acc shfl_up(Acc a, int o) { return __shfl_up_sync(0xffffffffu, a, o); }
-};
-
-// Low precision: values FP32 or BF16, x and y FP32, binary32 accumulation.
-// A product is kept with its rounding error (TwoProduct by FMA); rows that
-// are compensated accumulate (s, c) by TwoSum, i.e. Ogita-Rump-Oishi Dot2.
-struct F32Pair {
-  float s, c;
-};
-
-template <typename VT>
-struct PolF32 {
-  using V = VT;
-  using X = float;
-  using Prod = float2;  // (product, its rounding error)
-  using Acc = F32Pair;
-  __device__ static Prod prod(float v, float x) {
-    float p, e;
-    two_prod(v, x, p, e);
-    return make_float2(p, e);
-  }
-  __device__ static Acc zero() { return F32Pair{0.f, 0.f}; }
-  __device__ static Acc add(Acc a, Prod p, bool comp) {
-    if (comp) {
-      float s, e;
-      two_sum(a.s, p.x, s, e);
-      return F32Pair{s, __fadd_rn(a.c, __fadd_rn(e, p.y))};
-    }
-    return F32Pair{__fadd_rn(a.s, p.x), a.c};
-  }
-  __device__ static Acc combine(Acc a, Acc b) {
-    float s, e;
-    two_sum(a.s, b.s, s, e);
-    return F32Pair{s, __fadd_rn(__fadd_rn(a.c, b.c), e)};
-  }
-  __device__ static double to_f64(Acc a) { return double(a.s) + double(a.c); }
-  __device__ static X finish(Acc a, double alpha, double beta, X yold) {
-    float t = __fadd_rn(a.s, a.c);
-    float r = __fmul_rn(float(alpha), t);
-    return beta == 0.0 ? r : __fadd_rn(r, __fmul_rn(float(beta), yold));
-  }
-  __device__ static Acc shfl_up(Acc a, int o) {
-    return F32Pair{__shfl_up_sync(0xffffffffu, a.s, o),
-                   __shfl_up_sync(0xffffffffu, a.c, o)};
-  }
-};
-
-__device__ __forceinline__ double load_x(const double *x, int32_t c) { return __ldg(x + c); }
-__device__ __forceinline__ float load_x(const float *x, int32_t c) { return __ldg(x + c); }
-
-// ---------------------------------------------------------------------------
-// block-wide segmented scan of (flag, value): a set flag restarts the sum.
-// Returns the exclusive prefix; `last` receives the block-inclusive value
-// of the last thread.
-// ---------------------------------------------------------------------------
-
-template <class Pol, int THREADS>
-struct SegScan {
-  using Acc = typename Pol::Acc;
-  struct Storage {
-    Acc wv[THREADS / 32];
-    int wf[THREADS / 32];
-    Acc last;
-  };
-  __device__ static Acc run(Storage &sm, bool flag, Acc v, Acc &last) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int f = flag;
-    Acc inc = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      Acc u = Pol::shfl_up(inc, o);
-      int fu = __shfl_up_sync(0xffffffffu, f, o);
-      if (lane >= o) {
-        if (!f) inc = Pol::combine(u, inc);
-        f |= fu;
-      }
-    }
-    if (lane == 31) {
-      sm.wv[wid] = inc;
-      sm.wf[wid] = f;
-    }
-    __syncthreads();
-    if (wid == 0) {
-      constexpr int NW = THREADS / 32;
-      int wf = lane < NW ? sm.wf[lane] : 0;
-      Acc wv = lane < NW ? sm.wv[lane] : Pol::zero();
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        Acc u = Pol::shfl_up(wv, o);
-        int fu = __shfl_up_sync(0xffffffffu, wf, o);
-        if (lane >= o) {
-          if (!wf) wv = Pol::combine(u, wv);
-          wf |= fu;
-        }
-      }
-      // exclusive prefix over warps, stored back
-      Acc ev = Pol::shfl_up(wv, 1);
-      int ef = __shfl_up_sync(0xffffffffu, wf, 1);
-      if (lane == 0) {
-        ev = Pol::zero();
-        ef = 0;
-      }
-      if (lane < NW) {
-        sm.wv[lane] = ev;
-        sm.wf[lane] = ef;
-      }
-    }
-    __syncthreads();
-    // block-inclusive value of this thread
-    Acc wpre = sm.wv[wid];
-    Acc binc = f ? inc : Pol::combine(wpre, inc);
-    // exclusive = block-inclusive of the previous thread
-    Acc ex = Pol::shfl_up(binc, 1);
-    if (lane == 0) ex = wpre;
-    if (threadIdx.x == THREADS - 1) sm.last = binc;
-    __syncthreads();
-    last = sm.last;
-    return ex;
-  }
-};
-
-// ---------------------------------------------------------------------------
-// CSR: merge-path tiles
-// ---------------------------------------------------------------------------
-
-template <class Pol>
-struct CsrArgs {
-  const int32_t *row_ptr;
-  const int32_t *col_idx;
-  const typename Pol::V *val;
-  const typename Pol::X *x;
-  typename Pol::X *y;
-  double alpha, beta;
-  const int32_t *tile_row;  // [T+1]
-  const int32_t *tile_k;    // [T+1]
-  const int32_t *n_tiles;   // device scalar T
-  double *head, *tail;      // [T] FP64 partials of split rows
-  int32_t m;
-  unsigned comp_mode;       // 0 selective, MSREP_COMP_ALL, MSREP_COMP_NONE
-};
-
-template <class Pol>
-__device__ __forceinline__ bool want_comp(unsigned mode, int64_t len, bool split) {
-  if (mode & MSREP_COMP_ALL) return true;
-  if (mode & MSREP_COMP_NONE) return false;
-  return split || len > 256;
+template <class Pol, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS) csr_tiles(CsrArgs<Pol> a, const int32_t *n_tiles) {
+  __shared__ int32_t s_end[THREADS * IPT];
+  __shared__ ScanSmem<Pol, THREADS> ss;
+  const int T = *n_tiles;
+  for (int b = blockIdx.x; b < T; b += gridDim.x) csr_tile<Pol, THREADS, IPT>(a, b, s_end, ss);
 }
 
 template <class Pol, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS) csr_tiles(CsrArgs<Pol> a) {
-  using Acc = typename Pol::Acc;
-  using Prod = typename Pol::Prod;
-  constexpr int TILE = THREADS * IPT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Prod *s_prod = reinterpret_cast<Prod *>(smem_raw);
-  int32_t *s_end = reinterpret_cast<int32_t *>(smem_raw + sizeof(Prod) * TILE);
-  __shared__ typename SegScan<Pol, THREADS>::Storage scan_sm;
+__global__ void __launch_bounds__(THREADS) coo_tiles(CooArgs<Pol> a) {
+  __shared__ ScanSmem<Pol, THREADS> ss;
+  const int T = a.np * a.G;
+  for (int b = blockIdx.x; b < T; b += gridDim.x) coo_tile<Pol, THREADS, IPT>(a, b, ss);
+}
 
-  const int T = *a.n_tiles;
-  const int tid = threadIdx.x;
-  for (int b = blockIdx.x; b < T; b += gridDim.x) {
-    const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
-    const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
-    const int32_t nrows = r1 - r0, nnzt = k1 - k0;
-    const int32_t rs0 = __ldg(a.row_ptr + r0);
-    const bool flag = rs0 < k0;  // first row started in an earlier tile
-    // end of the last (partial) row, for the compensation predicate
-    const int32_t re_last = (r1 < a.m) ? __ldg(a.row_ptr + r1 + 1) : k1;
-
-    for (int i = tid; i < nrows; i += THREADS) s_end[i] = __ldg(a.row_ptr + r0 + 1 + i) - k0;
-    {
-      int32_t cj[IPT];
-#pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        int j = tid + u * THREADS;
-        cj[u] = j < nnzt ? ld_stream(a.col_idx + k0 + j) : 0;
-      }
-#pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        int j = tid + u * THREADS;
-        if (j < nnzt) s_prod[j] = Pol::prod(ld_stream(a.val + k0 + j), load_x(a.x, cj[u]));
-      }
-    }
-    __syncthreads();
-
-    // this thread's stretch of the tile's merge path
-    const int items = nrows + nnzt;
-    const int d = min(tid * IPT, items);
-    const int dend = min(d + IPT, items);
-    int lo = max(0, d - nnzt), hi = min(d, nrows);
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (s_end[mid] <= d - mid - 1)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    int r = lo, k = d - lo;
-
-    auto row_comp = [&](int rr) -> bool {
-      int64_t st = rr == 0 ? int64_t(rs0) : int64_t(k0) + s_end[rr - 1];
-      int64_t en = rr < nrows ? int64_t(k0) + s_end[rr] : int64_t(re_last);
-      bool split = (rr == 0 && flag) || rr == nrows;
-      return want_comp<Pol>(a.comp_mode, en - st, split);
-    };
-
-    Acc acc = Pol::zero(), first_acc = Pol::zero();
-    bool emitted = false;
-    int first_r = 0;
-    bool comp = (d < dend) ? row_comp(r) : false;
-    for (int it = d; it < dend; ++it) {
-      if (r < nrows && s_end[r] <= k) {
-        if (!emitted) {
-          emitted = true;
-          first_r = r;
-          first_acc = acc;
-        } else {
-          const int32_t row = r0 + r;
-          a.y[row] = Pol::finish(acc, a.alpha, a.beta, a.beta == 0.0 ? 0 : a.y[row]);
-        }
-        acc = Pol::zero();
-        ++r;
-        comp = row_comp(r);
-      } else {
-        acc = Pol::add(acc, s_prod[k], comp);
-        ++k;
-      }
-    }
-
-    Acc last;
-    Acc carry = SegScan<Pol, THREADS>::run(scan_sm, emitted, acc, last);
-    if (emitted) {
-      Acc tot = Pol::combine(carry, first_acc);
-      if (first_r == 0 && flag) {
-        a.head[b] = Pol::to_f64(tot);
-      } else {
-        const int32_t row = r0 + first_r;
-        a.y[row] = Pol::finish(tot, a.alpha, a.beta, a.beta == 0.0 ? 0 : a.y[row]);
-      }
-    }
-    if (tid == THREADS - 1) {
-      if (nrows == 0) {
-        if (flag)
-          a.head[b] = Pol::to_f64(last);
-        else if (nnzt > 0)
-          a.tail[b] = Pol::to_f64(last);
-      } else if (k1 > __ldg(a.row_ptr + r1)) {
-        a.tail[b] = Pol::to_f64(last);
-      }
-    }
-    __syncthreads();
-  }
+template <class Pol, int THREADS, int IPT>
+__global__ void __launch_bounds__(THREADS) csc_tiles(CscArgs<Pol> a, const int32_t *n_tiles) {
+  __shared__ int32_t s_end[THREADS * IPT];
+  const int T = *n_tiles;
+  for (int b = blockIdx.x; b < T; b += gridDim.x) csc_tile<Pol, THREADS, IPT>(a, b, s_end);
 }
 
 // ---------------------------------------------------------------------------
@@ -359,217 +114,6 @@ __global__ void fixup_split_rows(View v, const double *head, const double *tail,
   }
 }
 
-// ---------------------------------------------------------------------------
-// COO: nonzero tiles inside each partition
-// ---------------------------------------------------------------------------
-
-template <class Pol>
-struct CooArgs {
-  const int32_t *row_idx;
-  const int32_t *col_idx;
-  const typename Pol::V *val;
-  const typename Pol::X *x;
-  typename Pol::X *y;
-  double alpha, beta;
-  const int32_t *start_idx, *end_idx;  // partition metadata
-  int32_t np, G, m;
-  int64_t nnz;
-  double *head, *tail;
-  unsigned comp_mode;
-};
-
-template <class X>
-__device__ __forceinline__ void write_beta(X *y, int32_t row, double beta) {
-  y[row] = beta == 0.0 ? X(0) : static_cast<X>(beta * double(y[row]));
-}
-
-template <class Pol, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS) coo_tiles(CooArgs<Pol> a) {
-  using Acc = typename Pol::Acc;
-  using Prod = typename Pol::Prod;
-  constexpr int TILE = THREADS * IPT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Prod *s_prod = reinterpret_cast<Prod *>(smem_raw);
-  int32_t *s_row = reinterpret_cast<int32_t *>(smem_raw + sizeof(Prod) * TILE);
-  __shared__ typename SegScan<Pol, THREADS>::Storage scan_sm;
-
-  const int T = a.np * a.G;
-  const int tid = threadIdx.x;
-  for (int b = blockIdx.x; b < T; b += gridDim.x) {
-    const int i = b / a.G, g = b % a.G;
-    const int64_t s = a.start_idx[i], L = int64_t(a.end_idx[i]) - s + 1;
-    const int32_t k0 = static_cast<int32_t>(s + (int64_t(g) * L) / a.G);
-    const int32_t k1 = static_cast<int32_t>(s + (int64_t(g + 1) * L) / a.G);
-    const int32_t nnzt = k1 - k0;
-    if (tid == 0) {
-      a.head[b] = 0.0;
-      a.tail[b] = 0.0;
-    }
-    if (nnzt == 0) continue;  // uniform across the block
-    const int32_t prev_row = k0 > 0 ? __ldg(a.row_idx + k0 - 1) : -1;
-    const int32_t next_row = k1 < a.nnz ? __ldg(a.row_idx + k1) : a.m;
-    {
-      int32_t cj[IPT];
-#pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        int j = tid + u * THREADS;
-        if (j < nnzt) {
-          cj[u] = ld_stream(a.col_idx + k0 + j);
-          s_row[j] = ld_stream(a.row_idx + k0 + j);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < IPT; ++u) {
-        int j = tid + u * THREADS;
-        if (j < nnzt) s_prod[j] = Pol::prod(ld_stream(a.val + k0 + j), load_x(a.x, cj[u]));
-      }
-    }
-    __syncthreads();
-    const int32_t first_row = s_row[0], last_row = s_row[nnzt - 1];
-    const bool flag = prev_row == first_row;
-    const bool cont = next_row == last_row;
-
-    // leading empty rows (only the tile that holds nonzero 0)
-    if (k0 == 0)
-      for (int32_t rr = tid; rr < first_row; rr += THREADS) write_beta(a.y, rr, a.beta);
-
-    // compensation predicate of the run that starts at j: its length inside
-    // the tile (found by bisection in shared memory) and whether it is split
-    auto run_comp = [&](int j) -> bool {
-      if (a.comp_mode & (MSREP_COMP_ALL | MSREP_COMP_NONE))
-        return want_comp<Pol>(a.comp_mode, 0, false);
-      const int32_t rv = s_row[j];
-      int lo = 0, hi = j;  // first index with row == rv
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (s_row[mid] < rv) lo = mid + 1; else hi = mid;
-      }
-      int st = lo;
-      lo = j;
-      hi = nnzt;  // first index with row > rv
-      while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (s_row[mid] <= rv) lo = mid + 1; else hi = mid;
-      }
-      bool split = (st == 0 && flag) || (lo == nnzt && cont);
-      return want_comp<Pol>(a.comp_mode, lo - st, split);
-    };
-
-    const int j0 = min(tid * IPT, nnzt), j1 = min(j0 + IPT, nnzt);
-    Acc acc = Pol::zero(), first_acc = Pol::zero();
-    bool emitted = false;
-    int32_t first_r = 0;
-    int32_t cur = j0 < nnzt ? (tid == 0 ? first_row : s_row[j0 - 1]) : 0;
-    bool comp = j0 < j1 ? run_comp(j0) : false;
-    for (int j = j0; j < j1; ++j) {
-      const int32_t rj = s_row[j];
-      if (rj != cur) {
-        if (!emitted) {
-          emitted = true;
-          first_r = cur;
-          first_acc = acc;
-        } else {
-          a.y[cur] = Pol::finish(acc, a.alpha, a.beta, a.beta == 0.0 ? 0 : a.y[cur]);
-        }
-        for (int32_t rr = cur + 1; rr < rj; ++rr) write_beta(a.y, rr, a.beta);
-        cur = rj;
-        acc = Pol::zero();
-        comp = run_comp(j);
-      }
-      acc = Pol::add(acc, s_prod[j], comp);
-    }
-
-    Acc last;
-    Acc carry = SegScan<Pol, THREADS>::run(scan_sm, emitted, acc, last);
-    if (emitted) {
-      Acc tot = Pol::combine(carry, first_acc);
-      if (first_r == first_row && flag)
-        a.head[b] = Pol::to_f64(tot);
-      else
-        a.y[first_r] = Pol::finish(tot, a.alpha, a.beta, a.beta == 0.0 ? 0 : a.y[first_r]);
-    }
-    if (tid == THREADS - 1) {
-      if (last_row == first_row && flag)
-        a.head[b] = Pol::to_f64(last);
-      else if (cont)
-        a.tail[b] = Pol::to_f64(last);
-      else
-        a.y[last_row] = Pol::finish(last, a.alpha, a.beta, a.beta == 0.0 ? 0 : a.y[last_row]);
-    }
-    // empty rows between this tile's last row and the next tile's first row
-    if (!cont)
-      for (int32_t rr = last_row + 1 + tid; rr < next_row; rr += THREADS)
-        write_beta(a.y, rr, a.beta);
-    __syncthreads();
-  }
-}
-
-// ---------------------------------------------------------------------------
-// CSC: merge-path tiles over col_ptr, scatter-add into y
-// ---------------------------------------------------------------------------
-
-template <class Pol>
-struct CscArgs {
-  const int32_t *col_ptr;
-  const int32_t *row_idx;
-  const typename Pol::V *val;
-  const typename Pol::X *x;
-  double *yacc;  // FP64 accumulation target (y itself on the FP64 path)
-  double scale;  // alpha on the FP64 path, 1 when a finishing pass follows
-  const int32_t *tile_row, *tile_k, *n_tiles;
-  int32_t n;
-};
-
-template <class Pol, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS) csc_tiles(CscArgs<Pol> a) {
-  constexpr int TILE = THREADS * IPT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *s_val = reinterpret_cast<double *>(smem_raw);
-  int32_t *s_row = reinterpret_cast<int32_t *>(smem_raw + sizeof(double) * TILE);
-  int32_t *s_end = s_row + TILE;
-
-  const int T = *a.n_tiles;
-  const int tid = threadIdx.x;
-  for (int b = blockIdx.x; b < T; b += gridDim.x) {
-    const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
-    const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
-    const int32_t ncols = c1 - c0, nnzt = k1 - k0;
-    for (int i = tid; i < ncols; i += THREADS) s_end[i] = __ldg(a.col_ptr + c0 + 1 + i) - k0;
-#pragma unroll
-    for (int u = 0; u < IPT; ++u) {
-      int j = tid + u * THREADS;
-      if (j < nnzt) {
-        s_row[j] = ld_stream(a.row_idx + k0 + j);
-        s_val[j] = double(ld_stream(a.val + k0 + j));
-      }
-    }
-    __syncthreads();
-    const int items = ncols + nnzt;
-    const int d = min(tid * IPT, items);
-    const int dend = min(d + IPT, items);
-    int lo = max(0, d - nnzt), hi = min(d, ncols);
-    while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (s_end[mid] <= d - mid - 1)
-        lo = mid + 1;
-      else
-        hi = mid;
-    }
-    int c = lo, k = d - lo;
-    double xc = (d < dend && c0 + c < a.n) ? double(load_x(a.x, c0 + c)) * a.scale : 0.0;
-    for (int it = d; it < dend; ++it) {
-      if (c < ncols && s_end[c] <= k) {
-        ++c;
-        xc = (c0 + c < a.n) ? double(load_x(a.x, c0 + c)) * a.scale : 0.0;
-      } else {
-        atomicAdd(a.yacc + s_row[k], s_val[k] * xc);
-        ++k;
-      }
-    }
-    __syncthreads();
-  }
-}
-
 __global__ void scale_f64(double *y, int64_t m, double beta) {
   for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < m;
        r += int64_t(gridDim.x) * blockDim.x)
@@ -610,13 +154,6 @@ static int resident_blocks(K kernel, size_t smem) {
       nb < 1)
     nb = 1;
   return nb;
-}
-
-template <class K>
-static msrep_status prep_kernel(K kernel, size_t smem) {
-  MSREP_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem)));
-  return MSREP_OK;
 }
 
 struct Workspace {
@@ -661,28 +198,24 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
   a.y = static_cast<typename Pol::X *>(y);
   a.alpha = alpha;
   a.beta = beta;
+  a.finish = finish_mode(alpha, beta);
   a.tile_row = reinterpret_cast<const int32_t *>(plan + L.off_row);
   a.tile_k = reinterpret_cast<const int32_t *>(plan + L.off_k);
-  a.n_tiles = reinterpret_cast<const int32_t *>(plan + L.off_toff) + p->np;
+  const int32_t *n_tiles = reinterpret_cast<const int32_t *>(plan + L.off_toff) + p->np;
   a.head = w.head;
   a.tail = w.tail;
   a.m = A->m;
   a.comp_mode = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
-  constexpr int TILE = kThreads * IPT;
-  const size_t smem = (sizeof(typename Pol::Prod) + sizeof(int32_t)) * TILE;
   auto kern = csr_tiles<Pol, kThreads, IPT>;
   static int nb = -1;
-  if (nb < 0) {
-    MSREP_TRY(prep_kernel(kern, smem));
-    nb = resident_blocks(kern, smem);
-  }
+  if (nb < 0) nb = resident_blocks(kern, 0);
   int64_t grid = std::min<int64_t>(L.tmax, int64_t(nb) * sm_count());
   if (grid < 1) grid = 1;
   prof_begin(st);
-  kern<<<static_cast<int>(grid), kThreads, smem, st>>>(a);
+  kern<<<static_cast<int>(grid), kThreads, 0, st>>>(a, n_tiles);
   prof_end(st);
   MSREP_CUDA_TRY(cudaGetLastError());
-  CsrTileView v{a.tile_row, a.tile_k, A->ptr, a.n_tiles};
+  CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   int64_t fg = std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count());
   fixup_split_rows<typename Pol::X, CsrTileView>
       <<<static_cast<int>(std::max<int64_t>(fg, 1)), 256, 0, st>>>(
@@ -704,6 +237,7 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
   a.y = static_cast<typename Pol::X *>(y);
   a.alpha = alpha;
   a.beta = beta;
+  a.finish = finish_mode(alpha, beta);
   a.start_idx = p->start_idx;
   a.end_idx = p->end_idx;
   a.np = p->np;
@@ -713,18 +247,13 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
   a.head = w.head;
   a.tail = w.tail;
   a.comp_mode = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
-  constexpr int TILE = kThreads * IPT;
-  const size_t smem = (sizeof(typename Pol::Prod) + sizeof(int32_t)) * TILE;
   auto kern = coo_tiles<Pol, kThreads, IPT>;
   static int nb = -1;
-  if (nb < 0) {
-    MSREP_TRY(prep_kernel(kern, smem));
-    nb = resident_blocks(kern, smem);
-  }
+  if (nb < 0) nb = resident_blocks(kern, 0);
   const int64_t T = int64_t(a.np) * a.G;
   int64_t grid = std::min<int64_t>(T, int64_t(nb) * sm_count());
   prof_begin(st);
-  kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, smem, st>>>(a);
+  kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, 0, st>>>(a);
   prof_end(st);
   MSREP_CUDA_TRY(cudaGetLastError());
   CooTileView v{A->idx2, p->start_idx, p->end_idx, A->nnz, a.G, a.np, A->m};
@@ -751,13 +280,14 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   a.x = static_cast<const typename Pol::X *>(x);
   a.tile_row = reinterpret_cast<const int32_t *>(plan + L.off_row);
   a.tile_k = reinterpret_cast<const int32_t *>(plan + L.off_k);
-  a.n_tiles = reinterpret_cast<const int32_t *>(plan + L.off_toff) + p->np;
+  const int32_t *n_tiles = reinterpret_cast<const int32_t *>(plan + L.off_toff) + p->np;
   a.n = A->n;
   const int64_t m = A->m;
   const int sg = 4 * sm_count();
   if (kF64) {
     a.yacc = static_cast<double *>(y);
     a.scale = alpha;
+    a.scaled = alpha != 1.0;
     if (m > 0) {
       if (beta == 0.0)
         MSREP_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * m, st));
@@ -767,20 +297,16 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   } else {
     a.yacc = w.yacc;
     a.scale = 1.0;
+    a.scaled = false;
     if (m > 0) MSREP_CUDA_TRY(cudaMemsetAsync(w.yacc, 0, sizeof(double) * m, st));
   }
   MSREP_CUDA_TRY(cudaGetLastError());
-  constexpr int TILE = kThreads * IPT;
-  const size_t smem = (sizeof(double) + 2 * sizeof(int32_t)) * TILE;
   auto kern = csc_tiles<Pol, kThreads, IPT>;
   static int nb = -1;
-  if (nb < 0) {
-    MSREP_TRY(prep_kernel(kern, smem));
-    nb = resident_blocks(kern, smem);
-  }
+  if (nb < 0) nb = resident_blocks(kern, 0);
   int64_t grid = std::min<int64_t>(L.tmax, int64_t(nb) * sm_count());
   prof_begin(st);
-  kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, smem, st>>>(a);
+  kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, 0, st>>>(a, n_tiles);
   prof_end(st);
   MSREP_CUDA_TRY(cudaGetLastError());
   if (!kF64 && m > 0) {

@@ -1,0 +1,536 @@
+// Tile processors of the partitioned SpMV, shared by the single-matrix
+// kernels (spmv.cu) and the persistent batched kernel (batched.cu), so that
+// a matrix gives bit-identical results in both.
+//
+// Work decomposition (two levels, as in the two-level split of Sec. 4.2 with
+// thread blocks in place of GPUs):
+//  * a partition of Alg. 2/4/6 is cut into thread-block tiles; CSR/CSC tiles
+//    are equal stretches of the merge path of (row ends, nonzeros), so both
+//    rows and nonzeros per tile are bounded; COO tiles are equal nonzero
+//    ranges (Alg. 2's split applied inside the partition);
+//  * inside a tile the nonzeros are split evenly over the threads (the same
+//    floor(i*nnz/P) rule), and each thread sums its contiguous run with one
+//    fused multiply-add per nonzero.  On GB300 the FP64 pipe sustains about
+//    two lane operations per clock per SM, so the plain FP64 path is
+//    co-limited by FP64 issue and HBM; one DFMA per nonzero, equal nonzero
+//    counts per lane (no idle lanes in the DFMA warp instructions) and no
+//    FP64 work for row finishing when alpha = 1, beta = 0 keep it near the
+//    memory bound.
+//  * rows split between threads are merged by a segmented scan (a warp-level
+//    fast path when every lane finished a row), rows split between tiles by
+//    the fix-up kernel in tile order, with beta applied once (Sec. 3.2.1,
+//    Sec. 4.3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace msrep {
+
+// ---------------------------------------------------------------------------
+// arithmetic policies
+// ---------------------------------------------------------------------------
+
+// y-update modes, chosen on the host so the device never compares doubles
+enum : int { kFinishCopy = 0, kFinishScale = 1, kFinishAxpby = 2 };
+
+inline int finish_mode(double alpha, double beta) {
+  if (beta == 0.0) return alpha == 1.0 ? kFinishCopy : kFinishScale;
+  return kFinishAxpby;
+}
+
+// Plain FP64.  One fused multiply-add per nonzero.
+struct PolF64 {
+  using V = double;
+  using X = double;
+  using Acc = double;
+  static constexpr bool kLow = false;
+  __device__ static Acc zero() { return 0.0; }
+  __device__ static Acc fma(Acc a, double v, double x, bool) { return __fma_rn(v, x, a); }
+  __device__ static Acc combine(Acc a, Acc b) { return __dadd_rn(a, b); }
+  __device__ static double to_f64(Acc a) { return a; }
+  __device__ static X finish(Acc a, int mode, double alpha, double beta, const X *y) {
+    if (mode == kFinishCopy) return a;
+    if (mode == kFinishScale) return __dmul_rn(alpha, a);
+    return __fma_rn(alpha, a, __dmul_rn(beta, *y));
+  }
+  __device__ static Acc shfl_up(Acc a, int o) { return __shfl_up_sync(0xffffffffu, a, o); }
+  __device__ static Acc shfl(Acc a, int l) { return __shfl_sync(0xffffffffu, a, l); }
+};
+
+// Low precision: values FP32 or BF16, x and y FP32, binary32 accumulation.
+// A compensated row accumulates (s, c) by Ogita-Rump-Oishi Dot2: every
+// product keeps its rounding error (TwoProduct by FMA) and every addition
+// its error (TwoSum); a plain row uses one FP32 FMA per nonzero.
+struct F32Pair {
+  float s, c;
+};
+
+template <typename VT>
+struct PolF32 {
+  using V = VT;
+  using X = float;
+  using Acc = F32Pair;
+  static constexpr bool kLow = true;
+  __device__ static Acc zero() { return F32Pair{0.f, 0.f}; }
+  __device__ static Acc fma(Acc a, float v, float x, bool comp) {
+    if (comp) {
+      float p, ep, s, es;
+      two_prod(v, x, p, ep);
+      two_sum(a.s, p, s, es);
+      return F32Pair{s, __fadd_rn(a.c, __fadd_rn(ep, es))};
+    }
+    return F32Pair{__fmaf_rn(v, x, a.s), a.c};
+  }
+  __device__ static Acc combine(Acc a, Acc b) {
+    float s, e;
+    two_sum(a.s, b.s, s, e);
+    return F32Pair{s, __fadd_rn(__fadd_rn(a.c, b.c), e)};
+  }
+  __device__ static double to_f64(Acc a) { return double(a.s) + double(a.c); }
+  __device__ static X finish(Acc a, int mode, double alpha, double beta, const X *y) {
+    float t = __fadd_rn(a.s, a.c);
+    if (mode == kFinishCopy) return t;
+    float r = __fmul_rn(float(alpha), t);
+    if (mode == kFinishScale) return r;
+    return __fmaf_rn(float(beta), *y, r);
+  }
+  __device__ static Acc shfl_up(Acc a, int o) {
+    return F32Pair{__shfl_up_sync(0xffffffffu, a.s, o), __shfl_up_sync(0xffffffffu, a.c, o)};
+  }
+  __device__ static Acc shfl(Acc a, int l) {
+    return F32Pair{__shfl_sync(0xffffffffu, a.s, l), __shfl_sync(0xffffffffu, a.c, l)};
+  }
+};
+
+__device__ __forceinline__ double load_x(const double *x, int32_t c) { return __ldg(x + c); }
+__device__ __forceinline__ float load_x(const float *x, int32_t c) { return __ldg(x + c); }
+
+// Compensation predicate of the low-precision form: rows longer than 256
+// nonzeros and rows split between tiles or partitions, unless the caller
+// forces all / none.
+__device__ __forceinline__ bool want_comp(unsigned mode, int64_t len, bool split) {
+  if (mode & MSREP_COMP_ALL) return true;
+  if (mode & MSREP_COMP_NONE) return false;
+  return split || len > 256;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide segmented scan of (flag, value) over the threads of a tile.
+// A set flag means "this thread finished a row": the running sum restarts
+// after it.  Returns the exclusive prefix (the partial sum that flows into
+// the thread's first finished row) and the inclusive value of the last thread
+// (the partial of the row that continues past the tile).
+// ---------------------------------------------------------------------------
+
+template <class Pol, int THREADS>
+struct ScanSmem {
+  typename Pol::Acc wv[THREADS / 32];
+  int wf[THREADS / 32];
+  typename Pol::Acc last;
+};
+
+template <class Pol, int THREADS>
+__device__ __forceinline__ typename Pol::Acc block_seg_scan(ScanSmem<Pol, THREADS> &sm,
+                                                            bool flag, typename Pol::Acc v,
+                                                            typename Pol::Acc &last) {
+  using Acc = typename Pol::Acc;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int f = flag;
+  Acc inc = v;
+  if (!__all_sync(0xffffffffu, flag)) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      Acc u = Pol::shfl_up(inc, o);
+      int fu = __shfl_up_sync(0xffffffffu, f, o);
+      if (lane >= o) {
+        if (!f) inc = Pol::combine(u, inc);
+        f |= fu;
+      }
+    }
+  }
+  Acc ex = Pol::shfl_up(inc, 1);
+  int fex = __shfl_up_sync(0xffffffffu, f, 1);
+  if (lane == 0) {
+    ex = Pol::zero();
+    fex = 0;
+  }
+  if (lane == 31) {
+    sm.wv[wid] = inc;
+    sm.wf[wid] = f;
+  }
+  __syncthreads();
+  // partial flowing into this warp: walk back over earlier warps to the last
+  // one that finished a row (usually one step)
+  Acc cin = Pol::zero();
+  if (lane == 0) {
+    for (int w = wid - 1; w >= 0; --w) {
+      cin = Pol::combine(sm.wv[w], cin);
+      if (sm.wf[w]) break;
+    }
+  }
+  cin = Pol::shfl(cin, 0);
+  Acc bex = fex ? ex : Pol::combine(cin, ex);
+  if (threadIdx.x == THREADS - 1) sm.last = f ? inc : Pol::combine(cin, inc);
+  __syncthreads();
+  last = sm.last;
+  return bex;
+}
+
+// first index in s[0, n) with s[i] > key (s ascending)
+__device__ __forceinline__ int upper_bound_smem(const int32_t *s, int n, int32_t key) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (s[mid] <= key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// CSR tile
+// ---------------------------------------------------------------------------
+
+template <class Pol>
+struct CsrArgs {
+  const int32_t *row_ptr;
+  const int32_t *col_idx;
+  const typename Pol::V *val;
+  const typename Pol::X *x;
+  typename Pol::X *y;
+  double alpha, beta;
+  int finish;               // kFinish*
+  const int32_t *tile_row;  // [T+1]
+  const int32_t *tile_k;    // [T+1]
+  double *head, *tail;      // [T] FP64 partials of rows split between tiles
+  int32_t m;
+  unsigned comp_mode;
+};
+
+template <class Pol>
+__device__ __forceinline__ void write_row(const CsrArgs<Pol> &a, int32_t row,
+                                          typename Pol::Acc v) {
+  a.y[row] = Pol::finish(v, a.finish, a.alpha, a.beta, a.y + row);
+}
+
+constexpr int kChunk = 8;  // nonzeros loaded per batch of independent loads
+
+// One merge-path tile b.  s_end: shared buffer of >= TILE int32.
+template <class Pol, int THREADS, int IPT>
+__device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *s_end,
+                                         ScanSmem<Pol, THREADS> &ss) {
+  using Acc = typename Pol::Acc;
+  const int tid = threadIdx.x;
+  const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
+  const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
+  const int nrows = r1 - r0, nnzt = k1 - k0;
+  const int32_t rs0 = __ldg(a.row_ptr + r0);
+  const bool flag = rs0 < k0;  // the first row started in an earlier tile
+
+  for (int i = tid; i < nrows; i += THREADS) s_end[i] = __ldg(a.row_ptr + r0 + 1 + i) - k0;
+  __syncthreads();
+
+  // this thread's nonzeros [ka, kb) (tile-local) and rows [r, r_end)
+  const int ka = (tid * nnzt) / THREADS, kb = ((tid + 1) * nnzt) / THREADS;
+  int r = tid == 0 ? 0 : upper_bound_smem(s_end, nrows, ka);
+  const int r_end = upper_bound_smem(s_end, nrows, kb);
+
+  // compensation predicate (low-precision form only)
+  int32_t re_last = 0;
+  if (Pol::kLow) re_last = (r1 < a.m) ? __ldg(a.row_ptr + r1 + 1) : k1;
+  auto row_comp = [&](int rr) -> bool {
+    if (!Pol::kLow) return false;
+    int64_t st = rr == 0 ? int64_t(rs0) : int64_t(k0) + s_end[rr - 1];
+    int64_t en = rr < nrows ? int64_t(k0) + s_end[rr] : int64_t(re_last);
+    return want_comp(a.comp_mode, en - st, (rr == 0 && flag) || rr == nrows);
+  };
+
+  Acc acc = Pol::zero(), first_acc = Pol::zero();
+  bool emitted = false, comp = row_comp(r);
+  int first_r = 0;
+  auto emit = [&]() {
+    if (!emitted) {
+      emitted = true;
+      first_r = r;
+      first_acc = acc;
+    } else {
+      write_row(a, r0 + r, acc);
+    }
+    acc = Pol::zero();
+    ++r;
+    comp = row_comp(r);
+  };
+  while (r < r_end && s_end[r] <= ka) emit();
+
+  const int32_t *colp = a.col_idx + k0 + ka;
+  const typename Pol::V *valp = a.val + k0 + ka;
+  const int cnt = kb - ka;
+  for (int u0 = 0; u0 < cnt; u0 += kChunk) {
+    int32_t c[kChunk];
+    typename Pol::X xv[kChunk];
+    decltype(ld_stream(valp)) v[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u)
+      if (u0 + u < cnt) {
+        c[u] = ld_stream(colp + u0 + u);
+        v[u] = ld_stream(valp + u0 + u);
+      }
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u)
+      if (u0 + u < cnt) xv[u] = load_x(a.x, c[u]);
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u)
+      if (u0 + u < cnt) {
+        acc = Pol::fma(acc, v[u], xv[u], comp);
+        const int kk = ka + u0 + u + 1;
+        while (r < r_end && s_end[r] <= kk) emit();
+      }
+  }
+
+  Acc last;
+  const Acc carry = block_seg_scan<Pol, THREADS>(ss, emitted, acc, last);
+  if (emitted) {
+    const Acc tot = Pol::combine(carry, first_acc);
+    if (first_r == 0 && flag)
+      a.head[b] = Pol::to_f64(tot);
+    else
+      write_row(a, r0 + first_r, tot);
+  }
+  if (tid == THREADS - 1) {
+    if (nrows == 0) {
+      if (flag)
+        a.head[b] = Pol::to_f64(last);
+      else if (nnzt > 0)
+        a.tail[b] = Pol::to_f64(last);
+    } else if (k1 > __ldg(a.row_ptr + r1)) {
+      a.tail[b] = Pol::to_f64(last);
+    }
+  }
+  __syncthreads();  // s_end and the scan storage are reused by the next tile
+}
+
+// ---------------------------------------------------------------------------
+// COO tile (rows sorted)
+// ---------------------------------------------------------------------------
+
+template <class Pol>
+struct CooArgs {
+  const int32_t *row_idx;
+  const int32_t *col_idx;
+  const typename Pol::V *val;
+  const typename Pol::X *x;
+  typename Pol::X *y;
+  double alpha, beta;
+  int finish;
+  const int32_t *start_idx, *end_idx;  // partition metadata (Alg. 6)
+  int32_t np, G, m;
+  int64_t nnz;
+  double *head, *tail;
+  unsigned comp_mode;
+};
+
+template <class Pol>
+__device__ __forceinline__ void coo_write_row(const CooArgs<Pol> &a, int32_t row,
+                                              typename Pol::Acc v) {
+  a.y[row] = Pol::finish(v, a.finish, a.alpha, a.beta, a.y + row);
+}
+
+template <class Pol>
+__device__ __forceinline__ void coo_write_empty(const CooArgs<Pol> &a, int32_t row) {
+  a.y[row] = Pol::finish(Pol::zero(), a.finish, a.alpha, a.beta, a.y + row);
+}
+
+template <class Pol, int THREADS, int IPT>
+__device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b,
+                                         ScanSmem<Pol, THREADS> &ss) {
+  using Acc = typename Pol::Acc;
+  const int tid = threadIdx.x;
+  const int i = b / a.G, g = b % a.G;
+  const int64_t s = a.start_idx[i], L = int64_t(a.end_idx[i]) - s + 1;
+  const int32_t k0 = static_cast<int32_t>(s + (int64_t(g) * L) / a.G);
+  const int32_t k1 = static_cast<int32_t>(s + (int64_t(g + 1) * L) / a.G);
+  const int nnzt = k1 - k0;
+  if (tid == 0) {
+    a.head[b] = 0.0;
+    a.tail[b] = 0.0;
+  }
+  if (nnzt == 0) return;  // uniform across the block
+  const int32_t prev_row = k0 > 0 ? __ldg(a.row_idx + k0 - 1) : -1;
+  const int32_t next_row = k1 < a.nnz ? __ldg(a.row_idx + k1) : a.m;
+  const int32_t first_row = __ldg(a.row_idx + k0), last_row = __ldg(a.row_idx + k1 - 1);
+  const bool flag = prev_row == first_row;
+  const bool cont = next_row == last_row;
+
+  if (k0 == 0)
+    for (int32_t rr = tid; rr < first_row; rr += THREADS) coo_write_empty(a, rr);
+
+  const int ka = (tid * nnzt) / THREADS, kb = ((tid + 1) * nnzt) / THREADS;
+  const int cnt = kb - ka;
+  const int32_t *rowp = a.row_idx + k0 + ka;
+  const int32_t *colp = a.col_idx + k0 + ka;
+  const typename Pol::V *valp = a.val + k0 + ka;
+
+  // compensation predicate of the run of row rv that contains local nonzero
+  // j: length inside the tile by bisection in global row_idx, split if it
+  // touches a tile end that the row crosses
+  auto run_comp = [&](int32_t rv, int j) -> bool {
+    if (!Pol::kLow) return false;
+    if (a.comp_mode & (MSREP_COMP_ALL | MSREP_COMP_NONE))
+      return want_comp(a.comp_mode, 0, false);
+    int lo = 0, hi = j;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (__ldg(a.row_idx + k0 + mid) < rv) lo = mid + 1; else hi = mid;
+    }
+    const int st = lo;
+    lo = j;
+    hi = nnzt;
+    while (lo < hi) {
+      int mid = (lo + hi) >> 1;
+      if (__ldg(a.row_idx + k0 + mid) <= rv) lo = mid + 1; else hi = mid;
+    }
+    return want_comp(a.comp_mode, lo - st, (st == 0 && flag) || (lo == nnzt && cont));
+  };
+
+  Acc acc = Pol::zero(), first_acc = Pol::zero();
+  bool emitted = false, comp = false;
+  int32_t first_r = 0, cur = -1;
+  auto emit = [&]() {
+    if (!emitted) {
+      emitted = true;
+      first_r = cur;
+      first_acc = acc;
+    } else {
+      coo_write_row(a, cur, acc);
+    }
+    acc = Pol::zero();
+  };
+  if (cnt > 0) {
+    cur = __ldg(rowp);
+    comp = run_comp(cur, ka);
+  }
+  for (int u0 = 0; u0 < cnt; u0 += kChunk) {
+    int32_t rw[kChunk], c[kChunk];
+    typename Pol::X xv[kChunk];
+    decltype(ld_stream(valp)) v[kChunk];
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u)
+      if (u0 + u < cnt) {
+        rw[u] = ld_stream(rowp + u0 + u);
+        c[u] = ld_stream(colp + u0 + u);
+        v[u] = ld_stream(valp + u0 + u);
+      }
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u)
+      if (u0 + u < cnt) xv[u] = load_x(a.x, c[u]);
+#pragma unroll
+    for (int u = 0; u < kChunk; ++u)
+      if (u0 + u < cnt) {
+        if (rw[u] != cur) {
+          emit();
+          for (int32_t rr = cur + 1; rr < rw[u]; ++rr) coo_write_empty(a, rr);
+          cur = rw[u];
+          comp = run_comp(cur, ka + u0 + u);
+        }
+        acc = Pol::fma(acc, v[u], xv[u], comp);
+      }
+  }
+  // the thread's last run ends here if the next nonzero starts another row
+  if (cnt > 0) {
+    const int32_t nxt = kb < nnzt ? __ldg(a.row_idx + k0 + kb) : next_row;
+    if (nxt != cur) {
+      emit();
+      if (kb < nnzt)
+        for (int32_t rr = cur + 1; rr < nxt; ++rr) coo_write_empty(a, rr);
+    }
+  }
+
+  Acc last;
+  const Acc carry = block_seg_scan<Pol, THREADS>(ss, emitted, acc, last);
+  if (emitted) {
+    const Acc tot = Pol::combine(carry, first_acc);
+    if (first_r == first_row && flag)
+      a.head[b] = Pol::to_f64(tot);
+    else
+      coo_write_row(a, first_r, tot);
+  }
+  if (tid == THREADS - 1 && cont) {
+    if (last_row == first_row && flag)
+      a.head[b] = Pol::to_f64(last);
+    else
+      a.tail[b] = Pol::to_f64(last);
+  }
+  // empty rows between this tile's last row and the next tile's first row
+  if (!cont)
+    for (int32_t rr = last_row + 1 + tid; rr < next_row; rr += THREADS) coo_write_empty(a, rr);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// CSC tile: scatter-add into an FP64 accumulator (y itself on the FP64 path)
+// ---------------------------------------------------------------------------
+
+template <class Pol>
+struct CscArgs {
+  const int32_t *col_ptr;
+  const int32_t *row_idx;
+  const typename Pol::V *val;
+  const typename Pol::X *x;
+  double *yacc;
+  double scale;  // alpha on the FP64 path, 1 when a finishing pass follows
+  bool scaled;   // scale != 1
+  const int32_t *tile_row, *tile_k;
+  int32_t n;
+};
+
+template <class Pol, int THREADS, int IPT>
+__device__ __forceinline__ void csc_tile(const CscArgs<Pol> &a, int b, int32_t *s_end) {
+  const int tid = threadIdx.x;
+  const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
+  const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
+  const int ncols = c1 - c0, nnzt = k1 - k0;
+  for (int i = tid; i < ncols; i += THREADS) s_end[i] = __ldg(a.col_ptr + c0 + 1 + i) - k0;
+  __syncthreads();
+  const int ka = (tid * nnzt) / THREADS, kb = ((tid + 1) * nnzt) / THREADS;
+  const int cnt = kb - ka;
+  if (cnt > 0) {
+    int c = upper_bound_smem(s_end, ncols, ka);
+    auto colx = [&](int cc) -> double {
+      double xv = double(load_x(a.x, c0 + cc));
+      return a.scaled ? __dmul_rn(xv, a.scale) : xv;
+    };
+    double xc = colx(c);
+    const int32_t *rowp = a.row_idx + k0 + ka;
+    const typename Pol::V *valp = a.val + k0 + ka;
+    for (int u0 = 0; u0 < cnt; u0 += kChunk) {
+      int32_t rw[kChunk];
+      double v[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u)
+        if (u0 + u < cnt) {
+          rw[u] = ld_stream(rowp + u0 + u);
+          v[u] = double(ld_stream(valp + u0 + u));
+        }
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u)
+        if (u0 + u < cnt) {
+          const int kk = ka + u0 + u;
+          if (c < ncols && s_end[c] <= kk) {
+            do {
+              ++c;
+            } while (c < ncols && s_end[c] <= kk);
+            xc = colx(c);
+          }
+          atomicAdd(a.yacc + rw[u], __dmul_rn(v[u], xc));
+        }
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace msrep
