@@ -445,7 +445,7 @@ def run_sweep(args):
         for fmt in FORMATS:
             A = M.DeviceMatrix.from_host(a, fmt, "f64", device=dev)
             nb = algorithmic_bytes(fmt, a.m, a.n, a.nnz, 8, 8)
-            for tile in (1024, 2048, 4096):
+            for tile in (128, 256, 512):
                 for P in (148, 148 * 16, 148 * 64):
                     part = M.DevicePartition(A, P, tile=tile, device=dev)
                     M.msrep_partition(A, part)

@@ -46,11 +46,12 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // tile shapes
 // ---------------------------------------------------------------------------
 
-// A tile is THREADS * IPT merge-path items (rows + nonzeros for CSR/CSC,
-// nonzeros for COO).  The supported shapes are instantiated in spmv.cu.
-constexpr int kDefaultTile = 2048;
+// A tile is 32 * IPT merge-path items (rows + nonzeros for CSR/CSC,
+// nonzeros for COO), processed by one warp.  The supported shapes are
+// instantiated in spmv.cu.
+constexpr int kDefaultTile = 256;
 inline bool tile_supported(int t) {
-  return t == 512 || t == 1024 || t == 2048 || t == 4096;
+  return t == 128 || t == 256 || t == 512 || t == 1024;
 }
 
 // ---------------------------------------------------------------------------

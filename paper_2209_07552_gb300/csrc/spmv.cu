@@ -30,26 +30,30 @@ int32_t effective_tile(int32_t tile);
 // single-matrix kernels: a grid of (resident blocks x SMs) walks the tiles
 // ---------------------------------------------------------------------------
 
-template <class Pol, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS) csr_tiles(CsrArgs<Pol> a, const int32_t *n_tiles) {
-  __shared__ int32_t s_end[THREADS * IPT];
-  __shared__ ScanSmem<Pol, THREADS> ss;
-  const int T = *n_tiles;
-  for (int b = blockIdx.x; b < T; b += gridDim.x) csr_tile<Pol, THREADS, IPT>(a, b, s_end, ss);
+constexpr int kWarps = 8;  // warps per block; each warp owns whole tiles
+constexpr int kThreads = 32 * kWarps;
+
+template <class Pol, int IPT>
+__global__ void __launch_bounds__(kThreads, 4) csr_tiles(CsrArgs<Pol> a, const int32_t *n_tiles) {
+  __shared__ int32_t s_end[kWarps][32 * IPT];
+  const int T = *n_tiles, wid = threadIdx.x >> 5;
+  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps)
+    csr_tile<Pol, IPT>(a, b, s_end[wid]);
 }
 
-template <class Pol, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS) coo_tiles(CooArgs<Pol> a) {
-  __shared__ ScanSmem<Pol, THREADS> ss;
-  const int T = a.np * a.G;
-  for (int b = blockIdx.x; b < T; b += gridDim.x) coo_tile<Pol, THREADS, IPT>(a, b, ss);
+template <class Pol, int IPT>
+__global__ void __launch_bounds__(kThreads, 4) coo_tiles(CooArgs<Pol> a) {
+  const int T = a.np * a.G, wid = threadIdx.x >> 5;
+  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps)
+    coo_tile<Pol, IPT>(a, b);
 }
 
-template <class Pol, int THREADS, int IPT>
-__global__ void __launch_bounds__(THREADS) csc_tiles(CscArgs<Pol> a, const int32_t *n_tiles) {
-  __shared__ int32_t s_end[THREADS * IPT];
-  const int T = *n_tiles;
-  for (int b = blockIdx.x; b < T; b += gridDim.x) csc_tile<Pol, THREADS, IPT>(a, b, s_end);
+template <class Pol, int IPT>
+__global__ void __launch_bounds__(kThreads, 4) csc_tiles(CscArgs<Pol> a, const int32_t *n_tiles) {
+  __shared__ int32_t s_end[kWarps][32 * IPT];
+  const int T = *n_tiles, wid = threadIdx.x >> 5;
+  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps)
+    csc_tile<Pol, IPT>(a, b, s_end[wid]);
 }
 
 // ---------------------------------------------------------------------------
@@ -134,8 +138,6 @@ __global__ void finish_csc_f32(const double *yacc, float *y, int64_t m,
 // launch helpers
 // ---------------------------------------------------------------------------
 
-constexpr int kThreads = 256;
-
 // msrep_profile_events: events recorded around the main kernel
 static thread_local cudaEvent_t g_prof_start = nullptr, g_prof_stop = nullptr;
 
@@ -206,10 +208,10 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
   a.tail = w.tail;
   a.m = A->m;
   a.comp_mode = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
-  auto kern = csr_tiles<Pol, kThreads, IPT>;
+  auto kern = csr_tiles<Pol, IPT>;
   static int nb = -1;
   if (nb < 0) nb = resident_blocks(kern, 0);
-  int64_t grid = std::min<int64_t>(L.tmax, int64_t(nb) * sm_count());
+  int64_t grid = std::min<int64_t>(ceil_div(L.tmax, kWarps), int64_t(nb) * sm_count());
   if (grid < 1) grid = 1;
   prof_begin(st);
   kern<<<static_cast<int>(grid), kThreads, 0, st>>>(a, n_tiles);
@@ -247,11 +249,11 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
   a.head = w.head;
   a.tail = w.tail;
   a.comp_mode = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
-  auto kern = coo_tiles<Pol, kThreads, IPT>;
+  auto kern = coo_tiles<Pol, IPT>;
   static int nb = -1;
   if (nb < 0) nb = resident_blocks(kern, 0);
   const int64_t T = int64_t(a.np) * a.G;
-  int64_t grid = std::min<int64_t>(T, int64_t(nb) * sm_count());
+  int64_t grid = std::min<int64_t>(ceil_div(T, kWarps), int64_t(nb) * sm_count());
   prof_begin(st);
   kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, 0, st>>>(a);
   prof_end(st);
@@ -301,10 +303,10 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
     if (m > 0) MSREP_CUDA_TRY(cudaMemsetAsync(w.yacc, 0, sizeof(double) * m, st));
   }
   MSREP_CUDA_TRY(cudaGetLastError());
-  auto kern = csc_tiles<Pol, kThreads, IPT>;
+  auto kern = csc_tiles<Pol, IPT>;
   static int nb = -1;
   if (nb < 0) nb = resident_blocks(kern, 0);
-  int64_t grid = std::min<int64_t>(L.tmax, int64_t(nb) * sm_count());
+  int64_t grid = std::min<int64_t>(ceil_div(L.tmax, kWarps), int64_t(nb) * sm_count());
   prof_begin(st);
   kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, 0, st>>>(a, n_tiles);
   prof_end(st);
@@ -329,10 +331,10 @@ static msrep_status dispatch_tile(const msrep_matrix *A, const msrep_partition *
     default: return run_csc<Pol, IPT>(A, p, alpha, x, beta, y, w, st);        \
   }
   switch (tile) {
-    case 512: MSREP_FMT_CASE(2)
-    case 1024: MSREP_FMT_CASE(4)
-    case 2048: MSREP_FMT_CASE(8)
-    case 4096: MSREP_FMT_CASE(16)
+    case 128: MSREP_FMT_CASE(4)
+    case 256: MSREP_FMT_CASE(8)
+    case 512: MSREP_FMT_CASE(16)
+    case 1024: MSREP_FMT_CASE(32)
   }
 #undef MSREP_FMT_CASE
   return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", tile);

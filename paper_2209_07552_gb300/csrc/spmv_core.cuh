@@ -4,22 +4,23 @@
 //
 // Work decomposition (two levels, as in the two-level split of Sec. 4.2 with
 // thread blocks in place of GPUs):
-//  * a partition of Alg. 2/4/6 is cut into thread-block tiles; CSR/CSC tiles
-//    are equal stretches of the merge path of (row ends, nonzeros), so both
-//    rows and nonzeros per tile are bounded; COO tiles are equal nonzero
-//    ranges (Alg. 2's split applied inside the partition);
-//  * inside a tile the nonzeros are split evenly over the threads (the same
-//    floor(i*nnz/P) rule), and each thread sums its contiguous run with one
+//  * a partition of Alg. 2/4/6 is cut into warp tiles; CSR/CSC tiles are
+//    equal stretches of the merge path of (row ends, nonzeros), so both rows
+//    and nonzeros per tile are bounded; COO tiles are equal nonzero ranges
+//    (Alg. 2's split applied inside the partition).  A warp owns a tile
+//    alone: no block-wide barrier, so the warps of a block overlap their
+//    memory latencies freely;
+//  * inside a tile the nonzeros are split evenly over the 32 lanes (the same
+//    floor(i*nnz/P) rule), and each lane sums its contiguous run with one
 //    fused multiply-add per nonzero.  On GB300 the FP64 pipe sustains about
 //    two lane operations per clock per SM, so the plain FP64 path is
 //    co-limited by FP64 issue and HBM; one DFMA per nonzero, equal nonzero
 //    counts per lane (no idle lanes in the DFMA warp instructions) and no
 //    FP64 work for row finishing when alpha = 1, beta = 0 keep it near the
 //    memory bound.
-//  * rows split between threads are merged by a segmented scan (a warp-level
-//    fast path when every lane finished a row), rows split between tiles by
-//    the fix-up kernel in tile order, with beta applied once (Sec. 3.2.1,
-//    Sec. 4.3).
+//  * rows split between lanes are merged by a warp segmented scan (skipped
+//    when every lane finished a row), rows split between tiles by the fix-up
+//    kernel in tile order, with beta applied once (Sec. 3.2.1, Sec. 4.3).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -118,29 +119,21 @@ __device__ __forceinline__ bool want_comp(unsigned mode, int64_t len, bool split
 }
 
 // ---------------------------------------------------------------------------
-// block-wide segmented scan of (flag, value) over the threads of a tile.
-// A set flag means "this thread finished a row": the running sum restarts
-// after it.  Returns the exclusive prefix (the partial sum that flows into
-// the thread's first finished row) and the inclusive value of the last thread
-// (the partial of the row that continues past the tile).
+// warp segmented scan of (flag, value) over the lanes of a tile.  A set flag
+// means "this lane finished a row": the running sum restarts after it.
+// Returns the exclusive prefix (the partial that flows into the lane's first
+// finished row) and, in `last`, the inclusive value of lane 31 (the partial
+// of the row that continues past the tile).
 // ---------------------------------------------------------------------------
 
-template <class Pol, int THREADS>
-struct ScanSmem {
-  typename Pol::Acc wv[THREADS / 32];
-  int wf[THREADS / 32];
-  typename Pol::Acc last;
-};
-
-template <class Pol, int THREADS>
-__device__ __forceinline__ typename Pol::Acc block_seg_scan(ScanSmem<Pol, THREADS> &sm,
-                                                            bool flag, typename Pol::Acc v,
-                                                            typename Pol::Acc &last) {
+template <class Pol>
+__device__ __forceinline__ typename Pol::Acc warp_seg_scan(bool flag, typename Pol::Acc v,
+                                                           typename Pol::Acc &last) {
   using Acc = typename Pol::Acc;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int f = flag;
+  const int lane = threadIdx.x & 31;
   Acc inc = v;
   if (!__all_sync(0xffffffffu, flag)) {
+    int f = flag;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       Acc u = Pol::shfl_up(inc, o);
@@ -152,31 +145,9 @@ __device__ __forceinline__ typename Pol::Acc block_seg_scan(ScanSmem<Pol, THREAD
     }
   }
   Acc ex = Pol::shfl_up(inc, 1);
-  int fex = __shfl_up_sync(0xffffffffu, f, 1);
-  if (lane == 0) {
-    ex = Pol::zero();
-    fex = 0;
-  }
-  if (lane == 31) {
-    sm.wv[wid] = inc;
-    sm.wf[wid] = f;
-  }
-  __syncthreads();
-  // partial flowing into this warp: walk back over earlier warps to the last
-  // one that finished a row (usually one step)
-  Acc cin = Pol::zero();
-  if (lane == 0) {
-    for (int w = wid - 1; w >= 0; --w) {
-      cin = Pol::combine(sm.wv[w], cin);
-      if (sm.wf[w]) break;
-    }
-  }
-  cin = Pol::shfl(cin, 0);
-  Acc bex = fex ? ex : Pol::combine(cin, ex);
-  if (threadIdx.x == THREADS - 1) sm.last = f ? inc : Pol::combine(cin, inc);
-  __syncthreads();
-  last = sm.last;
-  return bex;
+  if (lane == 0) ex = Pol::zero();
+  last = Pol::shfl(inc, 31);
+  return ex;
 }
 
 // first index in s[0, n) with s[i] > key (s ascending)
@@ -220,25 +191,26 @@ __device__ __forceinline__ void write_row(const CsrArgs<Pol> &a, int32_t row,
 
 constexpr int kChunk = 8;  // nonzeros loaded per batch of independent loads
 
-// One merge-path tile b.  s_end: shared buffer of >= TILE int32.
-template <class Pol, int THREADS, int IPT>
-__device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *s_end,
-                                         ScanSmem<Pol, THREADS> &ss) {
+// One merge-path tile b, processed by one warp.  s_end: the warp's shared
+// buffer of >= 32 * IPT int32 (row ends of the tile, tile-local offsets).
+template <class Pol, int IPT>
+__device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *s_end) {
   using Acc = typename Pol::Acc;
-  const int tid = threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
   const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
   const int nrows = r1 - r0, nnzt = k1 - k0;
   const int32_t rs0 = __ldg(a.row_ptr + r0);
   const bool flag = rs0 < k0;  // the first row started in an earlier tile
 
-  for (int i = tid; i < nrows; i += THREADS) s_end[i] = __ldg(a.row_ptr + r0 + 1 + i) - k0;
-  __syncthreads();
+  for (int i = lane; i < nrows; i += 32) s_end[i] = __ldg(a.row_ptr + r0 + 1 + i) - k0;
+  __syncwarp();
 
-  // this thread's nonzeros [ka, kb) (tile-local) and rows [r, r_end)
-  const int ka = (tid * nnzt) / THREADS, kb = ((tid + 1) * nnzt) / THREADS;
-  int r = tid == 0 ? 0 : upper_bound_smem(s_end, nrows, ka);
+  // this lane's nonzeros [ka, kb) (tile-local) and the rows it finishes [r, r_end)
+  const int ka = (lane * nnzt) >> 5, kb = ((lane + 1) * nnzt) >> 5;
+  int r = lane == 0 ? 0 : upper_bound_smem(s_end, nrows, ka);
   const int r_end = upper_bound_smem(s_end, nrows, kb);
+  int next_end = r < r_end ? s_end[r] : INT32_MAX;
 
   // compensation predicate (low-precision form only)
   int32_t re_last = 0;
@@ -253,19 +225,23 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
   Acc acc = Pol::zero(), first_acc = Pol::zero();
   bool emitted = false, comp = row_comp(r);
   int first_r = 0;
-  auto emit = [&]() {
-    if (!emitted) {
-      emitted = true;
-      first_r = r;
-      first_acc = acc;
-    } else {
-      write_row(a, r0 + r, acc);
+  // finish every row whose end is <= kk (several when rows are empty)
+  auto finish_rows = [&](int kk) {
+    while (next_end <= kk) {
+      if (!emitted) {
+        emitted = true;
+        first_r = r;
+        first_acc = acc;
+      } else {
+        write_row(a, r0 + r, acc);
+      }
+      acc = Pol::zero();
+      ++r;
+      next_end = r < r_end ? s_end[r] : INT32_MAX;
+      comp = row_comp(r);
     }
-    acc = Pol::zero();
-    ++r;
-    comp = row_comp(r);
   };
-  while (r < r_end && s_end[r] <= ka) emit();
+  finish_rows(ka);
 
   const int32_t *colp = a.col_idx + k0 + ka;
   const typename Pol::V *valp = a.val + k0 + ka;
@@ -287,13 +263,12 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
     for (int u = 0; u < kChunk; ++u)
       if (u0 + u < cnt) {
         acc = Pol::fma(acc, v[u], xv[u], comp);
-        const int kk = ka + u0 + u + 1;
-        while (r < r_end && s_end[r] <= kk) emit();
+        finish_rows(ka + u0 + u + 1);
       }
   }
 
   Acc last;
-  const Acc carry = block_seg_scan<Pol, THREADS>(ss, emitted, acc, last);
+  const Acc carry = warp_seg_scan<Pol>(emitted, acc, last);
   if (emitted) {
     const Acc tot = Pol::combine(carry, first_acc);
     if (first_r == 0 && flag)
@@ -301,7 +276,7 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
     else
       write_row(a, r0 + first_r, tot);
   }
-  if (tid == THREADS - 1) {
+  if (lane == 31) {
     if (nrows == 0) {
       if (flag)
         a.head[b] = Pol::to_f64(last);
@@ -311,7 +286,7 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
       a.tail[b] = Pol::to_f64(last);
     }
   }
-  __syncthreads();  // s_end and the scan storage are reused by the next tile
+  __syncwarp();  // s_end is reused by the warp's next tile
 }
 
 // ---------------------------------------------------------------------------
@@ -345,21 +320,21 @@ __device__ __forceinline__ void coo_write_empty(const CooArgs<Pol> &a, int32_t r
   a.y[row] = Pol::finish(Pol::zero(), a.finish, a.alpha, a.beta, a.y + row);
 }
 
-template <class Pol, int THREADS, int IPT>
-__device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b,
-                                         ScanSmem<Pol, THREADS> &ss) {
+template <class Pol, int IPT>
+__device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b) {
   using Acc = typename Pol::Acc;
-  const int tid = threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const int i = b / a.G, g = b % a.G;
   const int64_t s = a.start_idx[i], L = int64_t(a.end_idx[i]) - s + 1;
   const int32_t k0 = static_cast<int32_t>(s + (int64_t(g) * L) / a.G);
   const int32_t k1 = static_cast<int32_t>(s + (int64_t(g + 1) * L) / a.G);
   const int nnzt = k1 - k0;
-  if (tid == 0) {
+  if (lane == 0) {
     a.head[b] = 0.0;
     a.tail[b] = 0.0;
   }
-  if (nnzt == 0) return;  // uniform across the block
+  __syncwarp();
+  if (nnzt == 0) return;  // uniform across the warp
   const int32_t prev_row = k0 > 0 ? __ldg(a.row_idx + k0 - 1) : -1;
   const int32_t next_row = k1 < a.nnz ? __ldg(a.row_idx + k1) : a.m;
   const int32_t first_row = __ldg(a.row_idx + k0), last_row = __ldg(a.row_idx + k1 - 1);
@@ -367,9 +342,9 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b,
   const bool cont = next_row == last_row;
 
   if (k0 == 0)
-    for (int32_t rr = tid; rr < first_row; rr += THREADS) coo_write_empty(a, rr);
+    for (int32_t rr = lane; rr < first_row; rr += 32) coo_write_empty(a, rr);
 
-  const int ka = (tid * nnzt) / THREADS, kb = ((tid + 1) * nnzt) / THREADS;
+  const int ka = (lane * nnzt) >> 5, kb = ((lane + 1) * nnzt) >> 5;
   const int cnt = kb - ka;
   const int32_t *rowp = a.row_idx + k0 + ka;
   const int32_t *colp = a.col_idx + k0 + ka;
@@ -451,7 +426,7 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b,
   }
 
   Acc last;
-  const Acc carry = block_seg_scan<Pol, THREADS>(ss, emitted, acc, last);
+  const Acc carry = warp_seg_scan<Pol>(emitted, acc, last);
   if (emitted) {
     const Acc tot = Pol::combine(carry, first_acc);
     if (first_r == first_row && flag)
@@ -459,7 +434,7 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b,
     else
       coo_write_row(a, first_r, tot);
   }
-  if (tid == THREADS - 1 && cont) {
+  if (lane == 31 && cont) {
     if (last_row == first_row && flag)
       a.head[b] = Pol::to_f64(last);
     else
@@ -467,8 +442,7 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b,
   }
   // empty rows between this tile's last row and the next tile's first row
   if (!cont)
-    for (int32_t rr = last_row + 1 + tid; rr < next_row; rr += THREADS) coo_write_empty(a, rr);
-  __syncthreads();
+    for (int32_t rr = last_row + 1 + lane; rr < next_row; rr += 32) coo_write_empty(a, rr);
 }
 
 // ---------------------------------------------------------------------------
@@ -488,15 +462,15 @@ struct CscArgs {
   int32_t n;
 };
 
-template <class Pol, int THREADS, int IPT>
+template <class Pol, int IPT>
 __device__ __forceinline__ void csc_tile(const CscArgs<Pol> &a, int b, int32_t *s_end) {
-  const int tid = threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
   const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
   const int ncols = c1 - c0, nnzt = k1 - k0;
-  for (int i = tid; i < ncols; i += THREADS) s_end[i] = __ldg(a.col_ptr + c0 + 1 + i) - k0;
-  __syncthreads();
-  const int ka = (tid * nnzt) / THREADS, kb = ((tid + 1) * nnzt) / THREADS;
+  for (int i = lane; i < ncols; i += 32) s_end[i] = __ldg(a.col_ptr + c0 + 1 + i) - k0;
+  __syncwarp();
+  const int ka = (lane * nnzt) >> 5, kb = ((lane + 1) * nnzt) >> 5;
   const int cnt = kb - ka;
   if (cnt > 0) {
     int c = upper_bound_smem(s_end, ncols, ka);
@@ -530,7 +504,7 @@ __device__ __forceinline__ void csc_tile(const CscArgs<Pol> &a, int b, int32_t *
         }
     }
   }
-  __syncthreads();
+  __syncwarp();
 }
 
 }  // namespace msrep

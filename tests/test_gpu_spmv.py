@@ -17,7 +17,7 @@ from paper_2209_07552_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
-TILES = (512, 1024, 2048, 4096)
+TILES = (128, 256, 512, 1024)
 
 
 def _small_set():
@@ -56,7 +56,7 @@ def test_small_set_alpha_beta(fmt):
             want = oracle_spmv(a, fmt, x, alpha, beta, y0)
             for P in (1, 5, 148, a.nnz + 5):
                 y = gpu_spmv(a, fmt, P, x, alpha, beta, y0 if beta else None,
-                             tile=512)
+                             tile=128)
                 assert normwise(y, want) <= TOL64, (name, alpha, beta, P)
 
 
@@ -66,7 +66,7 @@ def test_integer_valued_bit_exact(fmt):
         a, x = I.integer_twin(a0, seed=9)
         want = oracle_spmv(a, fmt, x)
         for P in (1, 2, 7, 148, 4096):
-            for tile in (512, 2048):
+            for tile in (128, 512):
                 y = gpu_spmv(a, fmt, P, x, tile=tile)
                 assert np.array_equal(y, want), (name, P, tile)
 
