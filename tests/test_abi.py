@@ -40,7 +40,7 @@ def test_host_only_entry_points(so):
     from paper_2209_07552_gb300 import native as N
     N.lib(so._name)
     assert N.msrep_version().startswith("msrep")
-    assert N.msrep_tile_supported(2048) and not N.msrep_tile_supported(100)
+    assert N.msrep_tile_supported(256) and not N.msrep_tile_supported(100)
     A = N.DeviceMatrix.__new__(N.DeviceMatrix)
     A.c = N.c_msrep_matrix(N.MSREP_CSR, N.MSREP_F64, 1000, 1000, 5000, 1, 1, None, 1)
     A.fmt = N.MSREP_CSR
