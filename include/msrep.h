@@ -179,7 +179,9 @@ msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
  * CSC scatters into y with atomic adds (the column merge of Alg. 5), so its
  * rounding order varies from run to run.
  * `workspace` must hold msrep_spmv_workspace_size() bytes, 16-byte
- * aligned.  Errors: INVALID_ARG, WORKSPACE, CUDA. */
+ * aligned.  idx, idx2 and val must be 32-byte aligned (the kernels read
+ * them in aligned groups of 8 elements).  Errors: INVALID_ARG, WORKSPACE,
+ * CUDA. */
 msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
                         double alpha, const void *x, double beta, void *y,
                         int32_t xy_dtype, unsigned flags, void *workspace,

@@ -113,6 +113,42 @@ __device__ __forceinline__ float ld_stream(const bf16_t *p) {
   return __uint_as_float(static_cast<uint32_t>(b) << 16);
 }
 
+// Group loads: 8 consecutive elements starting at an index that is a
+// multiple of 8, as one 256-bit (or 128-bit for bf16) load that bypasses L1
+// (the nonzero stream is read once; L1 is left to the x gathers).  The
+// arrays must be 32-byte aligned (16-byte for bf16 values).
+__device__ __forceinline__ void ld8(const int32_t *p, int32_t (&r)[8]) {
+  asm("ld.global.nc.L1::no_allocate.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+        "=r"(r[6]), "=r"(r[7])
+      : "l"(p));
+}
+__device__ __forceinline__ void ld8(const double *p, double (&v)[8]) {
+  asm("ld.global.nc.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
+      : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+      : "l"(p));
+  asm("ld.global.nc.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
+      : "=d"(v[4]), "=d"(v[5]), "=d"(v[6]), "=d"(v[7])
+      : "l"(p + 4));
+}
+__device__ __forceinline__ void ld8(const float *p, float (&v)[8]) {
+  asm("ld.global.nc.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+        "=f"(v[6]), "=f"(v[7])
+      : "l"(p));
+}
+__device__ __forceinline__ void ld8(const bf16_t *p, float (&v)[8]) {
+  uint32_t w[4];
+  asm("ld.global.nc.L1::no_allocate.v4.b32 {%0,%1,%2,%3}, [%4];"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+      : "l"(p));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = __uint_as_float(w[i] << 16);
+    v[2 * i + 1] = __uint_as_float(w[i] & 0xffff0000u);
+  }
+}
+
 // Knuth's TwoSum: s + e == a + b exactly (round-to-nearest, no FMA
 // contraction possible on these operations because each is a single add).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {

@@ -34,11 +34,12 @@ constexpr int kWarps = 8;  // warps per block; each warp owns whole tiles
 constexpr int kThreads = 32 * kWarps;
 
 template <class Pol, int IPT>
-__global__ void __launch_bounds__(kThreads, 4) csr_tiles(CsrArgs<Pol> a, const int32_t *n_tiles) {
+__global__ void __launch_bounds__(kThreads, 4) csr_tiles(CsrArgs<Pol> a, const int32_t *n_tiles,
+                                                          int64_t nnz) {
   __shared__ int32_t s_end[kWarps][32 * IPT];
   const int T = *n_tiles, wid = threadIdx.x >> 5;
   for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps)
-    csr_tile<Pol, IPT>(a, b, s_end[wid]);
+    csr_tile<Pol, IPT>(a, b, s_end[wid], nnz);
 }
 
 template <class Pol, int IPT>
@@ -49,11 +50,12 @@ __global__ void __launch_bounds__(kThreads, 4) coo_tiles(CooArgs<Pol> a) {
 }
 
 template <class Pol, int IPT>
-__global__ void __launch_bounds__(kThreads, 4) csc_tiles(CscArgs<Pol> a, const int32_t *n_tiles) {
+__global__ void __launch_bounds__(kThreads, 4) csc_tiles(CscArgs<Pol> a, const int32_t *n_tiles,
+                                                          int64_t nnz) {
   __shared__ int32_t s_end[kWarps][32 * IPT];
   const int T = *n_tiles, wid = threadIdx.x >> 5;
   for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps)
-    csc_tile<Pol, IPT>(a, b, s_end[wid]);
+    csc_tile<Pol, IPT>(a, b, s_end[wid], nnz);
 }
 
 // ---------------------------------------------------------------------------
@@ -214,7 +216,7 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
   int64_t grid = std::min<int64_t>(ceil_div(L.tmax, kWarps), int64_t(nb) * sm_count());
   if (grid < 1) grid = 1;
   prof_begin(st);
-  kern<<<static_cast<int>(grid), kThreads, 0, st>>>(a, n_tiles);
+  kern<<<static_cast<int>(grid), kThreads, 0, st>>>(a, n_tiles, A->nnz);
   prof_end(st);
   MSREP_CUDA_TRY(cudaGetLastError());
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
@@ -308,7 +310,7 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   if (nb < 0) nb = resident_blocks(kern, 0);
   int64_t grid = std::min<int64_t>(ceil_div(L.tmax, kWarps), int64_t(nb) * sm_count());
   prof_begin(st);
-  kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, 0, st>>>(a, n_tiles);
+  kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, 0, st>>>(a, n_tiles, A->nnz);
   prof_end(st);
   MSREP_CUDA_TRY(cudaGetLastError());
   if (!kF64 && m > 0) {
@@ -414,6 +416,14 @@ msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
       MSREP_CUDA_TRY(cudaGetLastError());
     }
     return ok();
+  }
+  {
+    // the kernels read the nonzero arrays in aligned groups of 8 elements
+    const uintptr_t mis = reinterpret_cast<uintptr_t>(A->idx) | reinterpret_cast<uintptr_t>(A->idx2) |
+                          reinterpret_cast<uintptr_t>(A->val);
+    if (mis & (A->val_dtype == MSREP_BF16 ? 15 : 31))
+      return fail(MSREP_ERR_INVALID_ARG,
+                  "idx, idx2 and val must be 32-byte aligned (16-byte for bf16-only val)");
   }
   if (!workspace) return fail(MSREP_ERR_WORKSPACE, "workspace is NULL");
   if (reinterpret_cast<uintptr_t>(workspace) & 15)

@@ -163,6 +163,16 @@ __device__ __forceinline__ int upper_bound_smem(const int32_t *s, int n, int32_t
   return lo;
 }
 
+// register type of a loaded value: bf16 values widen to float
+template <class V>
+struct LoadT {
+  using type = V;
+};
+template <>
+struct LoadT<bf16_t> {
+  using type = float;
+};
+
 // ---------------------------------------------------------------------------
 // CSR tile
 // ---------------------------------------------------------------------------
@@ -189,36 +199,66 @@ __device__ __forceinline__ void write_row(const CsrArgs<Pol> &a, int32_t row,
   a.y[row] = Pol::finish(v, a.finish, a.alpha, a.beta, a.y + row);
 }
 
-constexpr int kChunk = 8;  // nonzeros loaded per batch of independent loads
+// One group of 8 nonzeros starting at g8 (a multiple of 8): a single vector
+// load, or element-wise loads for the last group of the array.
+template <class T, class U>
+__device__ __forceinline__ void load_group(const T *arr, int64_t g8, int64_t nnz, U (&out)[8]) {
+  if (g8 + 8 <= nnz) {
+    ld8(arr + g8, out);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) out[u] = (g8 + u < nnz) ? U(ld_stream(arr + g8 + u)) : U(0);
+  }
+}
+
+// The lanes of a warp split the 8-aligned groups that cover the tile's
+// nonzeros [k0, k1) evenly (Alg. 2's floor(i*n/P) rule over groups); lane
+// `lane` owns groups [glo, ghi) and nonzeros [ka, kb) = their intersection
+// with [k0, k1).  Lane ranges are contiguous and cover [k0, k1) in order.
+struct LaneRange {
+  int64_t glo, ghi, ka, kb;
+};
+__device__ __forceinline__ LaneRange lane_range(int64_t k0, int64_t k1, int lane) {
+  const int64_t gA = k0 >> 3, ng = ((k1 + 7) >> 3) - gA;
+  LaneRange r;
+  r.glo = gA + ((lane * ng) >> 5);
+  r.ghi = gA + (((lane + 1) * ng) >> 5);
+  r.ka = min(max(k0, r.glo << 3), k1);
+  r.kb = min(max(k0, r.ghi << 3), k1);
+  return r;
+}
 
 // One merge-path tile b, processed by one warp.  s_end: the warp's shared
-// buffer of >= 32 * IPT int32 (row ends of the tile, tile-local offsets).
+// buffer of >= 32 * IPT int32 (absolute row ends of the tile's rows).
 template <class Pol, int IPT>
-__device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *s_end) {
+__device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *s_end,
+                                         int64_t nnz) {
   using Acc = typename Pol::Acc;
+  using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
   const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
   const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
-  const int nrows = r1 - r0, nnzt = k1 - k0;
+  const int nrows = r1 - r0;
   const int32_t rs0 = __ldg(a.row_ptr + r0);
   const bool flag = rs0 < k0;  // the first row started in an earlier tile
 
-  for (int i = lane; i < nrows; i += 32) s_end[i] = __ldg(a.row_ptr + r0 + 1 + i) - k0;
+  for (int i = lane; i < nrows; i += 32) s_end[i] = __ldg(a.row_ptr + r0 + 1 + i);
   __syncwarp();
 
-  // this lane's nonzeros [ka, kb) (tile-local) and the rows it finishes [r, r_end)
-  const int ka = (lane * nnzt) >> 5, kb = ((lane + 1) * nnzt) >> 5;
+  const LaneRange lr = lane_range(k0, k1, lane);
+  const int32_t ka = static_cast<int32_t>(lr.ka), kb = static_cast<int32_t>(lr.kb);
+  // rows finished by this lane: ends in (ka, kb], plus ends <= k0 for lane 0
   int r = lane == 0 ? 0 : upper_bound_smem(s_end, nrows, ka);
   const int r_end = upper_bound_smem(s_end, nrows, kb);
-  int next_end = r < r_end ? s_end[r] : INT32_MAX;
+  int32_t next_end = r < r_end ? s_end[r] : INT32_MAX;
 
   // compensation predicate (low-precision form only)
   int32_t re_last = 0;
   if (Pol::kLow) re_last = (r1 < a.m) ? __ldg(a.row_ptr + r1 + 1) : k1;
   auto row_comp = [&](int rr) -> bool {
     if (!Pol::kLow) return false;
-    int64_t st = rr == 0 ? int64_t(rs0) : int64_t(k0) + s_end[rr - 1];
-    int64_t en = rr < nrows ? int64_t(k0) + s_end[rr] : int64_t(re_last);
+    int64_t st = rr == 0 ? int64_t(rs0) : int64_t(s_end[rr - 1]);
+    int64_t en = rr < nrows ? int64_t(s_end[rr]) : int64_t(re_last);
     return want_comp(a.comp_mode, en - st, (rr == 0 && flag) || rr == nrows);
   };
 
@@ -226,7 +266,7 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
   bool emitted = false, comp = row_comp(r);
   int first_r = 0;
   // finish every row whose end is <= kk (several when rows are empty)
-  auto finish_rows = [&](int kk) {
+  auto finish_rows = [&](int32_t kk) {
     while (next_end <= kk) {
       if (!emitted) {
         emitted = true;
@@ -243,28 +283,33 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
   };
   finish_rows(ka);
 
-  const int32_t *colp = a.col_idx + k0 + ka;
-  const typename Pol::V *valp = a.val + k0 + ka;
-  const int cnt = kb - ka;
-  for (int u0 = 0; u0 < cnt; u0 += kChunk) {
-    int32_t c[kChunk];
-    typename Pol::X xv[kChunk];
-    decltype(ld_stream(valp)) v[kChunk];
+  for (int64_t g = lr.glo; g < lr.ghi; ++g) {
+    const int64_t g8 = g << 3;
+    int32_t c[8];
+    LV v[8];
+    typename Pol::X xv[8];
+    load_group(a.col_idx, g8, nnz, c);
+    load_group(a.val, g8, nnz, v);
 #pragma unroll
-    for (int u = 0; u < kChunk; ++u)
-      if (u0 + u < cnt) {
-        c[u] = ld_stream(colp + u0 + u);
-        v[u] = ld_stream(valp + u0 + u);
+    for (int u = 0; u < 8; ++u) {
+      const bool in = g8 + u >= ka && g8 + u < kb;
+      xv[u] = in ? load_x(a.x, c[u]) : typename Pol::X(0);
+      if (!in) v[u] = LV(0);
+    }
+    const int32_t gend = static_cast<int32_t>(min(g8 + 8, int64_t(kb)));
+    if (next_end > gend) {
+      // no row ends inside this group: straight multiply-adds
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc = Pol::fma(acc, v[u], xv[u], comp);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (g8 + u >= ka && g8 + u < kb) {
+          acc = Pol::fma(acc, v[u], xv[u], comp);
+          finish_rows(static_cast<int32_t>(g8 + u + 1));
+        }
       }
-#pragma unroll
-    for (int u = 0; u < kChunk; ++u)
-      if (u0 + u < cnt) xv[u] = load_x(a.x, c[u]);
-#pragma unroll
-    for (int u = 0; u < kChunk; ++u)
-      if (u0 + u < cnt) {
-        acc = Pol::fma(acc, v[u], xv[u], comp);
-        finish_rows(ka + u0 + u + 1);
-      }
+    }
   }
 
   Acc last;
@@ -280,7 +325,7 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
     if (nrows == 0) {
       if (flag)
         a.head[b] = Pol::to_f64(last);
-      else if (nnzt > 0)
+      else if (k1 > k0)
         a.tail[b] = Pol::to_f64(last);
     } else if (k1 > __ldg(a.row_ptr + r1)) {
       a.tail[b] = Pol::to_f64(last);
@@ -323,18 +368,18 @@ __device__ __forceinline__ void coo_write_empty(const CooArgs<Pol> &a, int32_t r
 template <class Pol, int IPT>
 __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b) {
   using Acc = typename Pol::Acc;
+  using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
   const int i = b / a.G, g = b % a.G;
   const int64_t s = a.start_idx[i], L = int64_t(a.end_idx[i]) - s + 1;
   const int32_t k0 = static_cast<int32_t>(s + (int64_t(g) * L) / a.G);
   const int32_t k1 = static_cast<int32_t>(s + (int64_t(g + 1) * L) / a.G);
-  const int nnzt = k1 - k0;
   if (lane == 0) {
     a.head[b] = 0.0;
     a.tail[b] = 0.0;
   }
   __syncwarp();
-  if (nnzt == 0) return;  // uniform across the warp
+  if (k1 == k0) return;  // uniform across the warp
   const int32_t prev_row = k0 > 0 ? __ldg(a.row_idx + k0 - 1) : -1;
   const int32_t next_row = k1 < a.nnz ? __ldg(a.row_idx + k1) : a.m;
   const int32_t first_row = __ldg(a.row_idx + k0), last_row = __ldg(a.row_idx + k1 - 1);
@@ -344,32 +389,29 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b) {
   if (k0 == 0)
     for (int32_t rr = lane; rr < first_row; rr += 32) coo_write_empty(a, rr);
 
-  const int ka = (lane * nnzt) >> 5, kb = ((lane + 1) * nnzt) >> 5;
-  const int cnt = kb - ka;
-  const int32_t *rowp = a.row_idx + k0 + ka;
-  const int32_t *colp = a.col_idx + k0 + ka;
-  const typename Pol::V *valp = a.val + k0 + ka;
+  const LaneRange lr = lane_range(k0, k1, lane);
+  const int64_t ka = lr.ka, kb = lr.kb;
 
-  // compensation predicate of the run of row rv that contains local nonzero
-  // j: length inside the tile by bisection in global row_idx, split if it
-  // touches a tile end that the row crosses
-  auto run_comp = [&](int32_t rv, int j) -> bool {
+  // compensation predicate of the run of row rv that contains nonzero j:
+  // its length inside the tile (bisection in row_idx), split if it touches
+  // a tile end that the row crosses
+  auto run_comp = [&](int32_t rv, int64_t j) -> bool {
     if (!Pol::kLow) return false;
     if (a.comp_mode & (MSREP_COMP_ALL | MSREP_COMP_NONE))
       return want_comp(a.comp_mode, 0, false);
-    int lo = 0, hi = j;
+    int64_t lo = k0, hi = j;
     while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (__ldg(a.row_idx + k0 + mid) < rv) lo = mid + 1; else hi = mid;
+      int64_t mid = (lo + hi) >> 1;
+      if (__ldg(a.row_idx + mid) < rv) lo = mid + 1; else hi = mid;
     }
-    const int st = lo;
+    const int64_t st = lo;
     lo = j;
-    hi = nnzt;
+    hi = k1;
     while (lo < hi) {
-      int mid = (lo + hi) >> 1;
-      if (__ldg(a.row_idx + k0 + mid) <= rv) lo = mid + 1; else hi = mid;
+      int64_t mid = (lo + hi) >> 1;
+      if (__ldg(a.row_idx + mid) <= rv) lo = mid + 1; else hi = mid;
     }
-    return want_comp(a.comp_mode, lo - st, (st == 0 && flag) || (lo == nnzt && cont));
+    return want_comp(a.comp_mode, lo - st, (st == k0 && flag) || (lo == k1 && cont));
   };
 
   Acc acc = Pol::zero(), first_acc = Pol::zero();
@@ -385,42 +427,49 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b) {
     }
     acc = Pol::zero();
   };
-  if (cnt > 0) {
-    cur = __ldg(rowp);
-    comp = run_comp(cur, ka);
-  }
-  for (int u0 = 0; u0 < cnt; u0 += kChunk) {
-    int32_t rw[kChunk], c[kChunk];
-    typename Pol::X xv[kChunk];
-    decltype(ld_stream(valp)) v[kChunk];
+  for (int64_t gg = lr.glo; gg < lr.ghi; ++gg) {
+    const int64_t g8 = gg << 3;
+    int32_t rw[8], c[8];
+    LV v[8];
+    typename Pol::X xv[8];
+    load_group(a.row_idx, g8, a.nnz, rw);
+    load_group(a.col_idx, g8, a.nnz, c);
+    load_group(a.val, g8, a.nnz, v);
 #pragma unroll
-    for (int u = 0; u < kChunk; ++u)
-      if (u0 + u < cnt) {
-        rw[u] = ld_stream(rowp + u0 + u);
-        c[u] = ld_stream(colp + u0 + u);
-        v[u] = ld_stream(valp + u0 + u);
-      }
+    for (int u = 0; u < 8; ++u) {
+      const bool in = g8 + u >= ka && g8 + u < kb;
+      xv[u] = in ? load_x(a.x, c[u]) : typename Pol::X(0);
+      if (!in) v[u] = LV(0);
+    }
+    const int ulo = static_cast<int>(max(ka - g8, int64_t(0)));
+    const int uhi = static_cast<int>(min(kb - g8, int64_t(8))) - 1;
+    if (rw[ulo] == cur && rw[uhi] == cur) {
+      // the whole group continues the current row
 #pragma unroll
-    for (int u = 0; u < kChunk; ++u)
-      if (u0 + u < cnt) xv[u] = load_x(a.x, c[u]);
+      for (int u = 0; u < 8; ++u) acc = Pol::fma(acc, v[u], xv[u], comp);
+    } else {
 #pragma unroll
-    for (int u = 0; u < kChunk; ++u)
-      if (u0 + u < cnt) {
-        if (rw[u] != cur) {
-          emit();
-          for (int32_t rr = cur + 1; rr < rw[u]; ++rr) coo_write_empty(a, rr);
-          cur = rw[u];
-          comp = run_comp(cur, ka + u0 + u);
+      for (int u = 0; u < 8; ++u) {
+        if (u >= ulo && u <= uhi) {
+          if (rw[u] != cur) {
+            if (cur >= 0) {
+              emit();
+              for (int32_t rr = cur + 1; rr < rw[u]; ++rr) coo_write_empty(a, rr);
+            }
+            cur = rw[u];
+            comp = run_comp(cur, g8 + u);
+          }
+          acc = Pol::fma(acc, v[u], xv[u], comp);
         }
-        acc = Pol::fma(acc, v[u], xv[u], comp);
       }
+    }
   }
-  // the thread's last run ends here if the next nonzero starts another row
-  if (cnt > 0) {
-    const int32_t nxt = kb < nnzt ? __ldg(a.row_idx + k0 + kb) : next_row;
+  // the lane's last run ends here if the next nonzero starts another row
+  if (kb > ka) {
+    const int32_t nxt = kb < k1 ? __ldg(a.row_idx + kb) : next_row;
     if (nxt != cur) {
       emit();
-      if (kb < nnzt)
+      if (kb < k1)
         for (int32_t rr = cur + 1; rr < nxt; ++rr) coo_write_empty(a, rr);
     }
   }
@@ -463,45 +512,45 @@ struct CscArgs {
 };
 
 template <class Pol, int IPT>
-__device__ __forceinline__ void csc_tile(const CscArgs<Pol> &a, int b, int32_t *s_end) {
+__device__ __forceinline__ void csc_tile(const CscArgs<Pol> &a, int b, int32_t *s_end,
+                                         int64_t nnz) {
+  using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
   const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
   const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
-  const int ncols = c1 - c0, nnzt = k1 - k0;
-  for (int i = lane; i < ncols; i += 32) s_end[i] = __ldg(a.col_ptr + c0 + 1 + i) - k0;
+  const int ncols = c1 - c0;
+  for (int i = lane; i < ncols; i += 32) s_end[i] = __ldg(a.col_ptr + c0 + 1 + i);
   __syncwarp();
-  const int ka = (lane * nnzt) >> 5, kb = ((lane + 1) * nnzt) >> 5;
-  const int cnt = kb - ka;
-  if (cnt > 0) {
-    int c = upper_bound_smem(s_end, ncols, ka);
+  const LaneRange lr = lane_range(k0, k1, lane);
+  const int64_t ka = lr.ka, kb = lr.kb;
+  if (kb > ka) {
+    int c = upper_bound_smem(s_end, ncols, static_cast<int32_t>(ka));
     auto colx = [&](int cc) -> double {
       double xv = double(load_x(a.x, c0 + cc));
       return a.scaled ? __dmul_rn(xv, a.scale) : xv;
     };
     double xc = colx(c);
-    const int32_t *rowp = a.row_idx + k0 + ka;
-    const typename Pol::V *valp = a.val + k0 + ka;
-    for (int u0 = 0; u0 < cnt; u0 += kChunk) {
-      int32_t rw[kChunk];
-      double v[kChunk];
+    int32_t cend = c < ncols ? s_end[c] : INT32_MAX;
+    for (int64_t gg = lr.glo; gg < lr.ghi; ++gg) {
+      const int64_t g8 = gg << 3;
+      int32_t rw[8];
+      LV v[8];
+      load_group(a.row_idx, g8, nnz, rw);
+      load_group(a.val, g8, nnz, v);
 #pragma unroll
-      for (int u = 0; u < kChunk; ++u)
-        if (u0 + u < cnt) {
-          rw[u] = ld_stream(rowp + u0 + u);
-          v[u] = double(ld_stream(valp + u0 + u));
-        }
-#pragma unroll
-      for (int u = 0; u < kChunk; ++u)
-        if (u0 + u < cnt) {
-          const int kk = ka + u0 + u;
-          if (c < ncols && s_end[c] <= kk) {
+      for (int u = 0; u < 8; ++u) {
+        const int64_t e = g8 + u;
+        if (e >= ka && e < kb) {
+          if (cend <= e) {
             do {
               ++c;
-            } while (c < ncols && s_end[c] <= kk);
+              cend = c < ncols ? s_end[c] : INT32_MAX;
+            } while (cend <= e);
             xc = colx(c);
           }
-          atomicAdd(a.yacc + rw[u], __dmul_rn(v[u], xc));
+          atomicAdd(a.yacc + rw[u], __dmul_rn(double(v[u]), xc));
         }
+      }
     }
   }
   __syncwarp();
