@@ -445,24 +445,25 @@ def run_sweep(args):
         for fmt in FORMATS:
             A = M.DeviceMatrix.from_host(a, fmt, "f64", device=dev)
             nb = algorithmic_bytes(fmt, a.m, a.n, a.nnz, 8, 8)
-            for tile in (128, 256, 512):
-                for P in (148, 148 * 16, 148 * 64):
+            for tile, P, direct in [(t, p, d) for t in (128, 256, 512) for p in (148, 148 * 16)
+                                    for d in (False, True)]:
+                    flags = M.MSREP_DIRECT_LOADS if direct else 0
                     part = M.DevicePartition(A, P, tile=tile, device=dev)
                     M.msrep_partition(A, part)
                     ws = M.alloc_workspace(A, part, device=dev)
                     for _ in range(3):
-                        M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+                        M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
                     s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     M.native.msrep_profile_events(s0, s1)
                     tot = 0.0
                     for _ in range(10):
-                        M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+                        M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
                         s1.synchronize()
                         tot += s0.elapsed_time(s1)
                     M.native.msrep_profile_events(None, None)
                     us = 100.0 * tot
                     print(json.dumps({"matrix": name, "fmt": fmt, "tile": tile, "P": P,
-                                      "kernel_us": us, "gbs": nb / us / 1e3,
+                                      "direct": direct, "kernel_us": us, "gbs": nb / us / 1e3,
                                       "frac": nb / us / 1e3 / peak}), flush=True)
             del A
 

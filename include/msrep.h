@@ -162,6 +162,8 @@ msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
 /* flags for msrep_spmv */
 #define MSREP_COMP_ALL 0x10u  /* low precision: compensate every row      */
 #define MSREP_COMP_NONE 0x20u /* low precision: plain FP32 accumulation   */
+#define MSREP_DIRECT_LOADS 0x40u /* read the nonzeros with direct 256-bit
+                                    loads instead of bulk-copy staging    */
 
 /* y = alpha*A*x + beta*y over the partitions of `part` (Alg. 3 for CSR,
  * Alg. 5 for CSC, Alg. 7 for COO).  `part` must come from the matching
@@ -179,13 +181,19 @@ msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
  * CSC scatters into y with atomic adds (the column merge of Alg. 5), so its
  * rounding order varies from run to run.
  * `workspace` must hold msrep_spmv_workspace_size() bytes, 16-byte
- * aligned.  idx, idx2 and val must be 32-byte aligned (the kernels read
- * them in aligned groups of 8 elements).  Errors: INVALID_ARG, WORKSPACE,
- * CUDA. */
+ * aligned.  idx, idx2 and val must be 32-byte aligned and ptr 16-byte
+ * aligned (the kernels bulk-copy them in aligned segments and read groups
+ * of 8 elements).  Errors: INVALID_ARG, WORKSPACE, CUDA. */
 msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
                         double alpha, const void *x, double beta, void *y,
                         int32_t xy_dtype, unsigned flags, void *workspace,
                         void *stream);
+
+/* Host; syncs `stream`.  Reads and clears the device error word that the
+ * streaming kernels set when a bounded wait on one of their bulk copies
+ * expires (which means the copy engine stalled or an argument was wrong).
+ * *status = 0 and MSREP_OK when no kernel failed, else MSREP_ERR_TIMEOUT. */
+msrep_status msrep_device_status(void *stream, int *status);
 
 /* Profiling aid (no counterpart in the paper).  While set, every msrep_spmv
  * call made on this host thread records `start` (a cudaEvent_t passed as

@@ -51,7 +51,7 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // instantiated in spmv.cu.
 constexpr int kDefaultTile = 256;
 inline bool tile_supported(int t) {
-  return t == 128 || t == 256 || t == 512 || t == 1024;
+  return t == 128 || t == 256 || t == 512;
 }
 
 // ---------------------------------------------------------------------------

@@ -26,36 +26,341 @@ namespace msrep {
 msrep_status check_matrix(const msrep_matrix *A);
 int32_t effective_tile(int32_t tile);
 
+// device error word of the streaming kernels (see msrep_device_status)
+static __device__ int g_kernel_err = 0;
+
+int *kernel_err_ptr() {
+  static int *cached[64] = {nullptr};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  if (!cached[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_kernel_err) != cudaSuccess) return nullptr;
+    cached[dev] = static_cast<int *>(p);
+  }
+  return cached[dev];
+}
+
 // ---------------------------------------------------------------------------
-// single-matrix kernels: a grid of (resident blocks x SMs) walks the tiles
+// single-matrix kernels.  A grid of (resident blocks x SMs) walks the tiles;
+// warp w of block k takes tiles w + 8k, w + 8k + 8*gridDim.x, ...
+//
+// Streaming variant (default): each warp keeps S tiles in flight.  Lane 0
+// issues bulk copies (TMA, cp.async.bulk) of a tile's row_ptr segment and
+// its nonzero arrays into one of the warp's S shared-memory stages; an
+// mbarrier per stage counts the bytes; the warp computes on stage i while
+// stages i+1..i+S-1 are being filled.  The nonzero stream therefore never
+// passes through L1, which is left to the x gathers.
+// Direct variant (MSREP_DIRECT_LOADS): no staging; each lane reads its
+// groups with 256-bit global loads.
 // ---------------------------------------------------------------------------
 
 constexpr int kWarps = 8;  // warps per block; each warp owns whole tiles
 constexpr int kThreads = 32 * kWarps;
 
-template <class Pol, int IPT>
-__global__ void __launch_bounds__(kThreads, 4) csr_tiles(CsrArgs<Pol> a, const int32_t *n_tiles,
-                                                          int64_t nnz) {
-  __shared__ int32_t s_end[kWarps][32 * IPT];
-  const int T = *n_tiles, wid = threadIdx.x >> 5;
-  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps)
-    csr_tile<Pol, IPT>(a, b, s_end[wid], nnz);
+constexpr size_t a128(size_t v) { return (v + 127) & ~size_t(127); }
+
+// shared-memory stage of one tile: up to TILE + 16 entries of each array
+template <class V, int IPT, int NIDX>
+struct StageGeom {
+  static constexpr int CAP = 32 * IPT + 16;
+  static constexpr size_t IDX = a128(4 * CAP);        // one int32 array
+  static constexpr size_t VAL = a128(sizeof(V) * CAP);
+  static constexpr size_t BYTES = NIDX * IDX + VAL;
+  static constexpr int S = BYTES <= 3000 ? 4 : (BYTES <= 4700 ? 3 : 2);
+  static constexpr size_t WARP = S * BYTES + 128;      // + mbarriers and tile records
+  static constexpr size_t BLOCK = kWarps * WARP;
+};
+
+// loads the elements [e0, e1) of arr that the bulk copy could not cover
+template <class T>
+__device__ __forceinline__ void fill_tail(T *dst, const T *arr, const SegCopy &c, int64_t e0,
+                                          int64_t e1) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t e = max(c.cend, e0) + lane; e < e1; e += 32) dst[e - c.base] = arr[e];
 }
 
 template <class Pol, int IPT>
-__global__ void __launch_bounds__(kThreads, 4) coo_tiles(CooArgs<Pol> a) {
+__global__ void __launch_bounds__(kThreads) csr_direct(CsrArgs<Pol> a, const int32_t *n_tiles,
+                                                       int64_t nnz) {
+  __shared__ int32_t s_rp[kWarps][32 * IPT + 8];
+  const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
+    const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
+    const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
+    const int32_t rend = min(r1 + 2, a.m + 1);
+    for (int32_t r = r0 + lane; r < rend; r += 32) s_rp[wid][r - r0] = __ldg(a.row_ptr + r);
+    __syncwarp();
+    csr_tile_compute<Pol>(a, b, r0, k0, r1, k1, s_rp[wid], Seg<int32_t>{a.col_idx, 0},
+                          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{});
+    __syncwarp();
+  }
+}
+
+template <class Pol, int IPT>
+__global__ void __launch_bounds__(kThreads) csr_stream(CsrArgs<Pol> a, const int32_t *n_tiles,
+                                                       int64_t nnz) {
+  using V = typename Pol::V;
+  using G = StageGeom<V, IPT, 2>;
+  constexpr int S = G::S;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char *wb = smem + wid * G::WARP;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(wb + S * G::BYTES);
+  int4 *rec = reinterpret_cast<int4 *>(wb + S * G::BYTES + 64);
+  auto rp_s = [&](int s) { return reinterpret_cast<int32_t *>(wb + s * G::BYTES); };
+  auto col_s = [&](int s) { return reinterpret_cast<int32_t *>(wb + s * G::BYTES + G::IDX); };
+  auto val_s = [&](int s) { return reinterpret_cast<V *>(wb + s * G::BYTES + 2 * G::IDX); };
+  const int T = *n_tiles;
+  const int first = blockIdx.x * kWarps + wid, W = gridDim.x * kWarps;
+  const int64_t mp1 = int64_t(a.m) + 1;
+
+  if (lane == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(bar + s, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  auto plans = [&](int4 c, SegCopy &p, SegCopy &q, SegCopy &v) {
+    p = seg_plan(c.x, min(int64_t(c.z) + 2, mp1), mp1, 4, 4);
+    q = seg_plan(c.y, c.w, nnz, 4, 8);
+    v = seg_plan(c.y, c.w, nnz, sizeof(V), 8);
+  };
+  auto coords = [&](int t) {
+    return make_int4(__ldg(a.tile_row + t), __ldg(a.tile_k + t), __ldg(a.tile_row + t + 1),
+                     __ldg(a.tile_k + t + 1));
+  };
+  // lane 0: stage s <- tile with coordinates c
+  auto issue = [&](int s, int4 c) {
+    SegCopy p, q, v;
+    plans(c, p, q, v);
+    rec[s] = c;
+    mbar_arrive_expect_tx(bar + s, p.bytes + q.bytes + v.bytes);
+    if (p.bytes) bulk_g2s(rp_s(s), a.row_ptr + p.base, p.bytes, bar + s);
+    if (q.bytes) bulk_g2s(col_s(s), a.col_idx + q.base, q.bytes, bar + s);
+    if (v.bytes) bulk_g2s(val_s(s), a.val + v.base, v.bytes, bar + s);
+  };
+  int4 pending = make_int4(0, 0, 0, 0);
+  if (lane == 0) {
+    for (int s = 0; s < S; ++s)
+      if (first + s * W < T) issue(s, coords(first + s * W));
+    if (first + S * W < T) pending = coords(first + S * W);
+  }
+  __syncwarp();
+  int i = 0;
+  bool ok = true;
+  for (; first + i * W < T; ++i) {
+    const int b = first + i * W, s = i % S;
+    if (!mbar_wait(bar + s, (i / S) & 1, a.err)) {
+      ok = false;
+      break;
+    }
+    const int4 c = rec[s];
+    SegCopy p, q, v;
+    plans(c, p, q, v);
+    fill_tail(rp_s(s), a.row_ptr, p, c.x, min(int64_t(c.z) + 2, mp1));
+    const int64_t g_end = min((int64_t(c.w) + 7) & ~int64_t(7), nnz);
+    fill_tail(col_s(s), a.col_idx, q, q.base, g_end);
+    fill_tail(val_s(s), a.val, v, v.base, g_end);
+    __syncwarp();
+    csr_tile_compute<Pol>(a, b, c.x, c.y, c.z, c.w, rp_s(s) + (c.x - p.base),
+                          Seg<int32_t>{col_s(s), q.base}, Seg<V>{val_s(s), v.base}, nnz,
+                          SharedSrc{});
+    __syncwarp();
+    if (lane == 0 && b + S * W < T) {
+      fence_proxy_async();
+      issue(s, pending);
+      if (b + (S + 1) * W < T) pending = coords(b + (S + 1) * W);
+    }
+    __syncwarp();
+  }
+  if (!ok) {
+    // give the copies still in flight a bounded chance to land, then leave
+    for (int j = i + 1; j < i + S && first + j * W < T; ++j) mbar_wait(bar + j % S, (j / S) & 1, a.err);
+  }
+}
+
+template <class Pol, int IPT>
+__global__ void __launch_bounds__(kThreads) coo_direct(CooArgs<Pol> a) {
   const int T = a.np * a.G, wid = threadIdx.x >> 5;
-  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps)
-    coo_tile<Pol, IPT>(a, b);
+  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
+    int32_t k0, k1;
+    coo_tile_range(a, b, k0, k1);
+    coo_tile_compute<Pol>(a, b, k0, k1, Seg<int32_t>{a.row_idx, 0}, Seg<int32_t>{a.col_idx, 0},
+                          Seg<typename Pol::V>{a.val, 0}, GlobalSrc{});
+    __syncwarp();
+  }
 }
 
 template <class Pol, int IPT>
-__global__ void __launch_bounds__(kThreads, 4) csc_tiles(CscArgs<Pol> a, const int32_t *n_tiles,
-                                                          int64_t nnz) {
-  __shared__ int32_t s_end[kWarps][32 * IPT];
-  const int T = *n_tiles, wid = threadIdx.x >> 5;
-  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps)
-    csc_tile<Pol, IPT>(a, b, s_end[wid], nnz);
+__global__ void __launch_bounds__(kThreads) coo_stream(CooArgs<Pol> a) {
+  using V = typename Pol::V;
+  using G = StageGeom<V, IPT, 2>;
+  constexpr int S = G::S;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char *wb = smem + wid * G::WARP;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(wb + S * G::BYTES);
+  int4 *rec = reinterpret_cast<int4 *>(wb + S * G::BYTES + 64);
+  auto row_s = [&](int s) { return reinterpret_cast<int32_t *>(wb + s * G::BYTES); };
+  auto col_s = [&](int s) { return reinterpret_cast<int32_t *>(wb + s * G::BYTES + G::IDX); };
+  auto val_s = [&](int s) { return reinterpret_cast<V *>(wb + s * G::BYTES + 2 * G::IDX); };
+  const int T = a.np * a.G;
+  const int first = blockIdx.x * kWarps + wid, W = gridDim.x * kWarps;
+  const int64_t nnz = a.nnz;
+  if (lane == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(bar + s, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  auto plans = [&](int4 c, SegCopy &r, SegCopy &q, SegCopy &v) {
+    r = seg_plan(c.x, c.y, nnz, 4, 8);
+    q = seg_plan(c.x, c.y, nnz, 4, 8);
+    v = seg_plan(c.x, c.y, nnz, sizeof(V), 8);
+  };
+  auto coords = [&](int t) {
+    int32_t k0, k1;
+    coo_tile_range(a, t, k0, k1);
+    return make_int4(k0, k1, 0, 0);
+  };
+  auto issue = [&](int s, int4 c) {
+    SegCopy r, q, v;
+    plans(c, r, q, v);
+    rec[s] = c;
+    mbar_arrive_expect_tx(bar + s, r.bytes + q.bytes + v.bytes);
+    if (r.bytes) bulk_g2s(row_s(s), a.row_idx + r.base, r.bytes, bar + s);
+    if (q.bytes) bulk_g2s(col_s(s), a.col_idx + q.base, q.bytes, bar + s);
+    if (v.bytes) bulk_g2s(val_s(s), a.val + v.base, v.bytes, bar + s);
+  };
+  int4 pending = make_int4(0, 0, 0, 0);
+  if (lane == 0) {
+    for (int s = 0; s < S; ++s)
+      if (first + s * W < T) issue(s, coords(first + s * W));
+    if (first + S * W < T) pending = coords(first + S * W);
+  }
+  __syncwarp();
+  int i = 0;
+  bool ok = true;
+  for (; first + i * W < T; ++i) {
+    const int b = first + i * W, s = i % S;
+    if (!mbar_wait(bar + s, (i / S) & 1, a.err)) {
+      ok = false;
+      break;
+    }
+    const int4 c = rec[s];
+    SegCopy r, q, v;
+    plans(c, r, q, v);
+    const int64_t g_end = min((int64_t(c.y) + 7) & ~int64_t(7), nnz);
+    fill_tail(row_s(s), a.row_idx, r, r.base, g_end);
+    fill_tail(col_s(s), a.col_idx, q, q.base, g_end);
+    fill_tail(val_s(s), a.val, v, v.base, g_end);
+    __syncwarp();
+    coo_tile_compute<Pol>(a, b, c.x, c.y, Seg<int32_t>{row_s(s), r.base},
+                          Seg<int32_t>{col_s(s), q.base}, Seg<V>{val_s(s), v.base}, SharedSrc{});
+    __syncwarp();
+    if (lane == 0 && b + S * W < T) {
+      fence_proxy_async();
+      issue(s, pending);
+      if (b + (S + 1) * W < T) pending = coords(b + (S + 1) * W);
+    }
+    __syncwarp();
+  }
+  if (!ok)
+    for (int j = i + 1; j < i + S && first + j * W < T; ++j) mbar_wait(bar + j % S, (j / S) & 1, a.err);
+}
+
+template <class Pol, int IPT>
+__global__ void __launch_bounds__(kThreads) csc_direct(CscArgs<Pol> a, const int32_t *n_tiles,
+                                                       int64_t nnz) {
+  __shared__ int32_t s_cp[kWarps][32 * IPT + 8];
+  const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
+    const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
+    const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
+    const int32_t cend = min(c1 + 1, a.n + 1);
+    for (int32_t c = c0 + lane; c < cend; c += 32) s_cp[wid][c - c0] = __ldg(a.col_ptr + c);
+    __syncwarp();
+    csc_tile_compute<Pol>(a, c0, k0, c1, k1, s_cp[wid], Seg<int32_t>{a.row_idx, 0},
+                          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{});
+    __syncwarp();
+  }
+}
+
+template <class Pol, int IPT>
+__global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int32_t *n_tiles,
+                                                       int64_t nnz) {
+  using V = typename Pol::V;
+  using G = StageGeom<V, IPT, 2>;
+  constexpr int S = G::S;
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char *wb = smem + wid * G::WARP;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(wb + S * G::BYTES);
+  int4 *rec = reinterpret_cast<int4 *>(wb + S * G::BYTES + 64);
+  auto cp_s = [&](int s) { return reinterpret_cast<int32_t *>(wb + s * G::BYTES); };
+  auto row_s = [&](int s) { return reinterpret_cast<int32_t *>(wb + s * G::BYTES + G::IDX); };
+  auto val_s = [&](int s) { return reinterpret_cast<V *>(wb + s * G::BYTES + 2 * G::IDX); };
+  const int T = *n_tiles;
+  const int first = blockIdx.x * kWarps + wid, W = gridDim.x * kWarps;
+  const int64_t np1 = int64_t(a.n) + 1;
+  if (lane == 0) {
+    for (int s = 0; s < S; ++s) mbar_init(bar + s, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  auto plans = [&](int4 c, SegCopy &p, SegCopy &r, SegCopy &v) {
+    p = seg_plan(c.x, min(int64_t(c.z) + 1, np1), np1, 4, 4);
+    r = seg_plan(c.y, c.w, nnz, 4, 8);
+    v = seg_plan(c.y, c.w, nnz, sizeof(V), 8);
+  };
+  auto coords = [&](int t) {
+    return make_int4(__ldg(a.tile_row + t), __ldg(a.tile_k + t), __ldg(a.tile_row + t + 1),
+                     __ldg(a.tile_k + t + 1));
+  };
+  auto issue = [&](int s, int4 c) {
+    SegCopy p, r, v;
+    plans(c, p, r, v);
+    rec[s] = c;
+    mbar_arrive_expect_tx(bar + s, p.bytes + r.bytes + v.bytes);
+    if (p.bytes) bulk_g2s(cp_s(s), a.col_ptr + p.base, p.bytes, bar + s);
+    if (r.bytes) bulk_g2s(row_s(s), a.row_idx + r.base, r.bytes, bar + s);
+    if (v.bytes) bulk_g2s(val_s(s), a.val + v.base, v.bytes, bar + s);
+  };
+  int4 pending = make_int4(0, 0, 0, 0);
+  if (lane == 0) {
+    for (int s = 0; s < S; ++s)
+      if (first + s * W < T) issue(s, coords(first + s * W));
+    if (first + S * W < T) pending = coords(first + S * W);
+  }
+  __syncwarp();
+  int i = 0;
+  bool ok = true;
+  for (; first + i * W < T; ++i) {
+    const int b = first + i * W, s = i % S;
+    if (!mbar_wait(bar + s, (i / S) & 1, a.err)) {
+      ok = false;
+      break;
+    }
+    const int4 c = rec[s];
+    SegCopy p, r, v;
+    plans(c, p, r, v);
+    fill_tail(cp_s(s), a.col_ptr, p, c.x, min(int64_t(c.z) + 1, np1));
+    const int64_t g_end = min((int64_t(c.w) + 7) & ~int64_t(7), nnz);
+    fill_tail(row_s(s), a.row_idx, r, r.base, g_end);
+    fill_tail(val_s(s), a.val, v, v.base, g_end);
+    __syncwarp();
+    csc_tile_compute<Pol>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base),
+                          Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base}, nnz,
+                          SharedSrc{});
+    __syncwarp();
+    if (lane == 0 && b + S * W < T) {
+      fence_proxy_async();
+      issue(s, pending);
+      if (b + (S + 1) * W < T) pending = coords(b + (S + 1) * W);
+    }
+    __syncwarp();
+  }
+  if (!ok)
+    for (int j = i + 1; j < i + S && first + j * W < T; ++j) mbar_wait(bar + j % S, (j / S) & 1, a.err);
 }
 
 // ---------------------------------------------------------------------------
@@ -187,6 +492,37 @@ static int64_t tiles_for(const msrep_matrix *A, const msrep_partition *p, int32_
   return plan_layout(n_major, A->nnz, p->np, tile).tmax;
 }
 
+// Launches the streaming kernel (dynamic shared-memory stages) unless the
+// caller asked for direct loads.  Grid: resident blocks x SMs, capped by the
+// number of tiles.
+template <class KS, class KD, class... Args>
+static msrep_status launch_tiles(KS kstream, KD kdirect, size_t stream_smem, bool direct,
+                                 int64_t tiles, cudaStream_t st, Args... args) {
+  static int nb_s = -1, nb_d = -1;
+  int nb;
+  if (direct) {
+    if (nb_d < 0) nb_d = resident_blocks(kdirect, 0);
+    nb = nb_d;
+  } else {
+    if (nb_s < 0) {
+      MSREP_CUDA_TRY(cudaFuncSetAttribute(kstream, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(stream_smem)));
+      nb_s = resident_blocks(kstream, stream_smem);
+    }
+    nb = nb_s;
+  }
+  int64_t grid = std::min<int64_t>(ceil_div(tiles, kWarps), int64_t(nb) * sm_count());
+  if (grid < 1) grid = 1;
+  prof_begin(st);
+  if (direct)
+    kdirect<<<static_cast<int>(grid), kThreads, 0, st>>>(args...);
+  else
+    kstream<<<static_cast<int>(grid), kThreads, stream_smem, st>>>(args...);
+  prof_end(st);
+  MSREP_CUDA_TRY(cudaGetLastError());
+  return MSREP_OK;
+}
+
 template <class Pol, int IPT>
 static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
                             double alpha, const void *x, double beta, void *y,
@@ -210,15 +546,11 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
   a.tail = w.tail;
   a.m = A->m;
   a.comp_mode = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
-  auto kern = csr_tiles<Pol, IPT>;
-  static int nb = -1;
-  if (nb < 0) nb = resident_blocks(kern, 0);
-  int64_t grid = std::min<int64_t>(ceil_div(L.tmax, kWarps), int64_t(nb) * sm_count());
-  if (grid < 1) grid = 1;
-  prof_begin(st);
-  kern<<<static_cast<int>(grid), kThreads, 0, st>>>(a, n_tiles, A->nnz);
-  prof_end(st);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  a.err = kernel_err_ptr();
+  if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
+  MSREP_TRY(launch_tiles(csr_stream<Pol, IPT>, csr_direct<Pol, IPT>,
+                         StageGeom<typename Pol::V, IPT, 2>::BLOCK,
+                         (flags & MSREP_DIRECT_LOADS) != 0, L.tmax, st, a, n_tiles, A->nnz));
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   int64_t fg = std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count());
   fixup_split_rows<typename Pol::X, CsrTileView>
@@ -251,15 +583,12 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
   a.head = w.head;
   a.tail = w.tail;
   a.comp_mode = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
-  auto kern = coo_tiles<Pol, IPT>;
-  static int nb = -1;
-  if (nb < 0) nb = resident_blocks(kern, 0);
+  a.err = kernel_err_ptr();
+  if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   const int64_t T = int64_t(a.np) * a.G;
-  int64_t grid = std::min<int64_t>(ceil_div(T, kWarps), int64_t(nb) * sm_count());
-  prof_begin(st);
-  kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, 0, st>>>(a);
-  prof_end(st);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_tiles(coo_stream<Pol, IPT>, coo_direct<Pol, IPT>,
+                         StageGeom<typename Pol::V, IPT, 2>::BLOCK,
+                         (flags & MSREP_DIRECT_LOADS) != 0, T, st, a));
   CooTileView v{A->idx2, p->start_idx, p->end_idx, A->nnz, a.G, a.np, A->m};
   int64_t fg = std::min<int64_t>(ceil_div(T, 256), 4 * sm_count());
   fixup_split_rows<typename Pol::X, CooTileView>
@@ -272,7 +601,7 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
 template <class Pol, int IPT>
 static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
                             double alpha, const void *x, double beta, void *y,
-                            const Workspace &w, cudaStream_t st) {
+                            unsigned flags, const Workspace &w, cudaStream_t st) {
   const int32_t tile = effective_tile(p->tile);
   PlanLayout L = plan_layout(A->n, A->nnz, p->np, tile);
   const char *plan = static_cast<const char *>(p->plan);
@@ -286,6 +615,8 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   a.tile_k = reinterpret_cast<const int32_t *>(plan + L.off_k);
   const int32_t *n_tiles = reinterpret_cast<const int32_t *>(plan + L.off_toff) + p->np;
   a.n = A->n;
+  a.err = kernel_err_ptr();
+  if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   const int64_t m = A->m;
   const int sg = 4 * sm_count();
   if (kF64) {
@@ -305,14 +636,9 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
     if (m > 0) MSREP_CUDA_TRY(cudaMemsetAsync(w.yacc, 0, sizeof(double) * m, st));
   }
   MSREP_CUDA_TRY(cudaGetLastError());
-  auto kern = csc_tiles<Pol, IPT>;
-  static int nb = -1;
-  if (nb < 0) nb = resident_blocks(kern, 0);
-  int64_t grid = std::min<int64_t>(ceil_div(L.tmax, kWarps), int64_t(nb) * sm_count());
-  prof_begin(st);
-  kern<<<static_cast<int>(std::max<int64_t>(grid, 1)), kThreads, 0, st>>>(a, n_tiles, A->nnz);
-  prof_end(st);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_tiles(csc_stream<Pol, IPT>, csc_direct<Pol, IPT>,
+                         StageGeom<typename Pol::V, IPT, 2>::BLOCK,
+                         (flags & MSREP_DIRECT_LOADS) != 0, L.tmax, st, a, n_tiles, A->nnz));
   if (!kF64 && m > 0) {
     finish_csc_f32<<<sg, 256, 0, st>>>(w.yacc, static_cast<float *>(y), m, alpha, beta);
     MSREP_CUDA_TRY(cudaGetLastError());
@@ -330,13 +656,12 @@ static msrep_status dispatch_tile(const msrep_matrix *A, const msrep_partition *
   switch (A->fmt) {                                                           \
     case MSREP_CSR: return run_csr<Pol, IPT>(A, p, alpha, x, beta, y, flags, w, st); \
     case MSREP_COO: return run_coo<Pol, IPT>(A, p, alpha, x, beta, y, flags, w, st); \
-    default: return run_csc<Pol, IPT>(A, p, alpha, x, beta, y, w, st);        \
+    default: return run_csc<Pol, IPT>(A, p, alpha, x, beta, y, flags, w, st); \
   }
   switch (tile) {
     case 128: MSREP_FMT_CASE(4)
     case 256: MSREP_FMT_CASE(8)
     case 512: MSREP_FMT_CASE(16)
-    case 1024: MSREP_FMT_CASE(32)
   }
 #undef MSREP_FMT_CASE
   return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", tile);
@@ -360,6 +685,20 @@ __global__ void scale_any(void *y, int64_t m, double beta, int is_f64) {
 using namespace msrep;
 
 extern "C" {
+
+msrep_status msrep_device_status(void *stream, int *status) {
+  if (!status) return fail(MSREP_ERR_INVALID_ARG, "status is NULL");
+  cudaStream_t st = as_stream(stream);
+  int zero = 0;
+  MSREP_CUDA_TRY(cudaMemcpyFromSymbolAsync(status, g_kernel_err, sizeof(int), 0,
+                                           cudaMemcpyDeviceToHost, st));
+  MSREP_CUDA_TRY(cudaStreamSynchronize(st));
+  MSREP_CUDA_TRY(cudaMemcpyToSymbolAsync(g_kernel_err, &zero, sizeof(int), 0,
+                                         cudaMemcpyHostToDevice, st));
+  MSREP_CUDA_TRY(cudaStreamSynchronize(st));
+  if (*status) return fail(MSREP_ERR_TIMEOUT, "a kernel gave up on a bounded wait (code %d)", *status);
+  return ok();
+}
 
 msrep_status msrep_profile_events(void *start, void *stop) {
   g_prof_start = reinterpret_cast<cudaEvent_t>(start);
@@ -421,9 +760,9 @@ msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
     // the kernels read the nonzero arrays in aligned groups of 8 elements
     const uintptr_t mis = reinterpret_cast<uintptr_t>(A->idx) | reinterpret_cast<uintptr_t>(A->idx2) |
                           reinterpret_cast<uintptr_t>(A->val);
-    if (mis & (A->val_dtype == MSREP_BF16 ? 15 : 31))
+    if ((mis & (A->val_dtype == MSREP_BF16 ? 15 : 31)) || (reinterpret_cast<uintptr_t>(A->ptr) & 15))
       return fail(MSREP_ERR_INVALID_ARG,
-                  "idx, idx2 and val must be 32-byte aligned (16-byte for bf16-only val)");
+                  "idx, idx2 and val must be 32-byte aligned (16-byte for bf16 val), ptr 16-byte");
   }
   if (!workspace) return fail(MSREP_ERR_WORKSPACE, "workspace is NULL");
   if (reinterpret_cast<uintptr_t>(workspace) & 15)

@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace msrep {
 
@@ -174,30 +175,9 @@ struct LoadT<bf16_t> {
 };
 
 // ---------------------------------------------------------------------------
-// CSR tile
+// group sources: 8 aligned consecutive elements from global memory (direct
+// 256-bit loads) or from a shared-memory stage filled by bulk copies
 // ---------------------------------------------------------------------------
-
-template <class Pol>
-struct CsrArgs {
-  const int32_t *row_ptr;
-  const int32_t *col_idx;
-  const typename Pol::V *val;
-  const typename Pol::X *x;
-  typename Pol::X *y;
-  double alpha, beta;
-  int finish;               // kFinish*
-  const int32_t *tile_row;  // [T+1]
-  const int32_t *tile_k;    // [T+1]
-  double *head, *tail;      // [T] FP64 partials of rows split between tiles
-  int32_t m;
-  unsigned comp_mode;
-};
-
-template <class Pol>
-__device__ __forceinline__ void write_row(const CsrArgs<Pol> &a, int32_t row,
-                                          typename Pol::Acc v) {
-  a.y[row] = Pol::finish(v, a.finish, a.alpha, a.beta, a.y + row);
-}
 
 // One group of 8 nonzeros starting at g8 (a multiple of 8): a single vector
 // load, or element-wise loads for the last group of the array.
@@ -210,6 +190,55 @@ __device__ __forceinline__ void load_group(const T *arr, int64_t g8, int64_t nnz
     for (int u = 0; u < 8; ++u) out[u] = (g8 + u < nnz) ? U(ld_stream(arr + g8 + u)) : U(0);
   }
 }
+
+__device__ __forceinline__ void lds8(const int32_t *p, int32_t (&r)[8]) {
+  const int4 a = reinterpret_cast<const int4 *>(p)[0], b = reinterpret_cast<const int4 *>(p)[1];
+  r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+  r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+}
+__device__ __forceinline__ void lds8(const double *p, double (&v)[8]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const double2 d = reinterpret_cast<const double2 *>(p)[i];
+    v[2 * i] = d.x;
+    v[2 * i + 1] = d.y;
+  }
+}
+__device__ __forceinline__ void lds8(const float *p, float (&v)[8]) {
+  const float4 a = reinterpret_cast<const float4 *>(p)[0], b = reinterpret_cast<const float4 *>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+}
+__device__ __forceinline__ void lds8(const bf16_t *p, float (&v)[8]) {
+  const uint4 w = *reinterpret_cast<const uint4 *>(p);
+  const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[2 * i] = __uint_as_float(ws[i] << 16);
+    v[2 * i + 1] = __uint_as_float(ws[i] & 0xffff0000u);
+  }
+}
+
+// An array as seen by a tile: element e lives at p[e - base].
+template <class T>
+struct Seg {
+  const T *p;
+  int64_t base;
+};
+
+struct GlobalSrc {
+  template <class T, class U>
+  __device__ __forceinline__ void group(Seg<T> s, int64_t g8, int64_t nnz, U (&out)[8]) const {
+    load_group(s.p, g8, nnz, out);
+  }
+};
+
+struct SharedSrc {
+  template <class T, class U>
+  __device__ __forceinline__ void group(Seg<T> s, int64_t g8, int64_t, U (&out)[8]) const {
+    lds8(s.p + (g8 - s.base), out);
+  }
+};
 
 // The lanes of a warp split the 8-aligned groups that cover the tile's
 // nonzeros [k0, k1) evenly (Alg. 2's floor(i*n/P) rule over groups); lane
@@ -228,22 +257,49 @@ __device__ __forceinline__ LaneRange lane_range(int64_t k0, int64_t k1, int lane
   return r;
 }
 
-// One merge-path tile b, processed by one warp.  s_end: the warp's shared
-// buffer of >= 32 * IPT int32 (absolute row ends of the tile's rows).
-template <class Pol, int IPT>
-__device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *s_end,
-                                         int64_t nnz) {
+// ---------------------------------------------------------------------------
+// CSR tile
+// ---------------------------------------------------------------------------
+
+template <class Pol>
+struct CsrArgs {
+  const int32_t *row_ptr;
+  const int32_t *col_idx;
+  const typename Pol::V *val;
+  const typename Pol::X *x;
+  typename Pol::X *y;
+  double alpha, beta;
+  int finish;               // kFinish*
+  const int32_t *tile_row;  // [T+1]
+  const int32_t *tile_k;    // [T+1]
+  double *head, *tail;      // [T] FP64 partials of rows split between tiles
+  int32_t m;
+  unsigned comp_mode;
+  int *err;                 // device error word
+};
+
+template <class Pol>
+__device__ __forceinline__ void write_row(const CsrArgs<Pol> &a, int32_t row,
+                                          typename Pol::Acc v) {
+  a.y[row] = Pol::finish(v, a.finish, a.alpha, a.beta, a.y + row);
+}
+
+// One merge-path tile b = rows [r0, r1] x nonzeros [k0, k1), processed by
+// one warp.  rp[j] = row_ptr[r0 + j] for j = 0..r1-r0, and also j = r1-r0+1
+// when r1 < m; rp must be in shared memory (it is searched).
+template <class Pol, class Src>
+__device__ __forceinline__ void csr_tile_compute(const CsrArgs<Pol> &a, int b, int32_t r0,
+                                                 int32_t k0, int32_t r1, int32_t k1,
+                                                 const int32_t *rp, Seg<int32_t> col,
+                                                 Seg<typename Pol::V> val, int64_t nnz,
+                                                 Src src) {
   using Acc = typename Pol::Acc;
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
-  const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
-  const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
   const int nrows = r1 - r0;
-  const int32_t rs0 = __ldg(a.row_ptr + r0);
-  const bool flag = rs0 < k0;  // the first row started in an earlier tile
-
-  for (int i = lane; i < nrows; i += 32) s_end[i] = __ldg(a.row_ptr + r0 + 1 + i);
-  __syncwarp();
+  const int32_t rs0 = rp[0];
+  const int32_t *s_end = rp + 1;  // s_end[i]: end of row r0 + i
+  const bool flag = rs0 < k0;     // the first row started in an earlier tile
 
   const LaneRange lr = lane_range(k0, k1, lane);
   const int32_t ka = static_cast<int32_t>(lr.ka), kb = static_cast<int32_t>(lr.kb);
@@ -254,7 +310,7 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
 
   // compensation predicate (low-precision form only)
   int32_t re_last = 0;
-  if (Pol::kLow) re_last = (r1 < a.m) ? __ldg(a.row_ptr + r1 + 1) : k1;
+  if (Pol::kLow) re_last = (r1 < a.m) ? rp[nrows + 1] : k1;
   auto row_comp = [&](int rr) -> bool {
     if (!Pol::kLow) return false;
     int64_t st = rr == 0 ? int64_t(rs0) : int64_t(s_end[rr - 1]);
@@ -288,8 +344,8 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
     int32_t c[8];
     LV v[8];
     typename Pol::X xv[8];
-    load_group(a.col_idx, g8, nnz, c);
-    load_group(a.val, g8, nnz, v);
+    src.group(col, g8, nnz, c);
+    src.group(val, g8, nnz, v);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const bool in = g8 + u >= ka && g8 + u < kb;
@@ -327,11 +383,10 @@ __device__ __forceinline__ void csr_tile(const CsrArgs<Pol> &a, int b, int32_t *
         a.head[b] = Pol::to_f64(last);
       else if (k1 > k0)
         a.tail[b] = Pol::to_f64(last);
-    } else if (k1 > __ldg(a.row_ptr + r1)) {
+    } else if (k1 > rp[nrows]) {
       a.tail[b] = Pol::to_f64(last);
     }
   }
-  __syncwarp();  // s_end is reused by the warp's next tile
 }
 
 // ---------------------------------------------------------------------------
@@ -352,6 +407,7 @@ struct CooArgs {
   int64_t nnz;
   double *head, *tail;
   unsigned comp_mode;
+  int *err;
 };
 
 template <class Pol>
@@ -365,15 +421,25 @@ __device__ __forceinline__ void coo_write_empty(const CooArgs<Pol> &a, int32_t r
   a.y[row] = Pol::finish(Pol::zero(), a.finish, a.alpha, a.beta, a.y + row);
 }
 
-template <class Pol, int IPT>
-__device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b) {
+// nonzero range of COO tile b: sub-range g of partition i (Alg. 2's split
+// applied inside the partition)
+template <class Pol>
+__device__ __forceinline__ void coo_tile_range(const CooArgs<Pol> &a, int b, int32_t &k0,
+                                               int32_t &k1) {
+  const int i = b / a.G, g = b % a.G;
+  const int64_t s = __ldg(a.start_idx + i), L = int64_t(__ldg(a.end_idx + i)) - s + 1;
+  k0 = static_cast<int32_t>(s + (int64_t(g) * L) / a.G);
+  k1 = static_cast<int32_t>(s + (int64_t(g + 1) * L) / a.G);
+}
+
+template <class Pol, class Src>
+__device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, int32_t k0,
+                                                 int32_t k1, Seg<int32_t> row,
+                                                 Seg<int32_t> col, Seg<typename Pol::V> val,
+                                                 Src src) {
   using Acc = typename Pol::Acc;
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
-  const int i = b / a.G, g = b % a.G;
-  const int64_t s = a.start_idx[i], L = int64_t(a.end_idx[i]) - s + 1;
-  const int32_t k0 = static_cast<int32_t>(s + (int64_t(g) * L) / a.G);
-  const int32_t k1 = static_cast<int32_t>(s + (int64_t(g + 1) * L) / a.G);
   if (lane == 0) {
     a.head[b] = 0.0;
     a.tail[b] = 0.0;
@@ -416,7 +482,7 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b) {
 
   Acc acc = Pol::zero(), first_acc = Pol::zero();
   bool emitted = false, comp = false;
-  int32_t first_r = 0, cur = -1;
+  int32_t first_r = 0, cur = -1, lane_next = -1;
   auto emit = [&]() {
     if (!emitted) {
       emitted = true;
@@ -432,9 +498,9 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b) {
     int32_t rw[8], c[8];
     LV v[8];
     typename Pol::X xv[8];
-    load_group(a.row_idx, g8, a.nnz, rw);
-    load_group(a.col_idx, g8, a.nnz, c);
-    load_group(a.val, g8, a.nnz, v);
+    src.group(row, g8, a.nnz, rw);
+    src.group(col, g8, a.nnz, c);
+    src.group(val, g8, a.nnz, v);
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const bool in = g8 + u >= ka && g8 + u < kb;
@@ -443,6 +509,8 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b) {
     }
     const int ulo = static_cast<int>(max(ka - g8, int64_t(0)));
     const int uhi = static_cast<int>(min(kb - g8, int64_t(8))) - 1;
+    // row of the nonzero right after the lane's range, if it is in this group
+    if (kb < k1 && kb - g8 >= 0 && kb - g8 < 8) lane_next = rw[kb - g8];
     if (rw[ulo] == cur && rw[uhi] == cur) {
       // the whole group continues the current row
 #pragma unroll
@@ -466,7 +534,8 @@ __device__ __forceinline__ void coo_tile(const CooArgs<Pol> &a, int b) {
   }
   // the lane's last run ends here if the next nonzero starts another row
   if (kb > ka) {
-    const int32_t nxt = kb < k1 ? __ldg(a.row_idx + kb) : next_row;
+    int32_t nxt = next_row;
+    if (kb < k1) nxt = (lane_next >= 0) ? lane_next : __ldg(a.row_idx + kb);
     if (nxt != cur) {
       emit();
       if (kb < k1)
@@ -509,18 +578,19 @@ struct CscArgs {
   bool scaled;   // scale != 1
   const int32_t *tile_row, *tile_k;
   int32_t n;
+  int *err;
 };
 
-template <class Pol, int IPT>
-__device__ __forceinline__ void csc_tile(const CscArgs<Pol> &a, int b, int32_t *s_end,
-                                         int64_t nnz) {
+// cp[j] = col_ptr[c0 + j], j = 0..c1-c0 (shared memory)
+template <class Pol, class Src>
+__device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t c0, int32_t k0,
+                                                 int32_t c1, int32_t k1, const int32_t *cp,
+                                                 Seg<int32_t> row, Seg<typename Pol::V> val,
+                                                 int64_t nnz, Src src) {
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
-  const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
-  const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
   const int ncols = c1 - c0;
-  for (int i = lane; i < ncols; i += 32) s_end[i] = __ldg(a.col_ptr + c0 + 1 + i);
-  __syncwarp();
+  const int32_t *s_end = cp + 1;
   const LaneRange lr = lane_range(k0, k1, lane);
   const int64_t ka = lr.ka, kb = lr.kb;
   if (kb > ka) {
@@ -535,8 +605,8 @@ __device__ __forceinline__ void csc_tile(const CscArgs<Pol> &a, int b, int32_t *
       const int64_t g8 = gg << 3;
       int32_t rw[8];
       LV v[8];
-      load_group(a.row_idx, g8, nnz, rw);
-      load_group(a.val, g8, nnz, v);
+      src.group(row, g8, nnz, rw);
+      src.group(val, g8, nnz, v);
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int64_t e = g8 + u;
@@ -553,7 +623,6 @@ __device__ __forceinline__ void csc_tile(const CscArgs<Pol> &a, int b, int32_t *
       }
     }
   }
-  __syncwarp();
 }
 
 }  // namespace msrep

@@ -25,6 +25,7 @@ MSREP_F64, MSREP_F32, MSREP_BF16 = 0, 1, 2
 MSREP_VALIDATE = 0x1
 MSREP_COMP_ALL = 0x10
 MSREP_COMP_NONE = 0x20
+MSREP_DIRECT_LOADS = 0x40
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_MATRIX", 3: "OOM", 4: "CUDA",
           5: "TIMEOUT", 6: "BUDGET", 7: "NOT_FOUND", 8: "SHUTDOWN",
@@ -77,6 +78,7 @@ SIGNATURES = {
     "msrep_spmv": (ctypes.c_int, [_M, _P, ctypes.c_double, _vp, ctypes.c_double,
                                   _vp, ctypes.c_int32, ctypes.c_uint, _vp, _vp]),
     "msrep_profile_events": (ctypes.c_int, [_vp, _vp]),
+    "msrep_device_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
 }
 
 
@@ -308,3 +310,11 @@ def msrep_profile_events(start=None, stop=None):
     sp = ctypes.c_void_p(start.cuda_event) if start is not None else None
     ep = ctypes.c_void_p(stop.cuda_event) if stop is not None else None
     _check(lib().msrep_profile_events(sp, ep))
+
+
+def msrep_device_status(stream=None) -> int:
+    """Read and clear the device error word (syncs); raises MsrepError with
+    status TIMEOUT if a kernel gave up on a bounded wait."""
+    st = ctypes.c_int()
+    _check(lib().msrep_device_status(_stream(stream), ctypes.byref(st)))
+    return st.value
