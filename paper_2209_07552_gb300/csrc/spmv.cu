@@ -17,6 +17,8 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
+#include <unordered_map>
 
 #include "common.cuh"
 #include "spmv_core.cuh"
@@ -495,22 +497,35 @@ static int64_t tiles_for(const msrep_matrix *A, const msrep_partition *p, int32_
 // Launches the streaming kernel (dynamic shared-memory stages) unless the
 // caller asked for direct loads.  Grid: resident blocks x SMs, capped by the
 // number of tiles.
+// resident blocks per SM of a kernel (keyed by its address), after the
+// dynamic shared-memory opt-in it needs
+template <class K>
+static msrep_status kernel_occupancy(K kernel, size_t smem, int *nb) {
+  static std::mutex mu;
+  static std::unordered_map<const void *, int> cache;
+  std::lock_guard<std::mutex> lk(mu);
+  const void *key = reinterpret_cast<const void *>(kernel);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *nb = it->second;
+    return MSREP_OK;
+  }
+  if (smem > 0)
+    MSREP_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(smem)));
+  *nb = resident_blocks(kernel, smem);
+  cache[key] = *nb;
+  return MSREP_OK;
+}
+
 template <class KS, class KD, class... Args>
 static msrep_status launch_tiles(KS kstream, KD kdirect, size_t stream_smem, bool direct,
                                  int64_t tiles, cudaStream_t st, Args... args) {
-  static int nb_s = -1, nb_d = -1;
-  int nb;
-  if (direct) {
-    if (nb_d < 0) nb_d = resident_blocks(kdirect, 0);
-    nb = nb_d;
-  } else {
-    if (nb_s < 0) {
-      MSREP_CUDA_TRY(cudaFuncSetAttribute(kstream, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          static_cast<int>(stream_smem)));
-      nb_s = resident_blocks(kstream, stream_smem);
-    }
-    nb = nb_s;
-  }
+  int nb = 1;
+  if (direct)
+    MSREP_TRY(kernel_occupancy(kdirect, 0, &nb));
+  else
+    MSREP_TRY(kernel_occupancy(kstream, stream_smem, &nb));
   int64_t grid = std::min<int64_t>(ceil_div(tiles, kWarps), int64_t(nb) * sm_count());
   if (grid < 1) grid = 1;
   prof_begin(st);
