@@ -421,10 +421,11 @@ def run_profile_case(args):
     x = torch.from_numpy(I.vector(a.n, I.SEED_BASE + 1)).to(dev, xt)
     y = torch.empty(a.m, dtype=xt, device=dev)
     ws = M.alloc_workspace(A, part, device=dev)
+    flags = M.MSREP_DIRECT_LOADS if args.direct else 0
     for _ in range(args.reps):
-        M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+        M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": args.profile, "matrix": args.profile_matrix,
+    print(json.dumps({"profile_case": args.profile, "direct": args.direct, "matrix": args.profile_matrix,
                       "dtype": dt, "reps": args.reps, "P": args.P,
                       "y_norm": float(torch.linalg.norm(y.double()))}))
 
@@ -484,6 +485,7 @@ def main():
     ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")
     ap.add_argument("--profile-dtype", choices=["f64", "f32", "bf16"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--direct", action="store_true", help="direct-load kernels (profile case)")
     ap.add_argument("--sweep", action="store_true", help="time every (format, tile, P)")
     args = ap.parse_args()
     if args.sweep:
