@@ -421,7 +421,7 @@ def run_profile_case(args):
     x = torch.from_numpy(I.vector(a.n, I.SEED_BASE + 1)).to(dev, xt)
     y = torch.empty(a.m, dtype=xt, device=dev)
     ws = M.alloc_workspace(A, part, device=dev)
-    flags = M.MSREP_DIRECT_LOADS if args.direct else 0
+    flags = 0 if args.direct else M.MSREP_STREAM_TMA
     for _ in range(args.reps):
         M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
     torch.cuda.synchronize()
@@ -446,9 +446,9 @@ def run_sweep(args):
         for fmt in FORMATS:
             A = M.DeviceMatrix.from_host(a, fmt, "f64", device=dev)
             nb = algorithmic_bytes(fmt, a.m, a.n, a.nnz, 8, 8)
-            for tile, P, direct in [(t, p, d) for t in (128, 256, 512) for p in (148, 148 * 16)
-                                    for d in (False, True)]:
-                    flags = M.MSREP_DIRECT_LOADS if direct else 0
+            for tile, P, direct in [(t, p, d) for t in (256, 512, 1024) for p in (148, 148 * 16)
+                                    for d in (False, True) if d or t <= 512]:
+                    flags = 0 if direct else M.MSREP_STREAM_TMA
                     part = M.DevicePartition(A, P, tile=tile, device=dev)
                     M.msrep_partition(A, part)
                     ws = M.alloc_workspace(A, part, device=dev)

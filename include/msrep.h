@@ -162,8 +162,9 @@ msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
 /* flags for msrep_spmv */
 #define MSREP_COMP_ALL 0x10u  /* low precision: compensate every row      */
 #define MSREP_COMP_NONE 0x20u /* low precision: plain FP32 accumulation   */
-#define MSREP_DIRECT_LOADS 0x40u /* read the nonzeros with direct 256-bit
-                                    loads instead of bulk-copy staging    */
+#define MSREP_STREAM_TMA 0x40u /* stage the nonzeros through shared memory
+                                  with bulk copies (TMA) instead of direct
+                                  256-bit loads; tiles up to 512         */
 
 /* y = alpha*A*x + beta*y over the partitions of `part` (Alg. 3 for CSR,
  * Alg. 5 for CSC, Alg. 7 for COO).  `part` must come from the matching

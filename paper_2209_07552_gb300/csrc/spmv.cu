@@ -47,14 +47,16 @@ int *kernel_err_ptr() {
 // single-matrix kernels.  A grid of (resident blocks x SMs) walks the tiles;
 // warp w of block k takes tiles w + 8k, w + 8k + 8*gridDim.x, ...
 //
-// Streaming variant (default): each warp keeps S tiles in flight.  Lane 0
+// Streaming variant (MSREP_STREAM_TMA): each warp keeps S tiles in flight.  Lane 0
 // issues bulk copies (TMA, cp.async.bulk) of a tile's row_ptr segment and
 // its nonzero arrays into one of the warp's S shared-memory stages; an
 // mbarrier per stage counts the bytes; the warp computes on stage i while
 // stages i+1..i+S-1 are being filled.  The nonzero stream therefore never
 // passes through L1, which is left to the x gathers.
-// Direct variant (MSREP_DIRECT_LOADS): no staging; each lane reads its
-// groups with 256-bit global loads.
+// Direct variant (default): no staging; each lane reads its groups with
+// 256-bit global loads that bypass L1.  On GB300 the SpMV is bound by the
+// FP64 pipe and by L2 sector requests for x, not by DRAM latency, and the
+// direct variant keeps twice as many warps resident and all of L1 for x.
 // ---------------------------------------------------------------------------
 
 constexpr int kWarps = 8;  // warps per block; each warp owns whole tiles
@@ -565,7 +567,7 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   MSREP_TRY(launch_tiles(csr_stream<Pol, IPT>, csr_direct<Pol, IPT>,
                          StageGeom<typename Pol::V, IPT, 2>::BLOCK,
-                         (flags & MSREP_DIRECT_LOADS) != 0, L.tmax, st, a, n_tiles, A->nnz));
+                         (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   int64_t fg = std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count());
   fixup_split_rows<typename Pol::X, CsrTileView>
@@ -603,7 +605,7 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
   const int64_t T = int64_t(a.np) * a.G;
   MSREP_TRY(launch_tiles(coo_stream<Pol, IPT>, coo_direct<Pol, IPT>,
                          StageGeom<typename Pol::V, IPT, 2>::BLOCK,
-                         (flags & MSREP_DIRECT_LOADS) != 0, T, st, a));
+                         (flags & MSREP_STREAM_TMA) == 0, T, st, a));
   CooTileView v{A->idx2, p->start_idx, p->end_idx, A->nnz, a.G, a.np, A->m};
   int64_t fg = std::min<int64_t>(ceil_div(T, 256), 4 * sm_count());
   fixup_split_rows<typename Pol::X, CooTileView>
@@ -653,7 +655,7 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   MSREP_CUDA_TRY(cudaGetLastError());
   MSREP_TRY(launch_tiles(csc_stream<Pol, IPT>, csc_direct<Pol, IPT>,
                          StageGeom<typename Pol::V, IPT, 2>::BLOCK,
-                         (flags & MSREP_DIRECT_LOADS) != 0, L.tmax, st, a, n_tiles, A->nnz));
+                         (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   if (!kF64 && m > 0) {
     finish_csc_f32<<<sg, 256, 0, st>>>(w.yacc, static_cast<float *>(y), m, alpha, beta);
     MSREP_CUDA_TRY(cudaGetLastError());
@@ -674,9 +676,9 @@ static msrep_status dispatch_tile(const msrep_matrix *A, const msrep_partition *
     default: return run_csc<Pol, IPT>(A, p, alpha, x, beta, y, flags, w, st); \
   }
   switch (tile) {
-    case 128: MSREP_FMT_CASE(4)
     case 256: MSREP_FMT_CASE(8)
     case 512: MSREP_FMT_CASE(16)
+    case 1024: MSREP_FMT_CASE(32)
   }
 #undef MSREP_FMT_CASE
   return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", tile);
@@ -744,6 +746,8 @@ msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
     return fail(MSREP_ERR_INVALID_ARG, "bad partition");
   const int32_t tile = effective_tile(part->tile);
   if (!tile_supported(tile)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", part->tile);
+  if ((flags & MSREP_STREAM_TMA) && tile > 512)
+    return fail(MSREP_ERR_INVALID_ARG, "MSREP_STREAM_TMA supports tiles up to 512");
   if ((A->m > 0 && !y) || (A->n > 0 && !x && A->nnz > 0))
     return fail(MSREP_ERR_INVALID_ARG, "x or y is NULL");
   const bool f64 = A->val_dtype == MSREP_F64;

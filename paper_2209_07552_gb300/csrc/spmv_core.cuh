@@ -352,19 +352,16 @@ __device__ __forceinline__ void csr_tile_compute(const CsrArgs<Pol> &a, int b, i
       xv[u] = in ? load_x(a.x, c[u]) : typename Pol::X(0);
       if (!in) v[u] = LV(0);
     }
-    const int32_t gend = static_cast<int32_t>(min(g8 + 8, int64_t(kb)));
-    if (next_end > gend) {
-      // no row ends inside this group: straight multiply-adds
+    // One multiply-add per element on every lane (masked elements add 0),
+    // so the FP64 instructions of a warp never diverge; row ends branch
+    // only around FP64-free code.  Positions outside the lane's range never
+    // finish a row: rows ending at or before ka were finished above, and
+    // r stops at r_end.
 #pragma unroll
-      for (int u = 0; u < 8; ++u) acc = Pol::fma(acc, v[u], xv[u], comp);
-    } else {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (g8 + u >= ka && g8 + u < kb) {
-          acc = Pol::fma(acc, v[u], xv[u], comp);
-          finish_rows(static_cast<int32_t>(g8 + u + 1));
-        }
-      }
+    for (int u = 0; u < 8; ++u) {
+      acc = Pol::fma(acc, v[u], xv[u], comp);
+      const int32_t kk = static_cast<int32_t>(g8 + u + 1);
+      if (next_end <= kk) finish_rows(kk);
     }
   }
 
@@ -511,25 +508,19 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
     const int uhi = static_cast<int>(min(kb - g8, int64_t(8))) - 1;
     // row of the nonzero right after the lane's range, if it is in this group
     if (kb < k1 && kb - g8 >= 0 && kb - g8 < 8) lane_next = rw[kb - g8];
-    if (rw[ulo] == cur && rw[uhi] == cur) {
-      // the whole group continues the current row
+    // row changes branch around FP64-free code; the multiply-adds are the
+    // same instructions on every lane (masked elements add 0)
 #pragma unroll
-      for (int u = 0; u < 8; ++u) acc = Pol::fma(acc, v[u], xv[u], comp);
-    } else {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (u >= ulo && u <= uhi) {
-          if (rw[u] != cur) {
-            if (cur >= 0) {
-              emit();
-              for (int32_t rr = cur + 1; rr < rw[u]; ++rr) coo_write_empty(a, rr);
-            }
-            cur = rw[u];
-            comp = run_comp(cur, g8 + u);
-          }
-          acc = Pol::fma(acc, v[u], xv[u], comp);
+    for (int u = 0; u < 8; ++u) {
+      if (u >= ulo && u <= uhi && rw[u] != cur) {
+        if (cur >= 0) {
+          emit();
+          for (int32_t rr = cur + 1; rr < rw[u]; ++rr) coo_write_empty(a, rr);
         }
+        cur = rw[u];
+        comp = run_comp(cur, g8 + u);
       }
+      acc = Pol::fma(acc, v[u], xv[u], comp);
     }
   }
   // the lane's last run ends here if the next nonzero starts another row

@@ -25,7 +25,7 @@ MSREP_F64, MSREP_F32, MSREP_BF16 = 0, 1, 2
 MSREP_VALIDATE = 0x1
 MSREP_COMP_ALL = 0x10
 MSREP_COMP_NONE = 0x20
-MSREP_DIRECT_LOADS = 0x40
+MSREP_STREAM_TMA = 0x40
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_MATRIX", 3: "OOM", 4: "CUDA",
           5: "TIMEOUT", 6: "BUDGET", 7: "NOT_FOUND", 8: "SHUTDOWN",

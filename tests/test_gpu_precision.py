@@ -84,7 +84,7 @@ def test_compensation_long_rows_exact(fmt):
     a, exact = _cancel_matrix(900, 4)   # rows of 900 > 256 nonzeros
     x = np.ones(a.n)
     for P in (1, 3, 17):                # also split rows across partitions
-        y = gpu_spmv(a, fmt, P, x, val_dtype="f32", tile=128)
+        y = gpu_spmv(a, fmt, P, x, val_dtype="f32", tile=256)
         assert np.array_equal(y, np.full(4, float(exact))), (P, y)
     y_plain = gpu_spmv(a, fmt, 1, x, val_dtype="f32", tile=512,
                        flags=0x20)   # MSREP_COMP_NONE
@@ -97,11 +97,11 @@ def test_compensation_split_short_rows(fmt):
     because they are split."""
     a, exact = _cancel_matrix(60, 40)
     x = np.ones(a.n)
-    y = gpu_spmv(a, fmt, 97, x, val_dtype="f32", tile=128)
+    y = gpu_spmv(a, fmt, 97, x, val_dtype="f32", tile=256)
     assert np.array_equal(y, np.full(40, float(exact)))
 
 
 def test_csc_low_precision_merges_in_fp64():
     a, exact = _cancel_matrix(900, 4)
-    y = gpu_spmv(a, "csc", 5, np.ones(a.n), val_dtype="f32", tile=128)
+    y = gpu_spmv(a, "csc", 5, np.ones(a.n), val_dtype="f32", tile=256)
     assert np.array_equal(y, np.full(4, float(exact)))
