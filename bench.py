@@ -440,14 +440,18 @@ def run_sweep(args):
     dev = torch.device("cuda", 0)
     peak, _ = measured_peaks()
     mats = load_workload()
+    fmts = args.sweep_formats.split(",")
     for name, a in mats.items():
         x = torch.from_numpy(I.vector(a.n, I.SEED_BASE + 1)).to(dev)
         y = torch.empty(a.m, dtype=torch.float64, device=dev)
-        for fmt in FORMATS:
+        for fmt in fmts:
             A = M.DeviceMatrix.from_host(a, fmt, "f64", device=dev)
             nb = algorithmic_bytes(fmt, a.m, a.n, a.nnz, 8, 8)
-            for tile, P, direct in [(t, p, d) for t in (256, 512, 1024) for p in (148, 148 * 16)
-                                    for d in (False, True) if d or t <= 512]:
+            tiles = [int(t) for t in args.sweep_tiles.split(",")]
+            Ps = [int(q) for q in args.sweep_P.split(",")]
+            modes = [True] if args.sweep_direct_only else [False, True]
+            for tile, P, direct in [(t, p, d) for t in tiles for p in Ps
+                                    for d in modes if d or t <= 512]:
                     flags = 0 if direct else M.MSREP_STREAM_TMA
                     part = M.DevicePartition(A, P, tile=tile, device=dev)
                     M.msrep_partition(A, part)
@@ -487,6 +491,10 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--direct", action="store_true", help="direct-load kernels (profile case)")
     ap.add_argument("--sweep", action="store_true", help="time every (format, tile, P)")
+    ap.add_argument("--sweep-formats", default="csr,csc,coo")
+    ap.add_argument("--sweep-tiles", default="256,512,1024")
+    ap.add_argument("--sweep-P", default="148,2368")
+    ap.add_argument("--sweep-direct-only", action="store_true")
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args)

@@ -24,7 +24,7 @@ LIB = os.path.join(PKG, "libmsrep.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
-              "-I" + INCLUDE, "-I" + CSRC]
+              "-I" + INCLUDE, "-I" + CSRC] + os.environ.get("MSREP_NVCC_FLAGS", "").split()
 
 
 def _nvcc() -> str:

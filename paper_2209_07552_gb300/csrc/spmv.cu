@@ -59,6 +59,9 @@ int *kernel_err_ptr() {
 // direct variant keeps twice as many warps resident and all of L1 for x.
 // ---------------------------------------------------------------------------
 
+#ifndef MSREP_MINB
+#define MSREP_MINB 1  // minimum resident blocks per SM asked of the register allocator
+#endif
 constexpr int kWarps = 8;  // warps per block; each warp owns whole tiles
 constexpr int kThreads = 32 * kWarps;
 
@@ -85,7 +88,7 @@ __device__ __forceinline__ void fill_tail(T *dst, const T *arr, const SegCopy &c
 }
 
 template <class Pol, int IPT>
-__global__ void __launch_bounds__(kThreads) csr_direct(CsrArgs<Pol> a, const int32_t *n_tiles,
+__global__ void __launch_bounds__(kThreads, MSREP_MINB) csr_direct(CsrArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
   __shared__ int32_t s_rp[kWarps][32 * IPT + 8];
   const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -184,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) csr_stream(CsrArgs<Pol> a, const int
 }
 
 template <class Pol, int IPT>
-__global__ void __launch_bounds__(kThreads) coo_direct(CooArgs<Pol> a) {
+__global__ void __launch_bounds__(kThreads, MSREP_MINB) coo_direct(CooArgs<Pol> a) {
   const int T = a.np * a.G, wid = threadIdx.x >> 5;
   for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
     int32_t k0, k1;
@@ -273,7 +276,7 @@ __global__ void __launch_bounds__(kThreads) coo_stream(CooArgs<Pol> a) {
 }
 
 template <class Pol, int IPT>
-__global__ void __launch_bounds__(kThreads) csc_direct(CscArgs<Pol> a, const int32_t *n_tiles,
+__global__ void __launch_bounds__(kThreads, MSREP_MINB) csc_direct(CscArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
   __shared__ int32_t s_cp[kWarps][32 * IPT + 8];
   const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;

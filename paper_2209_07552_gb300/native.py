@@ -16,7 +16,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libmsrep.so")
+LIB_PATH = os.environ.get("MSREP_LIB_PATH") or os.path.join(_HERE, "libmsrep.so")
 _LOCK = threading.Lock()
 _LIB = None
 
