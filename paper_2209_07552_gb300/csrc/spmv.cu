@@ -278,15 +278,21 @@ __global__ void __launch_bounds__(kThreads) coo_stream(CooArgs<Pol> a) {
 template <class Pol, int IPT>
 __global__ void __launch_bounds__(kThreads, MSREP_MINB) csc_direct(CscArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
-  __shared__ int32_t s_cp[kWarps][32 * IPT + 8];
+  // dynamic shared memory: per warp, x values then column pointers
+  extern __shared__ __align__(16) unsigned char dsm[];
+  constexpr int CAP = 32 * IPT + 8;
   const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double *s_x = reinterpret_cast<double *>(dsm) + wid * CAP;
+  int32_t *s_cp = reinterpret_cast<int32_t *>(reinterpret_cast<double *>(dsm) + kWarps * CAP) +
+                  wid * CAP;
   for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
     const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
     const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
     const int32_t cend = min(c1 + 1, a.n + 1);
-    for (int32_t c = c0 + lane; c < cend; c += 32) s_cp[wid][c - c0] = __ldg(a.col_ptr + c);
+    for (int32_t c = c0 + lane; c < cend; c += 32) s_cp[c - c0] = __ldg(a.col_ptr + c);
+    csc_stage_x(a, c0, c1, s_x);
     __syncwarp();
-    csc_tile_compute<Pol>(a, c0, k0, c1, k1, s_cp[wid], Seg<int32_t>{a.row_idx, 0},
+    csc_tile_compute<Pol>(a, c0, k0, c1, k1, s_cp, s_x, Seg<int32_t>{a.row_idx, 0},
                           Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{});
     __syncwarp();
   }
@@ -300,6 +306,7 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
   constexpr int S = G::S;
   extern __shared__ __align__(128) unsigned char smem[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double *xs = reinterpret_cast<double *>(smem + kWarps * G::WARP) + wid * (32 * IPT + 8);
   unsigned char *wb = smem + wid * G::WARP;
   uint64_t *bar = reinterpret_cast<uint64_t *>(wb + S * G::BYTES);
   int4 *rec = reinterpret_cast<int4 *>(wb + S * G::BYTES + 64);
@@ -354,8 +361,9 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
     const int64_t g_end = min((int64_t(c.w) + 7) & ~int64_t(7), nnz);
     fill_tail(row_s(s), a.row_idx, r, r.base, g_end);
     fill_tail(val_s(s), a.val, v, v.base, g_end);
+    csc_stage_x(a, c.x, c.z, xs);
     __syncwarp();
-    csc_tile_compute<Pol>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base),
+    csc_tile_compute<Pol>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xs,
                           Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base}, nnz,
                           SharedSrc{});
     __syncwarp();
@@ -524,18 +532,18 @@ static msrep_status kernel_occupancy(K kernel, size_t smem, int *nb) {
 }
 
 template <class KS, class KD, class... Args>
-static msrep_status launch_tiles(KS kstream, KD kdirect, size_t stream_smem, bool direct,
-                                 int64_t tiles, cudaStream_t st, Args... args) {
+static msrep_status launch_tiles(KS kstream, KD kdirect, size_t stream_smem, size_t direct_smem,
+                                 bool direct, int64_t tiles, cudaStream_t st, Args... args) {
   int nb = 1;
   if (direct)
-    MSREP_TRY(kernel_occupancy(kdirect, 0, &nb));
+    MSREP_TRY(kernel_occupancy(kdirect, direct_smem, &nb));
   else
     MSREP_TRY(kernel_occupancy(kstream, stream_smem, &nb));
   int64_t grid = std::min<int64_t>(ceil_div(tiles, kWarps), int64_t(nb) * sm_count());
   if (grid < 1) grid = 1;
   prof_begin(st);
   if (direct)
-    kdirect<<<static_cast<int>(grid), kThreads, 0, st>>>(args...);
+    kdirect<<<static_cast<int>(grid), kThreads, direct_smem, st>>>(args...);
   else
     kstream<<<static_cast<int>(grid), kThreads, stream_smem, st>>>(args...);
   prof_end(st);
@@ -569,7 +577,7 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
   a.err = kernel_err_ptr();
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   MSREP_TRY(launch_tiles(csr_stream<Pol, IPT>, csr_direct<Pol, IPT>,
-                         StageGeom<typename Pol::V, IPT, 2>::BLOCK,
+                         StageGeom<typename Pol::V, IPT, 2>::BLOCK, 0,
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   int64_t fg = std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count());
@@ -607,7 +615,7 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   const int64_t T = int64_t(a.np) * a.G;
   MSREP_TRY(launch_tiles(coo_stream<Pol, IPT>, coo_direct<Pol, IPT>,
-                         StageGeom<typename Pol::V, IPT, 2>::BLOCK,
+                         StageGeom<typename Pol::V, IPT, 2>::BLOCK, 0,
                          (flags & MSREP_STREAM_TMA) == 0, T, st, a));
   CooTileView v{A->idx2, p->start_idx, p->end_idx, A->nnz, a.G, a.np, A->m};
   int64_t fg = std::min<int64_t>(ceil_div(T, 256), 4 * sm_count());
@@ -657,7 +665,9 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   }
   MSREP_CUDA_TRY(cudaGetLastError());
   MSREP_TRY(launch_tiles(csc_stream<Pol, IPT>, csc_direct<Pol, IPT>,
-                         StageGeom<typename Pol::V, IPT, 2>::BLOCK,
+                         StageGeom<typename Pol::V, IPT, 2>::BLOCK +
+                             sizeof(double) * kWarps * (32 * IPT + 8),
+                         (sizeof(double) + sizeof(int32_t)) * kWarps * (32 * IPT + 8),
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   if (!kF64 && m > 0) {
     finish_csc_f32<<<sg, 256, 0, st>>>(w.yacc, static_cast<float *>(y), m, alpha, beta);

@@ -133,16 +133,18 @@ __device__ __forceinline__ typename Pol::Acc warp_seg_scan(bool flag, typename P
   using Acc = typename Pol::Acc;
   const int lane = threadIdx.x & 31;
   Acc inc = v;
-  if (!__all_sync(0xffffffffu, flag)) {
-    int f = flag;
+  int f = flag;
+  // Hillis-Steele doubling, stopped as soon as every lane's sum reaches back
+  // to a lane that finished a row (usually after one or two steps); each
+  // step costs one warp-wide FP64 add.
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      Acc u = Pol::shfl_up(inc, o);
-      int fu = __shfl_up_sync(0xffffffffu, f, o);
-      if (lane >= o) {
-        if (!f) inc = Pol::combine(u, inc);
-        f |= fu;
-      }
+  for (int o = 1; o < 32; o <<= 1) {
+    if (__all_sync(0xffffffffu, f || lane < o)) break;
+    Acc u = Pol::shfl_up(inc, o);
+    int fu = __shfl_up_sync(0xffffffffu, f, o);
+    if (lane >= o) {
+      if (!f) inc = Pol::combine(u, inc);
+      f |= fu;
     }
   }
   Acc ex = Pol::shfl_up(inc, 1);
@@ -572,47 +574,52 @@ struct CscArgs {
   int *err;
 };
 
-// cp[j] = col_ptr[c0 + j], j = 0..c1-c0 (shared memory)
+// cp[j] = col_ptr[c0 + j], j = 0..c1-c0, and xs[j] = scale * x[c0 + j] for
+// the columns that hold nonzeros of the tile, both in shared memory.
 template <class Pol, class Src>
 __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t c0, int32_t k0,
                                                  int32_t c1, int32_t k1, const int32_t *cp,
-                                                 Seg<int32_t> row, Seg<typename Pol::V> val,
-                                                 int64_t nnz, Src src) {
+                                                 const double *xs, Seg<int32_t> row,
+                                                 Seg<typename Pol::V> val, int64_t nnz, Src src) {
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
   const int ncols = c1 - c0;
   const int32_t *s_end = cp + 1;
   const LaneRange lr = lane_range(k0, k1, lane);
   const int64_t ka = lr.ka, kb = lr.kb;
-  if (kb > ka) {
-    int c = upper_bound_smem(s_end, ncols, static_cast<int32_t>(ka));
-    auto colx = [&](int cc) -> double {
-      double xv = double(load_x(a.x, c0 + cc));
-      return a.scaled ? __dmul_rn(xv, a.scale) : xv;
-    };
-    double xc = colx(c);
-    int32_t cend = c < ncols ? s_end[c] : INT32_MAX;
-    for (int64_t gg = lr.glo; gg < lr.ghi; ++gg) {
-      const int64_t g8 = gg << 3;
-      int32_t rw[8];
-      LV v[8];
-      src.group(row, g8, nnz, rw);
-      src.group(val, g8, nnz, v);
+  int c = upper_bound_smem(s_end, ncols, static_cast<int32_t>(ka));
+  int32_t cend = c < ncols ? s_end[c] : INT32_MAX;
+  for (int64_t gg = lr.glo; gg < lr.ghi; ++gg) {
+    const int64_t g8 = gg << 3;
+    int32_t rw[8];
+    LV v[8];
+    src.group(row, g8, nnz, rw);
+    src.group(val, g8, nnz, v);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int64_t e = g8 + u;
-        if (e >= ka && e < kb) {
-          if (cend <= e) {
-            do {
-              ++c;
-              cend = c < ncols ? s_end[c] : INT32_MAX;
-            } while (cend <= e);
-            xc = colx(c);
-          }
-          atomicAdd(a.yacc + rw[u], __dmul_rn(double(v[u]), xc));
-        }
+    for (int u = 0; u < 8; ++u) {
+      const int64_t e = g8 + u;
+      const bool in = e >= ka && e < kb;
+      while (in && cend <= e) {  // integer-only column advance
+        ++c;
+        cend = c < ncols ? s_end[c] : INT32_MAX;
       }
+      const double prod = __dmul_rn(double(v[u]), in ? xs[c] : 0.0);
+      if (in) atomicAdd(a.yacc + rw[u], prod);
     }
+  }
+}
+
+// Stages the tile's column pointers and (scaled) x values in shared memory:
+// cp[j] = col_ptr[c0 + j] for j = 0..min(c1 + 1, n + 1) - c0 - 1 and
+// xs[j] = scale * x[c0 + j] for columns c0 + j < n.
+template <class Pol>
+__device__ __forceinline__ void csc_stage_x(const CscArgs<Pol> &a, int32_t c0, int32_t c1,
+                                            double *xs) {
+  const int lane = threadIdx.x & 31;
+  const int32_t xe = min(c1 + 1, a.n);
+  for (int32_t c = c0 + lane; c < xe; c += 32) {
+    const double xv = double(load_x(a.x, c));
+    xs[c - c0] = a.scaled ? __dmul_rn(xv, a.scale) : xv;
   }
 }
 
