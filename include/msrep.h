@@ -190,6 +190,76 @@ msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
                         int32_t xy_dtype, unsigned flags, void *workspace,
                         void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Batched form: many independent CSR matrices in one persistent launch.  */
+/* No counterpart in the paper beyond its partitions (Sec. 3.2); the      */
+/* per-matrix work is Alg. 3 exactly as msrep_spmv runs it.               */
+/* ---------------------------------------------------------------------- */
+
+/* Tuning table: a matrix falls in bucket floor(log2(max(nnz, 1))); bucket
+ * b uses thread-block tile tile[b] (0 = default) and np = ceil(nnz /
+ * part_nnz[b]) partitions (part_nnz[b] = 0: one partition). */
+#define MSREP_TUNE_BUCKETS 32
+typedef struct {
+  int32_t tile[MSREP_TUNE_BUCKETS];
+  int64_t part_nnz[MSREP_TUNE_BUCKETS];
+} msrep_tune_table;
+
+/* A prepared batch (filled by msrep_batch_prepare; host memory, owned by
+ * the caller).  `dev` is the caller's device buffer that holds every
+ * matrix's partition and tile plan plus the batch's tile directory. */
+typedef struct {
+  int32_t count;       /* number of matrices                       */
+  int32_t val_dtype;   /* common value type of the batch           */
+  int64_t total_tiles; /* tiles over all matrices                  */
+  int64_t ws_bytes;    /* workspace msrep_spmv_batched needs       */
+  void *dev;
+  int64_t dev_bytes;
+  int64_t items_off;   /* byte offsets of the directory in dev     */
+  int64_t toff_off;
+} msrep_batch;
+
+/* Host only: the library's default table (tile 1024, one partition). */
+msrep_status msrep_tune_default(msrep_tune_table *tune);
+
+/* Host only: device bytes msrep_batch_prepare needs for As[0..count). */
+msrep_status msrep_batch_plan_size(int32_t count, const msrep_matrix *As,
+                                   const msrep_tune_table *tune,
+                                   int64_t *dev_bytes);
+
+/* Partitions every matrix (Alg. 2, np and tile from `tune`, NULL = the
+ * default table), builds its tile plan and the batch's tile directory in
+ * `dev`, and fills *out.  As is a host array of CSR matrices (device
+ * arrays) sharing one val_dtype.  Syncs `stream`. */
+msrep_status msrep_batch_prepare(int32_t count, const msrep_matrix *As,
+                                 const msrep_tune_table *tune, void *dev,
+                                 int64_t dev_bytes, msrep_batch *out,
+                                 void *stream);
+
+/* y_j = alpha*A_j*x_j + beta*y_j for every matrix of the batch, as one
+ * persistent kernel over all tiles plus one fix-up kernel (no host work,
+ * no allocation: safe to capture in a CUDA graph).  xs, ys: DEVICE arrays
+ * of `count` device pointers (F64 x/y for an F64 batch, else F32).  Each
+ * y_j equals bit for bit what msrep_spmv gives for A_j with the same np
+ * and tile.  workspace: B->ws_bytes, 16-byte aligned. */
+msrep_status msrep_spmv_batched(const msrep_batch *B, const void *const *xs,
+                                void *const *ys, double alpha, double beta,
+                                unsigned flags, void *workspace, void *stream);
+
+/* Host only: scratch bytes msrep_autotune needs for As. */
+msrep_status msrep_autotune_scratch_size(int32_t count, const msrep_matrix *As,
+                                         int64_t *bytes);
+
+/* Project-written autotuner: for every size bucket present in As, times
+ * msrep_spmv on up to three of the bucket's largest matrices for each
+ * candidate (tile 256/512/1024 x part_nnz 0/2^14/2^18) with CUDA events and
+ * keeps the fastest; absent buckets keep the default.  xs/ys: HOST arrays
+ * of device pointers (ys are overwritten).  Syncs `stream`. */
+msrep_status msrep_autotune(int32_t count, const msrep_matrix *As,
+                            const void *const *xs, void *const *ys,
+                            void *scratch, int64_t scratch_bytes,
+                            msrep_tune_table *out, void *stream);
+
 /* Host; syncs `stream`.  Reads and clears the device error word that the
  * streaming kernels set when a bounded wait on one of their bulk copies
  * expires (which means the copy engine stalled or an argument was wrong).

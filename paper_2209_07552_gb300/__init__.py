@@ -12,7 +12,9 @@ from .native import (MSREP_BF16, MSREP_COMP_ALL, MSREP_COMP_NONE, MSREP_COO,
                      msrep_partition, msrep_partition_coo, msrep_partition_csc,
                      msrep_partition_csr, msrep_partition_local_bound,
                      msrep_plan_size, msrep_spmv, msrep_spmv_workspace_size,
-                     msrep_tile_supported, msrep_version)
+                     msrep_tile_supported, msrep_version, DeviceBatch,
+                     msrep_autotune, msrep_batch_plan_size, msrep_spmv_batched,
+                     msrep_tune_default)
 
 __all__ = [n for n in dir() if n.startswith(("msrep_", "MSREP_"))] + [
-    "DeviceMatrix", "DevicePartition", "MsrepError", "alloc_workspace"]
+    "DeviceMatrix", "DevicePartition", "DeviceBatch", "MsrepError", "alloc_workspace"]

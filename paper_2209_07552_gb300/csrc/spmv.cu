@@ -382,62 +382,13 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
 // fix-up: rows split between tiles, merged in tile (= partition) order
 // ---------------------------------------------------------------------------
 
-struct CsrTileView {
-  const int32_t *tile_row, *tile_k, *row_ptr, *n_tiles;
-  __device__ int count() const { return *n_tiles; }
-  __device__ void row_flag(int b, int32_t &r, bool &f) const {
-    r = __ldg(tile_row + b);
-    f = __ldg(row_ptr + r) < __ldg(tile_k + b);
-  }
-};
-
-struct CooTileView {
-  const int32_t *row_idx, *start_idx, *end_idx;
-  int64_t nnz;
-  int32_t G, np, m;
-  __device__ int count() const { return np * G; }
-  __device__ int32_t k0(int b) const {
-    int i = b / G, g = b % G;
-    int64_t s = start_idx[i], L = int64_t(end_idx[i]) - s + 1;
-    return static_cast<int32_t>(s + (int64_t(g) * L) / G);
-  }
-  __device__ void row_flag(int b, int32_t &r, bool &f) const {
-    int32_t k = k0(b);
-    if (k >= nnz) {
-      r = m;
-      f = false;
-      return;
-    }
-    r = __ldg(row_idx + k);
-    f = k > 0 && __ldg(row_idx + k - 1) == r;
-  }
-};
-
 template <class X, class View>
 __global__ void fixup_split_rows(View v, const double *head, const double *tail,
                                  X *y, double alpha, double beta) {
   const int T = v.count();
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < T;
-       b += gridDim.x * blockDim.x) {
-    int32_t r;
-    bool f;
-    v.row_flag(b, r, f);
-    if (!f || b == 0) continue;
-    int32_t rp;
-    bool fp;
-    v.row_flag(b - 1, rp, fp);
-    if (fp && rp == r) continue;  // not the first flagged tile of the run
-    double s = tail[b - 1];
-    for (int j = b; j < T; ++j) {
-      int32_t rj;
-      bool fj;
-      v.row_flag(j, rj, fj);
-      if (!fj || rj != r) break;
-      s += head[j];
-    }
-    double yo = beta == 0.0 ? 0.0 : double(y[r]);
-    y[r] = static_cast<X>(beta == 0.0 ? alpha * s : alpha * s + beta * yo);
-  }
+       b += gridDim.x * blockDim.x)
+    fixup_tile(v, T, b, head, tail, y, alpha, beta);
 }
 
 __global__ void scale_f64(double *y, int64_t m, double beta) {

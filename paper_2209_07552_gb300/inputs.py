@@ -314,23 +314,53 @@ def batched_sizes(count: int = 512, seed: int = SEED_BASE + 3,
 
 def geometric_matrix(m: int, mu: float, seed: int, dtype=np.float32) -> CSR:
     """Square m x m matrix; row lengths ~ Geometric(p = 1/mu) on {1, 2, ...}
-    clamped to m; columns distinct and sorted within a row.  Distinct
-    columns come from sorting L draws from U{0..m-L} and adding 0..L-1 (a
-    one-to-one map from sorted draws to L-subsets).  Values ~ U(-1, 1)."""
+    clamped to m; columns distinct and sorted within a row.  A row of
+    length L takes the order statistics of L uniforms on [0, 1) (normalised
+    cumulative sums of L+1 exponential gaps), maps them to draws in
+    {0..m-L} and adds 0..L-1, which gives L distinct sorted columns.
+    Values ~ U(-1, 1)."""
     g = rng(seed, _S_COLS)
     lens = np.minimum(g.geometric(1.0 / mu, m), m).astype(np.int64)
     ptr = row_ptr_from_counts(lens)
     nnz = int(ptr[-1])
+    starts = ptr[:-1].astype(np.int64)
+    # L+1 gaps per row; cumulative sums inside each row, normalised by the
+    # row's total, are L sorted uniforms
+    gaps = g.standard_exponential(nnz + m)
+    cs = np.cumsum(gaps)
+    gap_starts = starts + np.arange(m, dtype=np.int64)        # row r's gaps start here
+    before = np.where(gap_starts > 0, cs[np.maximum(gap_starts - 1, 0)], 0.0)
+    row_total = cs[gap_starts + lens] - before                 # sum of the row's L+1 gaps
     rows = np.repeat(np.arange(m, dtype=np.int64), lens)
+    within = np.arange(nnz, dtype=np.int64) - starts[rows]
+    u = (cs[gap_starts[rows] + within] - before[rows]) / row_total[rows]
     span = (m - lens + 1)[rows]
-    draw = np.floor(g.random(nnz) * span).astype(np.int64)
-    order = np.lexsort((draw, rows))
-    draw = draw[order]
-    within = np.arange(nnz, dtype=np.int64) - ptr[:-1].astype(np.int64)[rows]
+    draw = np.minimum(np.floor(u * span).astype(np.int64), span - 1)
     cols = (draw + within).astype(np.int32)
     val = rng(seed, _S_VALS).uniform(-1.0, 1.0, nnz).astype(dtype)
     return CSR(m, m, ptr, cols, val, meta={"kind": "geometric", "mu": mu,
                                             "seed": seed})
+
+
+def _batched_one(job):
+    i, m, mu, seed, dtype = job
+    s = seed * 1000 + i
+    a = geometric_matrix(int(m), float(mu), s, dtype)
+    return a, vector(int(m), s).astype(dtype)
+
+
+def batched_set_parallel(count: int = 512, seed: int = SEED_BASE + 3, dtype=np.float32,
+                         workers: int = 0, **size_kw):
+    """batched_set computed by a pool of spawned worker processes (same
+    result, element for element)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    ms, mus = batched_sizes(count, seed, **size_kw)
+    jobs = [(i, int(m), float(mu), seed, dtype) for i, (m, mu) in enumerate(zip(ms, mus))]
+    workers = workers or min(16, os.cpu_count() or 1)
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        out = list(ex.map(_batched_one, jobs, chunksize=4))
+    return [a for a, _ in out], [x for _, x in out]
 
 
 def batched_set(count: int = 512, seed: int = SEED_BASE + 3, dtype=np.float32,

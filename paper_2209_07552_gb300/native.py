@@ -57,6 +57,17 @@ class c_msrep_partition(ctypes.Structure):
                 ("plan_bytes", ctypes.c_int64)]
 
 
+class c_msrep_tune_table(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32 * 32), ("part_nnz", ctypes.c_int64 * 32)]
+
+
+class c_msrep_batch(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("val_dtype", ctypes.c_int32),
+                ("total_tiles", ctypes.c_int64), ("ws_bytes", ctypes.c_int64),
+                ("dev", ctypes.c_void_p), ("dev_bytes", ctypes.c_int64),
+                ("items_off", ctypes.c_int64), ("toff_off", ctypes.c_int64)]
+
+
 _M = ctypes.POINTER(c_msrep_matrix)
 _P = ctypes.POINTER(c_msrep_partition)
 _vp = ctypes.c_void_p
@@ -79,6 +90,22 @@ SIGNATURES = {
                                   _vp, ctypes.c_int32, ctypes.c_uint, _vp, _vp]),
     "msrep_profile_events": (ctypes.c_int, [_vp, _vp]),
     "msrep_device_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "msrep_tune_default": (ctypes.c_int, [ctypes.POINTER(c_msrep_tune_table)]),
+    "msrep_batch_plan_size": (ctypes.c_int, [ctypes.c_int32, _M,
+                                             ctypes.POINTER(c_msrep_tune_table),
+                                             ctypes.POINTER(ctypes.c_int64)]),
+    "msrep_batch_prepare": (ctypes.c_int, [ctypes.c_int32, _M,
+                                           ctypes.POINTER(c_msrep_tune_table), _vp,
+                                           ctypes.c_int64, ctypes.POINTER(c_msrep_batch),
+                                           _vp]),
+    "msrep_spmv_batched": (ctypes.c_int, [ctypes.POINTER(c_msrep_batch), _vp, _vp,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_uint,
+                                          _vp, _vp]),
+    "msrep_autotune_scratch_size": (ctypes.c_int, [ctypes.c_int32, _M,
+                                                   ctypes.POINTER(ctypes.c_int64)]),
+    "msrep_autotune": (ctypes.c_int, [ctypes.c_int32, _M, ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_void_p), _vp, ctypes.c_int64,
+                                      ctypes.POINTER(c_msrep_tune_table), _vp]),
 }
 
 
@@ -318,3 +345,82 @@ def msrep_device_status(stream=None) -> int:
     st = ctypes.c_int()
     _check(lib().msrep_device_status(_stream(stream), ctypes.byref(st)))
     return st.value
+
+
+# --------------------------------------------------------------------------
+# batched form
+# --------------------------------------------------------------------------
+
+def msrep_tune_default() -> c_msrep_tune_table:
+    t = c_msrep_tune_table()
+    _check(lib().msrep_tune_default(ctypes.byref(t)))
+    return t
+
+
+def _mat_array(mats):
+    arr = (c_msrep_matrix * len(mats))()
+    for i, A in enumerate(mats):
+        arr[i] = A.c
+    return arr
+
+
+def msrep_batch_plan_size(mats, tune=None) -> int:
+    out = ctypes.c_int64()
+    arr = _mat_array(mats)
+    _check(lib().msrep_batch_plan_size(len(mats), arr,
+                                       ctypes.byref(tune) if tune is not None else None,
+                                       ctypes.byref(out)))
+    return out.value
+
+
+class DeviceBatch:
+    """A prepared batch of CSR DeviceMatrix objects (msrep_batch_prepare),
+    with device pointer arrays for x and y and the workspace."""
+
+    def __init__(self, mats, xs, ys, tune=None, device="cuda", stream=None):
+        import torch
+        self.mats, self.xs, self.ys = list(mats), list(xs), list(ys)
+        self.tune = tune
+        arr = _mat_array(self.mats)
+        self._arr = arr
+        need = msrep_batch_plan_size(self.mats, tune)
+        self.dev = torch.empty(max(need, 256), dtype=torch.uint8, device=device)
+        self.c = c_msrep_batch()
+        _check(lib().msrep_batch_prepare(
+            len(self.mats), arr, ctypes.byref(tune) if tune is not None else None,
+            _ptr(self.dev), need, ctypes.byref(self.c), _stream(stream)))
+        self.ws = torch.empty(max(int(self.c.ws_bytes), 256), dtype=torch.uint8,
+                              device=device)
+        self.xptr = torch.tensor([t.data_ptr() for t in self.xs], dtype=torch.int64,
+                                 device=device)
+        self.yptr = torch.tensor([t.data_ptr() for t in self.ys], dtype=torch.int64,
+                                 device=device)
+
+    @property
+    def total_tiles(self) -> int:
+        return int(self.c.total_tiles)
+
+    def run(self, alpha=1.0, beta=0.0, flags=0, stream=None):
+        msrep_spmv_batched(self, alpha, beta, flags, stream)
+
+
+def msrep_spmv_batched(batch: DeviceBatch, alpha=1.0, beta=0.0, flags=0, stream=None):
+    """One persistent launch (plus fix-up) over every matrix of the batch."""
+    _check(lib().msrep_spmv_batched(ctypes.byref(batch.c), _ptr(batch.xptr),
+                                    _ptr(batch.yptr), float(alpha), float(beta), flags,
+                                    _ptr(batch.ws), _stream(stream)))
+
+
+def msrep_autotune(mats, xs, ys, device="cuda", stream=None) -> c_msrep_tune_table:
+    """Run the autotuner over the batch's size buckets; returns the table."""
+    import torch
+    arr = _mat_array(mats)
+    need = ctypes.c_int64()
+    _check(lib().msrep_autotune_scratch_size(len(mats), arr, ctypes.byref(need)))
+    scratch = torch.empty(max(need.value, 256), dtype=torch.uint8, device=device)
+    xp = (ctypes.c_void_p * len(mats))(*[t.data_ptr() for t in xs])
+    yp = (ctypes.c_void_p * len(mats))(*[t.data_ptr() for t in ys])
+    out = c_msrep_tune_table()
+    _check(lib().msrep_autotune(len(mats), arr, xp, yp, _ptr(scratch), need.value,
+                                ctypes.byref(out), _stream(stream)))
+    return out
