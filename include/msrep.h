@@ -260,6 +260,72 @@ msrep_status msrep_autotune(int32_t count, const msrep_matrix *As,
                             void *scratch, int64_t scratch_bytes,
                             msrep_tune_table *out, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Serving: a request loop over device-resident matrices with continuous */
+/* batching.  No counterpart in the paper.                                */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+  int64_t budget_bytes;   /* device memory the server may hold in total  */
+  int64_t arena_bytes;    /* per in-flight launch: x and y staging (each) */
+  int32_t contexts;       /* launches in flight at once (>= 1)           */
+  int32_t max_items;      /* SpMV items (vectors) per launch             */
+  int32_t max_k;          /* vectors per request                         */
+  int32_t tile;           /* tile of every registered matrix (0 = def.)  */
+  int64_t max_tiles;      /* tiles per launch                            */
+  int32_t device;         /* CUDA device ordinal                         */
+} msrep_serve_config;
+
+typedef struct msrep_server msrep_server; /* opaque */
+
+typedef struct {
+  uint64_t submitted, completed, rejected, launches;
+  double p50_us, p99_us, mean_us, max_us; /* submit -> y on the host      */
+  double gbs;             /* algorithmic bytes of completed work / busy s */
+  double mean_items;      /* vectors per launch                           */
+  double busy_s;          /* wall time with at least one launch in flight */
+  int64_t resident_bytes; /* device bytes held (matrices + arenas)        */
+} msrep_serve_counters;
+
+/* Defaults: 60 GB budget, 64 MB arenas, 3 contexts, 256 items, k <= 8. */
+msrep_status msrep_serve_config_default(msrep_serve_config *cfg);
+
+/* Starts a server (allocates its arenas and two host threads).  Errors:
+ * INVALID_ARG, BUDGET (arenas alone exceed the budget), OOM, CUDA. */
+msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **out);
+
+/* Copies a CSR matrix whose arrays are in HOST memory to the device (values
+ * stored as FP32; F64 values are rounded), partitions it (Alg. 2, one
+ * partition per 2^20 nonzeros) and builds its tile plan.  Syncs.  Errors:
+ * BUDGET when it does not fit in what the budget leaves, OOM, INVALID_ARG. */
+msrep_status msrep_serve_register(msrep_server *s, const msrep_matrix *host_csr,
+                                  int64_t *matrix_id);
+
+/* Removes a matrix once no queued or running request names it; its device
+ * memory returns to the budget.  NOT_FOUND for an unknown id. */
+msrep_status msrep_serve_unregister(msrep_server *s, int64_t matrix_id);
+
+/* Queues y_v = A x_v for v = 0..k-1 (x_host: k vectors of n floats, one
+ * after the other; y_host: k vectors of m floats); both host buffers stay
+ * owned by the caller and must live until the request completes.  Does not
+ * block.  The request joins a launch as soon as a context and arena space
+ * are free (continuous batching).  Errors: NOT_FOUND, INVALID_ARG (k out
+ * of range), SHUTDOWN. */
+msrep_status msrep_serve_submit(msrep_server *s, int64_t matrix_id, int32_t k,
+                                const float *x_host, float *y_host, uint64_t *req_id);
+
+/* Waits up to timeout_us (< 0: no limit) for the request; MSREP_OK when y
+ * is in place, TIMEOUT otherwise (the request stays queued or running),
+ * NOT_FOUND for an unknown or already collected id. */
+msrep_status msrep_serve_wait(msrep_server *s, uint64_t req_id, int64_t timeout_us);
+
+/* Counters and latency percentiles of completed requests since creation
+ * or the last reset (reset != 0 clears them after reading). */
+msrep_status msrep_serve_stats(msrep_server *s, msrep_serve_counters *out, int32_t reset);
+
+/* Stops the threads after finishing queued work, frees everything. */
+msrep_status msrep_serve_destroy(msrep_server *s);
+
 /* Host; syncs `stream`.  Reads and clears the device error word that the
  * streaming kernels set when a bounded wait on one of their bulk copies
  * expires (which means the copy engine stalled or an argument was wrong).

@@ -14,7 +14,9 @@ from .native import (MSREP_BF16, MSREP_COMP_ALL, MSREP_COMP_NONE, MSREP_COO,
                      msrep_plan_size, msrep_spmv, msrep_spmv_workspace_size,
                      msrep_tile_supported, msrep_version, DeviceBatch,
                      msrep_autotune, msrep_batch_plan_size, msrep_spmv_batched,
-                     msrep_tune_default)
+                     msrep_tune_default, Server, ServeTicket,
+                     msrep_serve_config_default)
 
 __all__ = [n for n in dir() if n.startswith(("msrep_", "MSREP_"))] + [
-    "DeviceMatrix", "DevicePartition", "DeviceBatch", "MsrepError", "alloc_workspace"]
+    "DeviceMatrix", "DevicePartition", "DeviceBatch", "MsrepError", "alloc_workspace",
+    "Server", "ServeTicket"]

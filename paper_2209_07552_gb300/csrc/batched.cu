@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "spmv_core.cuh"
+#include "batch.cuh"
 
 namespace msrep {
 
@@ -18,16 +19,6 @@ msrep_status check_matrix(const msrep_matrix *A);
 int32_t effective_tile(int32_t tile);
 int *kernel_err_ptr();
 
-// one matrix of the batch, as the kernels see it
-struct BatchItem {
-  const int32_t *row_ptr;
-  const int32_t *col_idx;
-  const void *val;
-  const int32_t *tile_row;
-  const int32_t *tile_k;
-  int32_t m, n;
-  int64_t nnz;
-};
 
 constexpr int kBWarps = 8;
 constexpr int kBThreads = 32 * kBWarps;
@@ -170,6 +161,39 @@ static size_t batch_bytes(int32_t count, const msrep_matrix *As, const msrep_tun
   return at;
 }
 
+msrep_status launch_batched(const BatchItem *items, const int64_t *toff, int count,
+                            int64_t total_tiles, int32_t val_dtype, const void *const *xs,
+                            void *const *ys, double *head, double *tail, double alpha,
+                            double beta, unsigned flags, cudaStream_t st) {
+  int *err = kernel_err_ptr();
+  if (!err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
+  const int finish = finish_mode(alpha, beta);
+  const unsigned comp = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
+  const int64_t T = total_tiles;
+  if (T == 0) return MSREP_OK;
+  const int sms = sm_count();
+  auto launch = [&](auto kern, auto fix) -> msrep_status {
+    static int nb = -1;
+    if (nb < 0) {
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBThreads, 0) != cudaSuccess || nb < 1)
+        nb = 1;
+    }
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(T, kBWarps), int64_t(nb) * sms));
+    kern<<<static_cast<int>(grid), kBThreads, 0, st>>>(items, toff, count, xs, ys, head, tail,
+                                                       alpha, beta, finish, comp, err);
+    MSREP_CUDA_TRY(cudaGetLastError());
+    const int64_t fg = std::max<int64_t>(1, std::min<int64_t>(ceil_div(T, 256), 4 * sms));
+    fix<<<static_cast<int>(fg), 256, 0, st>>>(items, toff, count, ys, head, tail, alpha, beta);
+    MSREP_CUDA_TRY(cudaGetLastError());
+    return MSREP_OK;
+  };
+  switch (val_dtype) {
+    case MSREP_F64: return launch(batched_csr<PolF64>, batched_fixup<double>);
+    case MSREP_F32: return launch(batched_csr<PolF32<float>>, batched_fixup<float>);
+    default: return launch(batched_csr<PolF32<bf16_t>>, batched_fixup<float>);
+  }
+}
+
 }  // namespace msrep
 
 using namespace msrep;
@@ -265,42 +289,14 @@ msrep_status msrep_spmv_batched(const msrep_batch *B, const void *const *xs, voi
   if (!xs || !ys || !workspace) return fail(MSREP_ERR_INVALID_ARG, "xs, ys or workspace is NULL");
   if (reinterpret_cast<uintptr_t>(workspace) & 15)
     return fail(MSREP_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
-  cudaStream_t st = as_stream(stream);
   const char *base = static_cast<const char *>(B->dev);
-  const BatchItem *items = reinterpret_cast<const BatchItem *>(base + B->items_off);
-  const int64_t *toff = reinterpret_cast<const int64_t *>(base + B->toff_off);
   double *head = static_cast<double *>(workspace);
   double *tail = reinterpret_cast<double *>(static_cast<char *>(workspace) +
                                             align256(sizeof(double) * std::max<int64_t>(B->total_tiles, 1)));
-  int *err = kernel_err_ptr();
-  if (!err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
-  const int finish = finish_mode(alpha, beta);
-  const unsigned comp = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
-  const int64_t T = B->total_tiles;
-  if (T == 0) return ok();
-  const int sms = sm_count();
-  auto launch = [&](auto kern, auto fix) -> msrep_status {
-    static int nb = -1;
-    if (nb < 0) {
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBThreads, 0) != cudaSuccess || nb < 1)
-        nb = 1;
-    }
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(T, kBWarps), int64_t(nb) * sms));
-    kern<<<static_cast<int>(grid), kBThreads, 0, st>>>(items, toff, B->count, xs, ys, head, tail,
-                                                       alpha, beta, finish, comp, err);
-    MSREP_CUDA_TRY(cudaGetLastError());
-    const int64_t fg = std::max<int64_t>(1, std::min<int64_t>(ceil_div(T, 256), 4 * sms));
-    fix<<<static_cast<int>(fg), 256, 0, st>>>(items, toff, B->count, ys, head, tail, alpha, beta);
-    MSREP_CUDA_TRY(cudaGetLastError());
-    return MSREP_OK;
-  };
-  msrep_status s;
-  switch (B->val_dtype) {
-    case MSREP_F64: s = launch(batched_csr<PolF64>, batched_fixup<double>); break;
-    case MSREP_F32: s = launch(batched_csr<PolF32<float>>, batched_fixup<float>); break;
-    default: s = launch(batched_csr<PolF32<bf16_t>>, batched_fixup<float>); break;
-  }
-  if (s != MSREP_OK) return s;
+  MSREP_TRY(launch_batched(reinterpret_cast<const BatchItem *>(base + B->items_off),
+                           reinterpret_cast<const int64_t *>(base + B->toff_off), B->count,
+                           B->total_tiles, B->val_dtype, xs, ys, head, tail, alpha, beta, flags,
+                           as_stream(stream)));
   return ok();
 }
 

@@ -1,0 +1,579 @@
+// Serving: device-resident matrices, HBM-budget admission and continuous
+// batching of SpMV requests onto the persistent batched kernel.
+//
+// Threads: the caller's threads submit and wait; a scheduler thread packs
+// queued requests into a launch whenever a context (stream + x/y arenas +
+// directory buffers) is free; a completion thread polls each context's
+// event, copies y back to the callers' buffers and wakes the waiters.
+// Several contexts are in flight at once, so requests that arrive while
+// others run are admitted as soon as a context frees up, and their work
+// overlaps on the device.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "batch.cuh"
+#include "common.cuh"
+
+extern "C" msrep_status msrep_partition_csr(const msrep_matrix *A, msrep_partition *part,
+                                            unsigned flags, void *stream);
+
+namespace msrep {
+
+int32_t effective_tile(int32_t tile);
+
+using Clock = std::chrono::steady_clock;
+
+struct Resident {
+  int64_t id;
+  int32_t m, n;
+  int64_t nnz;
+  int32_t np, tile;
+  int64_t tiles;     // tile count of the plan
+  void *mem;         // one device allocation for everything below
+  size_t bytes;
+  BatchItem item;    // pointers into mem
+  int64_t refs = 0;  // queued or running requests
+  bool dying = false;
+};
+
+struct Request {
+  uint64_t id;
+  int64_t matrix;
+  int32_t k;
+  const float *x;
+  float *y;
+  Clock::time_point t_submit;
+  bool done = false;
+  msrep_status status = MSREP_OK;
+};
+
+struct Context {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done_ev = nullptr;
+  float *x_dev = nullptr, *y_dev = nullptr;    // arenas
+  float *x_pin = nullptr, *y_pin = nullptr;    // pinned staging
+  int64_t arena_floats = 0;
+  char *dir_dev = nullptr;                     // items | toff | xs | ys
+  char *dir_pin = nullptr;
+  size_t dir_bytes = 0;
+  double *head = nullptr, *tail = nullptr;
+  int64_t max_tiles = 0;
+  bool busy = false;
+  std::vector<std::shared_ptr<Request>> reqs;  // in this launch
+  std::vector<int64_t> y_off;                  // per request, floats into y arena
+  double bytes = 0;                            // algorithmic bytes of the launch
+  Clock::time_point t_launch;
+};
+
+}  // namespace msrep
+
+struct msrep_server {
+  msrep_serve_config cfg;
+  std::mutex mu;
+  std::condition_variable cv_work;   // scheduler: new request or free context
+  std::condition_variable cv_done;   // waiters
+  std::map<int64_t, msrep::Resident> mats;
+  std::deque<std::shared_ptr<msrep::Request>> queue;
+  std::unordered_map<uint64_t, std::shared_ptr<msrep::Request>> reqs;
+  std::vector<msrep::Context> ctx;
+  int64_t next_matrix = 1;
+  uint64_t next_req = 1;
+  int64_t resident = 0;
+  bool stop = false;
+  std::thread scheduler, completer;
+  // statistics
+  std::vector<double> lat_us;
+  uint64_t submitted = 0, completed = 0, rejected = 0, launches = 0, items = 0;
+  double work_bytes = 0, busy_s = 0;
+  int inflight = 0;
+  msrep::Clock::time_point busy_since;
+};
+
+namespace msrep {
+
+static size_t dir_size(int32_t max_items) {
+  return align256(sizeof(BatchItem) * max_items) + align256(sizeof(int64_t) * (max_items + 1)) +
+         2 * align256(sizeof(void *) * max_items);
+}
+
+static void free_context(Context &c) {
+  if (c.stream) cudaStreamSynchronize(c.stream);
+  cudaFree(c.x_dev);
+  cudaFree(c.y_dev);
+  cudaFree(c.dir_dev);
+  cudaFree(c.head);
+  cudaFree(c.tail);
+  cudaFreeHost(c.x_pin);
+  cudaFreeHost(c.y_pin);
+  cudaFreeHost(c.dir_pin);
+  if (c.done_ev) cudaEventDestroy(c.done_ev);
+  if (c.stream) cudaStreamDestroy(c.stream);
+  c = Context{};
+}
+
+// Launch the requests in c.reqs (scheduler thread, server lock NOT held
+// while copying; the matrices they name are pinned by their refs).
+static msrep_status launch_context(msrep_server *s, Context &c,
+                                   const std::vector<BatchItem> &items,
+                                   const std::vector<int64_t> &tiles) {
+  const int cnt = static_cast<int>(items.size());
+  // directory in pinned memory, then one copy
+  char *dp = c.dir_pin;
+  BatchItem *it = reinterpret_cast<BatchItem *>(dp);
+  size_t o = align256(sizeof(BatchItem) * s->cfg.max_items);
+  int64_t *toff = reinterpret_cast<int64_t *>(dp + o);
+  o += align256(sizeof(int64_t) * (s->cfg.max_items + 1));
+  const void **xs = reinterpret_cast<const void **>(dp + o);
+  o += align256(sizeof(void *) * s->cfg.max_items);
+  void **ys = reinterpret_cast<void **>(dp + o);
+  int64_t xo = 0, yo = 0, tt = 0;
+  int item = 0;
+  c.y_off.clear();
+  for (auto &r : c.reqs) {
+    c.y_off.push_back(yo);
+    const BatchItem &bi = items[item];
+    std::memcpy(c.x_pin + xo, r->x, sizeof(float) * size_t(bi.n) * r->k);
+    for (int v = 0; v < r->k; ++v, ++item) {
+      it[item] = items[item];
+      toff[item] = tt;
+      tt += tiles[item];
+      xs[item] = c.x_dev + xo + int64_t(v) * bi.n;
+      ys[item] = c.y_dev + yo + int64_t(v) * bi.m;
+    }
+    xo += int64_t(bi.n) * r->k;
+    yo += int64_t(bi.m) * r->k;
+  }
+  toff[cnt] = tt;
+  const size_t dir_used = align256(sizeof(BatchItem) * s->cfg.max_items) +
+                          align256(sizeof(int64_t) * (s->cfg.max_items + 1)) +
+                          2 * align256(sizeof(void *) * s->cfg.max_items);
+  MSREP_CUDA_TRY(cudaMemcpyAsync(c.x_dev, c.x_pin, sizeof(float) * xo, cudaMemcpyHostToDevice, c.stream));
+  MSREP_CUDA_TRY(cudaMemcpyAsync(c.dir_dev, c.dir_pin, dir_used, cudaMemcpyHostToDevice, c.stream));
+  const char *dd = c.dir_dev;
+  size_t q = align256(sizeof(BatchItem) * s->cfg.max_items);
+  const int64_t *dtoff = reinterpret_cast<const int64_t *>(dd + q);
+  q += align256(sizeof(int64_t) * (s->cfg.max_items + 1));
+  const void *const *dxs = reinterpret_cast<const void *const *>(dd + q);
+  q += align256(sizeof(void *) * s->cfg.max_items);
+  void *const *dys = reinterpret_cast<void *const *>(dd + q);
+  MSREP_TRY(launch_batched(reinterpret_cast<const BatchItem *>(dd), dtoff, cnt, tt, MSREP_F32,
+                           dxs, dys, c.head, c.tail, 1.0, 0.0, 0, c.stream));
+  MSREP_CUDA_TRY(cudaMemcpyAsync(c.y_pin, c.y_dev, sizeof(float) * yo, cudaMemcpyDeviceToHost, c.stream));
+  MSREP_CUDA_TRY(cudaEventRecord(c.done_ev, c.stream));
+  return MSREP_OK;
+}
+
+static void scheduler_loop(msrep_server *s) {
+  cudaSetDevice(s->cfg.device);
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    s->cv_work.wait(lk, [&] {
+      if (s->stop && s->queue.empty()) return true;
+      if (s->queue.empty()) return false;
+      for (auto &c : s->ctx)
+        if (!c.busy) return true;
+      return false;
+    });
+    if (s->stop && s->queue.empty()) return;
+    Context *c = nullptr;
+    for (auto &cc : s->ctx)
+      if (!cc.busy) {
+        c = &cc;
+        break;
+      }
+    if (!c) continue;
+    // pack requests in arrival order while the context has room
+    std::vector<BatchItem> items;
+    std::vector<int64_t> tiles;
+    int64_t xf = 0, yf = 0, tt = 0;
+    double bytes = 0;
+    c->reqs.clear();
+    while (!s->queue.empty()) {
+      auto r = s->queue.front();
+      auto mit = s->mats.find(r->matrix);
+      const Resident &R = mit->second;
+      const int64_t nx = int64_t(R.n) * r->k, ny = int64_t(R.m) * r->k;
+      if (!c->reqs.empty() &&
+          (int(items.size()) + r->k > s->cfg.max_items || xf + nx > c->arena_floats ||
+           yf + ny > c->arena_floats || tt + R.tiles * r->k > c->max_tiles))
+        break;
+      s->queue.pop_front();
+      c->reqs.push_back(r);
+      for (int v = 0; v < r->k; ++v) {
+        items.push_back(R.item);
+        tiles.push_back(R.tiles);
+      }
+      xf += nx;
+      yf += ny;
+      tt += R.tiles * r->k;
+      // algorithmic bytes: FP32 CSR formula per vector
+      bytes += double(r->k) * (8.0 * R.nnz + 4.0 * (R.m + 1) + 4.0 * R.n + 4.0 * R.m);
+    }
+    c->busy = true;
+    c->bytes = bytes;
+    c->t_launch = Clock::now();
+    if (s->inflight++ == 0) s->busy_since = c->t_launch;
+    s->launches++;
+    s->items += items.size();
+    lk.unlock();
+    msrep_status st = launch_context(s, *c, items, tiles);
+    lk.lock();
+    if (st != MSREP_OK) {
+      // fail the requests of this launch; the context stays usable
+      cudaStreamSynchronize(c->stream);
+      for (auto &r : c->reqs) {
+        r->status = st;
+        r->done = true;
+        s->mats[r->matrix].refs--;
+      }
+      c->reqs.clear();
+      c->busy = false;
+      if (--s->inflight == 0)
+        s->busy_s += std::chrono::duration<double>(Clock::now() - s->busy_since).count();
+      s->cv_done.notify_all();
+    }
+  }
+}
+
+static void completion_loop(msrep_server *s) {
+  cudaSetDevice(s->cfg.device);
+  for (;;) {
+    bool any = false, stop = false;
+    {
+      std::lock_guard<std::mutex> lk(s->mu);
+      stop = s->stop && s->queue.empty();
+      for (auto &c : s->ctx) any |= c.busy;
+      if (stop && !any) return;
+    }
+    bool progressed = false;
+    for (auto &c : s->ctx) {
+      bool busy;
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        busy = c.busy;
+      }
+      if (!busy) continue;
+      const cudaError_t q = cudaEventQuery(c.done_ev);
+      if (q == cudaErrorNotReady) continue;
+      progressed = true;
+      // results to the callers' buffers, outside the lock
+      for (size_t i = 0; i < c.reqs.size(); ++i) {
+        auto &r = c.reqs[i];
+        int32_t m;
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          m = s->mats[r->matrix].m;
+        }
+        if (q == cudaSuccess)
+          std::memcpy(r->y, c.y_pin + c.y_off[i], sizeof(float) * size_t(m) * r->k);
+      }
+      const auto now = Clock::now();
+      std::lock_guard<std::mutex> lk(s->mu);
+      for (auto &r : c.reqs) {
+        r->status = q == cudaSuccess ? MSREP_OK : MSREP_ERR_CUDA;
+        r->done = true;
+        s->mats[r->matrix].refs--;
+        s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r->t_submit).count());
+        s->completed++;
+      }
+      s->work_bytes += c.bytes;
+      c.reqs.clear();
+      c.busy = false;
+      if (--s->inflight == 0)
+        s->busy_s += std::chrono::duration<double>(now - s->busy_since).count();
+      s->cv_done.notify_all();
+      s->cv_work.notify_all();
+    }
+    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+}  // namespace msrep
+
+using namespace msrep;
+
+extern "C" {
+
+msrep_status msrep_serve_config_default(msrep_serve_config *c) {
+  if (!c) return fail(MSREP_ERR_INVALID_ARG, "cfg is NULL");
+  c->budget_bytes = int64_t(60) << 30;
+  c->arena_bytes = int64_t(64) << 20;
+  c->contexts = 3;
+  c->max_items = 256;
+  c->max_k = 8;
+  c->tile = 0;
+  c->max_tiles = int64_t(1) << 20;
+  c->device = 0;
+  return ok();
+}
+
+msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **out) {
+  if (!cfg || !out) return fail(MSREP_ERR_INVALID_ARG, "cfg or out is NULL");
+  if (cfg->contexts < 1 || cfg->max_items < 1 || cfg->max_k < 1 || cfg->max_k > cfg->max_items ||
+      cfg->arena_bytes < 4096 || cfg->max_tiles < 1 || !tile_supported(effective_tile(cfg->tile)))
+    return fail(MSREP_ERR_INVALID_ARG, "bad serve config");
+  const int64_t per_ctx = 2 * align256(cfg->arena_bytes) + int64_t(dir_size(cfg->max_items)) +
+                          2 * int64_t(align256(sizeof(double) * cfg->max_tiles));
+  if (per_ctx * cfg->contexts > cfg->budget_bytes)
+    return fail(MSREP_ERR_BUDGET, "the launch contexts alone exceed the budget");
+  MSREP_CUDA_TRY(cudaSetDevice(cfg->device));
+  auto s = std::make_unique<msrep_server>();
+  s->cfg = *cfg;
+  s->ctx.resize(cfg->contexts);
+  for (auto &c : s->ctx) {
+    c.arena_floats = cfg->arena_bytes / int64_t(sizeof(float));
+    c.max_tiles = cfg->max_tiles;
+    c.dir_bytes = dir_size(cfg->max_items);
+    bool okc = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&c.done_ev, cudaEventDisableTiming) == cudaSuccess &&
+               cudaMalloc(&c.x_dev, cfg->arena_bytes) == cudaSuccess &&
+               cudaMalloc(&c.y_dev, cfg->arena_bytes) == cudaSuccess &&
+               cudaMalloc(&c.dir_dev, c.dir_bytes) == cudaSuccess &&
+               cudaMalloc(&c.head, sizeof(double) * cfg->max_tiles) == cudaSuccess &&
+               cudaMalloc(&c.tail, sizeof(double) * cfg->max_tiles) == cudaSuccess &&
+               cudaMallocHost(&c.x_pin, cfg->arena_bytes) == cudaSuccess &&
+               cudaMallocHost(&c.y_pin, cfg->arena_bytes) == cudaSuccess &&
+               cudaMallocHost(&c.dir_pin, c.dir_bytes) == cudaSuccess;
+    if (!okc) {
+      for (auto &cc : s->ctx) free_context(cc);
+      cudaGetLastError();
+      return fail(MSREP_ERR_OOM, "cannot allocate the launch contexts");
+    }
+  }
+  s->resident = per_ctx * cfg->contexts;
+  msrep_server *raw = s.release();
+  raw->scheduler = std::thread(scheduler_loop, raw);
+  raw->completer = std::thread(completion_loop, raw);
+  *out = raw;
+  return ok();
+}
+
+msrep_status msrep_serve_register(msrep_server *s, const msrep_matrix *A, int64_t *matrix_id) {
+  if (!s || !A || !matrix_id) return fail(MSREP_ERR_INVALID_ARG, "NULL argument");
+  if (A->fmt != MSREP_CSR || !A->ptr || (A->nnz > 0 && (!A->idx || !A->val)) || A->m < 0 ||
+      A->n < 0 || A->nnz < 0 || A->nnz > INT32_MAX || A->val_dtype < MSREP_F64 ||
+      A->val_dtype > MSREP_BF16)
+    return fail(MSREP_ERR_INVALID_ARG, "register needs a CSR matrix with host arrays");
+  MSREP_CUDA_TRY(cudaSetDevice(s->cfg.device));
+  const int32_t tile = effective_tile(s->cfg.tile);
+  const int32_t np = static_cast<int32_t>(std::max<int64_t>(1, ceil_div(A->nnz, int64_t(1) << 20)));
+  const PlanLayout PL = plan_layout(A->m, A->nnz, np, tile);
+  size_t o = 0;
+  const size_t o_ptr = o;  o = align256(o + sizeof(int32_t) * (size_t(A->m) + 1));
+  const size_t o_col = o;  o = align256(o + sizeof(int32_t) * size_t(A->nnz));
+  const size_t o_val = o;  o = align256(o + sizeof(float) * size_t(A->nnz));
+  const size_t o_meta = o; o = align256(o + 4 * sizeof(int32_t) * size_t(np));
+  const size_t o_flag = o; o = align256(o + size_t(np));
+  const size_t o_plan = o; o = align256(o + PL.bytes);
+  const size_t bytes = o;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) return fail(MSREP_ERR_SHUTDOWN, "server is stopping");
+    if (s->resident + int64_t(bytes) > s->cfg.budget_bytes) {
+      s->rejected++;
+      return fail(MSREP_ERR_BUDGET, "matrix needs %zu bytes, %lld of %lld in use", bytes,
+                  (long long)s->resident, (long long)s->cfg.budget_bytes);
+    }
+    s->resident += int64_t(bytes);  // reserve
+  }
+  void *mem = nullptr;
+  auto unreserve = [&](msrep_status st) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->resident -= int64_t(bytes);
+    if (mem) cudaFree(mem);
+    return st;
+  };
+  if (cudaMalloc(&mem, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return unreserve(fail(MSREP_ERR_OOM, "device allocation of %zu bytes failed", bytes));
+  }
+  char *b = static_cast<char *>(mem);
+  // values to FP32 on the host
+  std::vector<float> vf(size_t(A->nnz));
+  for (int64_t k = 0; k < A->nnz; ++k) {
+    if (A->val_dtype == MSREP_F64)
+      vf[k] = static_cast<float>(static_cast<const double *>(A->val)[k]);
+    else if (A->val_dtype == MSREP_F32)
+      vf[k] = static_cast<const float *>(A->val)[k];
+    else {
+      uint32_t w = uint32_t(static_cast<const uint16_t *>(A->val)[k]) << 16;
+      std::memcpy(&vf[k], &w, 4);
+    }
+  }
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+    return unreserve(fail(MSREP_ERR_CUDA, "stream creation failed"));
+  bool good = cudaMemcpyAsync(b + o_ptr, A->ptr, sizeof(int32_t) * (size_t(A->m) + 1),
+                              cudaMemcpyHostToDevice, st) == cudaSuccess &&
+              (A->nnz == 0 ||
+               (cudaMemcpyAsync(b + o_col, A->idx, sizeof(int32_t) * size_t(A->nnz),
+                                cudaMemcpyHostToDevice, st) == cudaSuccess &&
+                cudaMemcpyAsync(b + o_val, vf.data(), sizeof(float) * size_t(A->nnz),
+                                cudaMemcpyHostToDevice, st) == cudaSuccess));
+  msrep_matrix D = *A;
+  D.val_dtype = MSREP_F32;
+  D.ptr = reinterpret_cast<const int32_t *>(b + o_ptr);
+  D.idx = reinterpret_cast<const int32_t *>(b + o_col);
+  D.val = b + o_val;
+  msrep_partition p{};
+  p.np = np;
+  p.tile = tile;
+  int32_t *meta = reinterpret_cast<int32_t *>(b + o_meta);
+  p.start_idx = meta;
+  p.end_idx = meta + np;
+  p.start_major = meta + 2 * np;
+  p.end_major = meta + 3 * np;
+  p.start_flag = reinterpret_cast<uint8_t *>(b + o_flag);
+  p.plan = b + o_plan;
+  p.plan_bytes = static_cast<int64_t>(PL.bytes);
+  int32_t ntiles = 0;
+  if (good) good = msrep_partition_csr(&D, &p, 0, st) == MSREP_OK;
+  if (good)
+    good = cudaMemcpyAsync(&ntiles, b + o_plan + PL.off_toff + sizeof(int32_t) * np,
+                           sizeof(int32_t), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+           cudaStreamSynchronize(st) == cudaSuccess;
+  cudaStreamDestroy(st);
+  if (!good) {
+    cudaGetLastError();
+    return unreserve(fail(MSREP_ERR_CUDA, "upload or partition failed"));
+  }
+  Resident R;
+  R.m = A->m;
+  R.n = A->n;
+  R.nnz = A->nnz;
+  R.np = np;
+  R.tile = tile;
+  R.tiles = ntiles;
+  R.mem = mem;
+  R.bytes = bytes;
+  R.item = BatchItem{D.ptr, D.idx, D.val, reinterpret_cast<const int32_t *>(b + o_plan + PL.off_row),
+                     reinterpret_cast<const int32_t *>(b + o_plan + PL.off_k), A->m, A->n, A->nnz};
+  std::lock_guard<std::mutex> lk(s->mu);
+  R.id = s->next_matrix++;
+  *matrix_id = R.id;
+  s->mats[R.id] = R;
+  return ok();
+}
+
+msrep_status msrep_serve_unregister(msrep_server *s, int64_t id) {
+  if (!s) return fail(MSREP_ERR_INVALID_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->mats.find(id);
+  if (it == s->mats.end() || it->second.dying) return fail(MSREP_ERR_NOT_FOUND, "unknown matrix %lld", (long long)id);
+  it->second.dying = true;
+  s->cv_done.wait(lk, [&] { return it->second.refs == 0; });
+  cudaFree(it->second.mem);
+  s->resident -= int64_t(it->second.bytes);
+  s->mats.erase(it);
+  return ok();
+}
+
+msrep_status msrep_serve_submit(msrep_server *s, int64_t id, int32_t k, const float *x,
+                                float *y, uint64_t *req_id) {
+  if (!s || !x || !y || !req_id) return fail(MSREP_ERR_INVALID_ARG, "NULL argument");
+  if (k < 1 || k > s->cfg.max_k) return fail(MSREP_ERR_INVALID_ARG, "k must be 1..%d", s->cfg.max_k);
+  auto r = std::make_shared<Request>();
+  r->matrix = id;
+  r->k = k;
+  r->x = x;
+  r->y = y;
+  r->t_submit = Clock::now();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) return fail(MSREP_ERR_SHUTDOWN, "server is stopping");
+  auto it = s->mats.find(id);
+  if (it == s->mats.end() || it->second.dying)
+    return fail(MSREP_ERR_NOT_FOUND, "unknown matrix %lld", (long long)id);
+  const int64_t nx = int64_t(it->second.n) * k, ny = int64_t(it->second.m) * k;
+  const int64_t cap = s->cfg.arena_bytes / int64_t(sizeof(float));
+  if (nx > cap || ny > cap || it->second.tiles * k > s->cfg.max_tiles)
+    return fail(MSREP_ERR_INVALID_ARG, "request does not fit one launch context");
+  it->second.refs++;
+  r->id = s->next_req++;
+  *req_id = r->id;
+  s->reqs[r->id] = r;
+  s->queue.push_back(r);
+  s->submitted++;
+  s->cv_work.notify_one();
+  return ok();
+}
+
+msrep_status msrep_serve_wait(msrep_server *s, uint64_t req_id, int64_t timeout_us) {
+  if (!s) return fail(MSREP_ERR_INVALID_ARG, "server is NULL");
+  std::unique_lock<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(req_id);
+  if (it == s->reqs.end()) return fail(MSREP_ERR_NOT_FOUND, "unknown request %llu", (unsigned long long)req_id);
+  auto r = it->second;
+  if (timeout_us < 0) {
+    s->cv_done.wait(lk, [&] { return r->done; });
+  } else if (!s->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), [&] { return r->done; })) {
+    return fail(MSREP_ERR_TIMEOUT, "request %llu not finished", (unsigned long long)req_id);
+  }
+  s->reqs.erase(req_id);
+  if (r->status != MSREP_OK) return fail(r->status, "request %llu failed", (unsigned long long)req_id);
+  return ok();
+}
+
+msrep_status msrep_serve_stats(msrep_server *s, msrep_serve_counters *o, int32_t reset) {
+  if (!s || !o) return fail(MSREP_ERR_INVALID_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(s->mu);
+  std::memset(o, 0, sizeof *o);
+  o->submitted = s->submitted;
+  o->completed = s->completed;
+  o->rejected = s->rejected;
+  o->launches = s->launches;
+  std::vector<double> l = s->lat_us;
+  if (!l.empty()) {
+    std::sort(l.begin(), l.end());
+    auto pct = [&](double p) { return l[std::min(l.size() - 1, size_t(p * (l.size() - 1) + 0.5))]; };
+    o->p50_us = pct(0.50);
+    o->p99_us = pct(0.99);
+    double sum = 0;
+    for (double v : l) sum += v;
+    o->mean_us = sum / l.size();
+    o->max_us = l.back();
+  }
+  double busy = s->busy_s;
+  if (s->inflight > 0) busy += std::chrono::duration<double>(Clock::now() - s->busy_since).count();
+  o->busy_s = busy;
+  o->gbs = busy > 0 ? s->work_bytes / busy / 1e9 : 0.0;
+  o->mean_items = s->launches ? double(s->items) / double(s->launches) : 0.0;
+  o->resident_bytes = s->resident;
+  if (reset) {
+    s->lat_us.clear();
+    s->submitted = s->completed = s->rejected = s->launches = s->items = 0;
+    s->work_bytes = 0;
+    s->busy_s = 0;
+    if (s->inflight > 0) s->busy_since = Clock::now();
+  }
+  return ok();
+}
+
+msrep_status msrep_serve_destroy(msrep_server *s) {
+  if (!s) return fail(MSREP_ERR_INVALID_ARG, "server is NULL");
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv_work.notify_all();
+  }
+  if (s->scheduler.joinable()) s->scheduler.join();
+  if (s->completer.joinable()) s->completer.join();
+  for (auto &c : s->ctx) free_context(c);
+  for (auto &kv : s->mats) cudaFree(kv.second.mem);
+  delete s;
+  return ok();
+}
+
+}  // extern "C"

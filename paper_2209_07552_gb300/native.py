@@ -68,6 +68,22 @@ class c_msrep_batch(ctypes.Structure):
                 ("items_off", ctypes.c_int64), ("toff_off", ctypes.c_int64)]
 
 
+class c_msrep_serve_config(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
+                ("contexts", ctypes.c_int32), ("max_items", ctypes.c_int32),
+                ("max_k", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("max_tiles", ctypes.c_int64), ("device", ctypes.c_int32)]
+
+
+class c_msrep_serve_counters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("gbs", ctypes.c_double), ("mean_items", ctypes.c_double),
+                ("busy_s", ctypes.c_double), ("resident_bytes", ctypes.c_int64)]
+
+
 _M = ctypes.POINTER(c_msrep_matrix)
 _P = ctypes.POINTER(c_msrep_partition)
 _vp = ctypes.c_void_p
@@ -103,6 +119,17 @@ SIGNATURES = {
                                           _vp, _vp]),
     "msrep_autotune_scratch_size": (ctypes.c_int, [ctypes.c_int32, _M,
                                                    ctypes.POINTER(ctypes.c_int64)]),
+    "msrep_serve_config_default": (ctypes.c_int, [ctypes.POINTER(c_msrep_serve_config)]),
+    "msrep_serve_create": (ctypes.c_int, [ctypes.POINTER(c_msrep_serve_config),
+                                          ctypes.POINTER(ctypes.c_void_p)]),
+    "msrep_serve_register": (ctypes.c_int, [_vp, _M, ctypes.POINTER(ctypes.c_int64)]),
+    "msrep_serve_unregister": (ctypes.c_int, [_vp, ctypes.c_int64]),
+    "msrep_serve_submit": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "msrep_serve_wait": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.c_int64]),
+    "msrep_serve_stats": (ctypes.c_int, [_vp, ctypes.POINTER(c_msrep_serve_counters),
+                                         ctypes.c_int32]),
+    "msrep_serve_destroy": (ctypes.c_int, [_vp]),
     "msrep_autotune": (ctypes.c_int, [ctypes.c_int32, _M, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_void_p), _vp, ctypes.c_int64,
                                       ctypes.POINTER(c_msrep_tune_table), _vp]),
@@ -424,3 +451,89 @@ def msrep_autotune(mats, xs, ys, device="cuda", stream=None) -> c_msrep_tune_tab
     _check(lib().msrep_autotune(len(mats), arr, xp, yp, _ptr(scratch), need.value,
                                 ctypes.byref(out), _stream(stream)))
     return out
+
+
+# --------------------------------------------------------------------------
+# serving
+# --------------------------------------------------------------------------
+
+def msrep_serve_config_default() -> c_msrep_serve_config:
+    c = c_msrep_serve_config()
+    _check(lib().msrep_serve_config_default(ctypes.byref(c)))
+    return c
+
+
+class ServeTicket:
+    """A submitted request: keeps the host x and y buffers alive."""
+
+    def __init__(self, req_id, x, y, k, m):
+        self.id, self.x, self.y, self.k, self.m = req_id, x, y, k, m
+
+    @property
+    def result(self) -> np.ndarray:
+        return self.y.reshape(self.k, self.m)
+
+
+class Server:
+    """msrep_serve_* around host numpy buffers."""
+
+    def __init__(self, **cfg):
+        self.cfg = msrep_serve_config_default()
+        for k, v in cfg.items():
+            setattr(self.cfg, k, v)
+        h = ctypes.c_void_p()
+        _check(lib().msrep_serve_create(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self.h = h
+        self.shapes = {}
+
+    def register(self, a) -> int:
+        """Register an inputs.CSR (host arrays); values are stored as FP32."""
+        ptr = np.ascontiguousarray(a.row_ptr, np.int32)
+        col = np.ascontiguousarray(a.col_idx, np.int32)
+        if a.val.dtype == np.float64:
+            val, dt = np.ascontiguousarray(a.val), MSREP_F64
+        else:
+            val, dt = np.ascontiguousarray(a.val, np.float32), MSREP_F32
+        c = c_msrep_matrix(MSREP_CSR, dt, a.m, a.n, a.nnz, ptr.ctypes.data,
+                           col.ctypes.data, None, val.ctypes.data)
+        out = ctypes.c_int64()
+        _check(lib().msrep_serve_register(self.h, ctypes.byref(c), ctypes.byref(out)))
+        self.shapes[out.value] = (a.m, a.n)
+        return out.value
+
+    def unregister(self, mid: int):
+        _check(lib().msrep_serve_unregister(self.h, mid))
+        self.shapes.pop(mid, None)
+
+    def submit(self, mid: int, X: np.ndarray, y: np.ndarray | None = None) -> ServeTicket:
+        """X: (k, n) float32 (or (n,)); returns a ticket whose .result is (k, m)."""
+        X = np.ascontiguousarray(np.atleast_2d(X), np.float32)
+        k = X.shape[0]
+        m, n = self.shapes[mid]
+        assert X.shape[1] == n
+        if y is None:
+            y = np.empty(k * m, np.float32)
+        rid = ctypes.c_uint64()
+        _check(lib().msrep_serve_submit(self.h, mid, k, X.ctypes.data, y.ctypes.data,
+                                        ctypes.byref(rid)))
+        return ServeTicket(rid.value, X, y, k, m)
+
+    def wait(self, t: ServeTicket, timeout_us: int = -1) -> np.ndarray:
+        _check(lib().msrep_serve_wait(self.h, t.id, timeout_us))
+        return t.result
+
+    def stats(self, reset: bool = False) -> dict:
+        c = c_msrep_serve_counters()
+        _check(lib().msrep_serve_stats(self.h, ctypes.byref(c), 1 if reset else 0))
+        return {f: getattr(c, f) for f, _ in c._fields_}
+
+    def close(self):
+        if self.h:
+            _check(lib().msrep_serve_destroy(self.h))
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,117 @@
+"""Serving: device-resident matrices, budget admission, continuous batching.
+
+Every result must equal, bit for bit, msrep_spmv of the same matrix (FP32
+values, one partition per 2^20 nonzeros, the default tile) on the same x,
+whether the request ran alone or inside a mixed batch of requests for other
+matrices; and it must match the FP64 oracle on the stored values."""
+import threading
+
+import numpy as np
+import pytest
+
+from helpers import normwise, oracle_spmv
+from paper_2209_07552_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _mats(seed=5):
+    out = []
+    ms, mus = I.batched_sizes(6, seed, m_lo=500, m_hi=30000)
+    for i, (m, mu) in enumerate(zip(ms, mus)):
+        out.append(I.geometric_matrix(int(m), float(mu), seed * 10 + i, np.float32))
+    out.append(I.rmat(scale=12, nnz=50_000, seed=seed))
+    return out
+
+
+def _solo(M, a, X):
+    import torch
+    A = M.DeviceMatrix.from_host(a, "csr", "f32")
+    np_ = max(1, -(-a.nnz // (1 << 20)))
+    part = M.DevicePartition(A, np_)
+    M.msrep_partition(A, part)
+    ws = M.alloc_workspace(A, part)
+    ys = []
+    for x in X:
+        y = torch.empty(a.m, dtype=torch.float32, device="cuda")
+        M.msrep_spmv(A, part, 1.0, torch.from_numpy(np.ascontiguousarray(x)).cuda(), 0.0, y,
+                     workspace=ws)
+        ys.append(y.cpu().numpy())
+    return np.stack(ys)
+
+
+def test_serve_results_alone_and_in_the_mix():
+    import paper_2209_07552_gb300 as M
+    mats = _mats()
+    with M.Server(budget_bytes=4 << 30, arena_bytes=16 << 20, contexts=3) as S:
+        ids = [S.register(a) for a in mats]
+        rng = I.rng(9, 9)
+        X = [rng.uniform(-1, 1, (8, a.n)).astype(np.float32) for a in mats]
+        # alone: one request at a time
+        alone = []
+        for mid, x in zip(ids, X):
+            alone.append(S.wait(S.submit(mid, x[:3])).copy())
+        # in the mix: many requests of every matrix from several threads
+        tickets, lock = [], threading.Lock()
+
+        def client(tid):
+            g = I.rng(100 + tid, 1)
+            for _ in range(25):
+                j = int(g.integers(len(ids)))
+                k = int(g.integers(1, 9))
+                t = S.submit(ids[j], X[j][:k])
+                with lock:
+                    tickets.append((j, k, t))
+
+        th = [threading.Thread(target=client, args=(t,)) for t in range(4)]
+        for t in th:
+            t.start()
+        for t in th:
+            t.join()
+        for j, k, t in tickets:
+            y = S.wait(t, 60_000_000)
+            assert np.array_equal(y[: min(k, 3)], alone[j][: min(k, 3)])
+        st = S.stats()
+        assert st["completed"] >= len(tickets) + len(ids)
+        assert st["launches"] >= 1 and st["p99_us"] >= st["p50_us"] > 0
+    for a, x, y in zip(mats, X, alone):
+        assert np.array_equal(y, _solo(M, a, x[:3]))
+        st = I.CSR(a.m, a.n, a.row_ptr, a.col_idx, a.val.astype(np.float64))
+        for v in range(3):
+            assert normwise(y[v], oracle_spmv(st, "csr", x[v].astype(np.float64))) <= 1e-6
+
+
+def test_serve_budget_admission_and_unregister():
+    import paper_2209_07552_gb300 as M
+    big = I.rmat(scale=14, nnz=400_000, seed=3)
+    small = I.geometric_matrix(2000, 8.0, 4, np.float32)
+    ctx = 3 * (2 * (1 << 20) + 2 * 8 * (1 << 16) + 64 * 1024)
+    with M.Server(budget_bytes=ctx + 2_000_000, arena_bytes=1 << 20, contexts=3,
+                  max_tiles=1 << 16, max_items=64) as S:
+        sid = S.register(small)
+        with pytest.raises(M.MsrepError) as e:
+            S.register(big)               # about 3.3 MB does not fit
+        assert e.value.status == 6        # MSREP_ERR_BUDGET
+        assert S.stats()["rejected"] == 1
+        S.unregister(sid)
+        with pytest.raises(M.MsrepError) as e:
+            S.submit(sid, np.zeros((1, small.n), np.float32))
+        assert e.value.status == 7        # NOT_FOUND after unregister
+
+
+def test_serve_wait_timeout_then_complete():
+    import paper_2209_07552_gb300 as M
+    a = I.rmat(scale=16, nnz=1_000_000, seed=8)
+    with M.Server(budget_bytes=2 << 30) as S:
+        mid = S.register(a)
+        t = S.submit(mid, np.ones((8, a.n), np.float32))
+        with pytest.raises(M.MsrepError) as e:
+            S.wait(t, 0)
+        assert e.value.status == 5        # MSREP_ERR_TIMEOUT: not done after 0 us
+        y = S.wait(t, -1)
+        ones = I.CSR(a.m, a.n, a.row_ptr, a.col_idx,
+                     I.to_f32(a.val).astype(np.float64))
+        assert normwise(y[0], oracle_spmv(ones, "csr", np.ones(a.n))) <= 1e-6
+        with pytest.raises(M.MsrepError) as e:
+            S.wait(t, 0)
+        assert e.value.status == 7        # collected already
