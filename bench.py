@@ -291,6 +291,7 @@ def run_ours(args):
     # low-precision form on the R-MAT matrix (CSR)
     prec = run_precision(M, args, dev) if not args.skip_precision else None
     batched = run_batched(M, args, dev) if args.batched_count > 0 else None
+    serving = run_serving(M, args, dev) if args.serve_seconds > 0 else None
 
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
@@ -313,6 +314,8 @@ def run_ours(args):
         line["precision"] = prec
     if batched:
         line["batched"] = batched
+    if serving:
+        line["serving"] = serving
     if rank == 0 and not args.no_cpu_baseline:
         mats = load_workload()
         v, sample = cpu_oracle_run(mats, args.cpu_budget)
@@ -401,6 +404,75 @@ def run_batched(M, args, dev):
             "bytes_per_launch": nbytes, "total_tiles": B.total_tiles,
             "tune": {str(b): tiles[b] for b in used}, "gen_s": gen_s, "autotune_s": tune_s,
             "graph": "one CUDA graph: persistent batched kernel + fix-up"}
+
+
+def run_serving(M, args, dev):
+    """The served form: 64 matrices drawn like the batched set plus two 2^20
+    R-MAT matrices (16.8M nonzeros each) registered under a 60 GB budget; a
+    Poisson stream of requests (args.serve_rate per second), each naming a
+    matrix uniformly and carrying k ~ U{1..8} FP32 vectors.  Latency is
+    submit -> y in the caller's host buffer, measured by the server."""
+    import queue
+    import threading
+    seed = I.SEED_BASE + 4
+    mats, _ = I.batched_set_parallel(64, seed=seed)
+    mats = list(mats) + [I.rmat_full(), I.cached_csr(f"rmat20_{seed}", lambda: I.rmat(seed=seed))]
+    g = I.rng(seed, 300)
+    X = [I.to_f32(g.uniform(-1, 1, (8, a.n))) for a in mats]
+    S = M.Server(budget_bytes=60 << 30, arena_bytes=256 << 20, contexts=4,
+                 max_items=512, device=dev.index or 0)
+    ids = [S.register(a) for a in mats]
+    resident = S.stats()["resident_bytes"]
+    arrivals = I.poisson_arrivals(args.serve_rate, args.serve_seconds, seed)
+    pick = g.integers(0, len(ids), arrivals.shape[0])
+    ks = g.integers(1, 9, arrivals.shape[0])
+    pools = [[] for _ in mats]
+    lock = threading.Lock()
+    q = queue.Queue()
+
+    def waiter():
+        while True:
+            item = q.get()
+            if item is None:
+                return
+            j, t = item
+            S.wait(t)
+            with lock:
+                pools[j].append(t.y)
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    warm = min(1.0, 0.2 * args.serve_seconds)
+    reset_done = False
+    t0 = time.perf_counter()
+    for i in range(arrivals.shape[0]):
+        target = t0 + arrivals[i]
+        while True:
+            now = time.perf_counter()
+            if now >= target:
+                break
+            if target - now > 2e-4:
+                time.sleep((target - now) * 0.5)
+        if not reset_done and now - t0 >= warm:
+            S.stats(reset=True)
+            reset_done = True
+        j, k = int(pick[i]), int(ks[i])
+        with lock:
+            y = pools[j].pop() if pools[j] else None
+        if y is None:
+            y = np.empty(8 * mats[j].m, np.float32)
+        t = S.submit(ids[j], X[j][:k], y)
+        q.put((j, t))
+    sent = time.perf_counter() - t0
+    q.put(None)
+    th.join()
+    st = S.stats()
+    S.close()
+    st.update({"offered_rate": arrivals.shape[0] / args.serve_seconds,
+               "achieved_submit_s": sent, "matrices": len(mats),
+               "window_s": args.serve_seconds, "discarded_warmup_s": warm,
+               "budget_bytes": 60 << 30, "resident_bytes_after_register": resident})
+    return st
 
 
 def run_precision(M, args, dev):
@@ -539,6 +611,9 @@ def main():
     ap.add_argument("--skip-precision", action="store_true")
     ap.add_argument("--batched-count", type=int, default=512,
                     help="matrices in the batched-form measurement (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=4.0,
+                    help="length of the served request stream (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--profile", choices=FORMATS, default=None,
                     help="run only a short fixed case (for ncu captures)")
     ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")

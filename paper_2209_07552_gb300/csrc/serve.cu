@@ -71,7 +71,8 @@ struct Context {
   size_t dir_bytes = 0;
   double *head = nullptr, *tail = nullptr;
   int64_t max_tiles = 0;
-  bool busy = false;
+  bool busy = false;      // packed by the scheduler (launching or in flight)
+  bool in_flight = false; // its event has been recorded for this launch
   std::vector<std::shared_ptr<Request>> reqs;  // in this launch
   std::vector<int64_t> y_off;                  // per request, floats into y arena
   double bytes = 0;                            // algorithmic bytes of the launch
@@ -231,6 +232,7 @@ static void scheduler_loop(msrep_server *s) {
     lk.unlock();
     msrep_status st = launch_context(s, *c, items, tiles);
     lk.lock();
+    if (st == MSREP_OK) c->in_flight = true;  // only now may its event be polled
     if (st != MSREP_OK) {
       // fail the requests of this launch; the context stays usable
       cudaStreamSynchronize(c->stream);
@@ -260,12 +262,12 @@ static void completion_loop(msrep_server *s) {
     }
     bool progressed = false;
     for (auto &c : s->ctx) {
-      bool busy;
+      bool flying;
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        busy = c.busy;
+        flying = c.busy && c.in_flight;
       }
-      if (!busy) continue;
+      if (!flying) continue;
       const cudaError_t q = cudaEventQuery(c.done_ev);
       if (q == cudaErrorNotReady) continue;
       progressed = true;
@@ -292,6 +294,7 @@ static void completion_loop(msrep_server *s) {
       s->work_bytes += c.bytes;
       c.reqs.clear();
       c.busy = false;
+      c.in_flight = false;
       if (--s->inflight == 0)
         s->busy_s += std::chrono::duration<double>(now - s->busy_since).count();
       s->cv_done.notify_all();
