@@ -502,17 +502,19 @@ class Server:
         return out.value
 
     def unregister(self, mid: int):
+        # the shape stays known so that later calls reach the library and
+        # get its NOT_FOUND status
         _check(lib().msrep_serve_unregister(self.h, mid))
-        self.shapes.pop(mid, None)
 
     def submit(self, mid: int, X: np.ndarray, y: np.ndarray | None = None) -> ServeTicket:
         """X: (k, n) float32 (or (n,)); returns a ticket whose .result is (k, m)."""
         X = np.ascontiguousarray(np.atleast_2d(X), np.float32)
         k = X.shape[0]
-        m, n = self.shapes[mid]
-        assert X.shape[1] == n
+        m, n = self.shapes.get(mid, (0, X.shape[1]))
+        if X.shape[1] != n:
+            raise ValueError(f"x has {X.shape[1]} entries, matrix has {n} columns")
         if y is None:
-            y = np.empty(k * m, np.float32)
+            y = np.empty(max(k * m, 1), np.float32)
         rid = ctypes.c_uint64()
         _check(lib().msrep_serve_submit(self.h, mid, k, X.ctypes.data, y.ctypes.data,
                                         ctypes.byref(rid)))
