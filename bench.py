@@ -418,7 +418,11 @@ def run_serving(M, args, dev):
     mats, _ = I.batched_set_parallel(64, seed=seed)
     mats = list(mats) + [I.rmat_full(), I.cached_csr(f"rmat20_{seed}", lambda: I.rmat(seed=seed))]
     g = I.rng(seed, 300)
-    X = [I.to_f32(g.uniform(-1, 1, (8, a.n))) for a in mats]
+    X = []
+    for a in mats:   # page-locked inputs, as a serving front end would hold them
+        xa = M.native.pinned_empty((8, a.n))
+        xa[:] = I.to_f32(g.uniform(-1, 1, (8, a.n)))
+        X.append(xa)
     S = M.Server(budget_bytes=60 << 30, arena_bytes=256 << 20, contexts=4,
                  max_items=512, device=dev.index or 0)
     ids = [S.register(a) for a in mats]
@@ -460,7 +464,7 @@ def run_serving(M, args, dev):
         with lock:
             y = pools[j].pop() if pools[j] else None
         if y is None:
-            y = np.empty(8 * mats[j].m, np.float32)
+            y = M.native.pinned_empty((8 * mats[j].m,))
         t = S.submit(ids[j], X[j][:k], y)
         q.put((j, t))
     sent = time.perf_counter() - t0

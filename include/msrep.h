@@ -307,7 +307,9 @@ msrep_status msrep_serve_unregister(msrep_server *s, int64_t matrix_id);
 
 /* Queues y_v = A x_v for v = 0..k-1 (x_host: k vectors of n floats, one
  * after the other; y_host: k vectors of m floats); both host buffers stay
- * owned by the caller and must live until the request completes.  Does not
+ * owned by the caller and must live until the request completes; page-
+ * locked buffers (cudaMallocHost / cudaHostRegister) are transferred by DMA
+ * directly, others through the server's staging buffers.  Does not
  * block.  The request joins a launch as soon as a context and arena space
  * are free (continuous batching).  Errors: NOT_FOUND, INVALID_ARG (k out
  * of range), SHUTDOWN. */

@@ -56,6 +56,7 @@ struct Request {
   const float *x;
   float *y;
   Clock::time_point t_submit;
+  bool x_pinned = false, y_pinned = false;  // page-locked: DMA directly
   bool done = false;
   msrep_status status = MSREP_OK;
 };
@@ -146,7 +147,13 @@ static msrep_status launch_context(msrep_server *s, Context &c,
   for (auto &r : c.reqs) {
     c.y_off.push_back(yo);
     const BatchItem &bi = items[item];
-    std::memcpy(c.x_pin + xo, r->x, sizeof(float) * size_t(bi.n) * r->k);
+    const size_t xb = sizeof(float) * size_t(bi.n) * r->k;
+    if (r->x_pinned) {
+      MSREP_CUDA_TRY(cudaMemcpyAsync(c.x_dev + xo, r->x, xb, cudaMemcpyHostToDevice, c.stream));
+    } else {
+      std::memcpy(c.x_pin + xo, r->x, xb);
+      MSREP_CUDA_TRY(cudaMemcpyAsync(c.x_dev + xo, c.x_pin + xo, xb, cudaMemcpyHostToDevice, c.stream));
+    }
     for (int v = 0; v < r->k; ++v, ++item) {
       it[item] = items[item];
       toff[item] = tt;
@@ -161,7 +168,6 @@ static msrep_status launch_context(msrep_server *s, Context &c,
   const size_t dir_used = align256(sizeof(BatchItem) * s->cfg.max_items) +
                           align256(sizeof(int64_t) * (s->cfg.max_items + 1)) +
                           2 * align256(sizeof(void *) * s->cfg.max_items);
-  MSREP_CUDA_TRY(cudaMemcpyAsync(c.x_dev, c.x_pin, sizeof(float) * xo, cudaMemcpyHostToDevice, c.stream));
   MSREP_CUDA_TRY(cudaMemcpyAsync(c.dir_dev, c.dir_pin, dir_used, cudaMemcpyHostToDevice, c.stream));
   const char *dd = c.dir_dev;
   size_t q = align256(sizeof(BatchItem) * s->cfg.max_items);
@@ -172,7 +178,13 @@ static msrep_status launch_context(msrep_server *s, Context &c,
   void *const *dys = reinterpret_cast<void *const *>(dd + q);
   MSREP_TRY(launch_batched(reinterpret_cast<const BatchItem *>(dd), dtoff, cnt, tt, MSREP_F32,
                            dxs, dys, c.head, c.tail, 1.0, 0.0, 0, c.stream));
-  MSREP_CUDA_TRY(cudaMemcpyAsync(c.y_pin, c.y_dev, sizeof(float) * yo, cudaMemcpyDeviceToHost, c.stream));
+  for (size_t i = 0; i < c.reqs.size(); ++i) {
+    const auto &r = c.reqs[i];
+    const int64_t ylen = (i + 1 < c.reqs.size() ? c.y_off[i + 1] : yo) - c.y_off[i];
+    float *dst = r->y_pinned ? r->y : c.y_pin + c.y_off[i];
+    MSREP_CUDA_TRY(cudaMemcpyAsync(dst, c.y_dev + c.y_off[i], sizeof(float) * ylen,
+                                   cudaMemcpyDeviceToHost, c.stream));
+  }
   MSREP_CUDA_TRY(cudaEventRecord(c.done_ev, c.stream));
   return MSREP_OK;
 }
@@ -279,7 +291,7 @@ static void completion_loop(msrep_server *s) {
           std::lock_guard<std::mutex> lk(s->mu);
           m = s->mats[r->matrix].m;
         }
-        if (q == cudaSuccess)
+        if (q == cudaSuccess && !r->y_pinned)
           std::memcpy(r->y, c.y_pin + c.y_off[i], sizeof(float) * size_t(m) * r->k);
       }
       const auto now = Clock::now();
@@ -494,6 +506,13 @@ msrep_status msrep_serve_submit(msrep_server *s, int64_t id, int32_t k, const fl
   r->x = x;
   r->y = y;
   r->t_submit = Clock::now();
+  {
+    // page-locked caller buffers are copied by DMA without a staging copy
+    cudaPointerAttributes at;
+    r->x_pinned = cudaPointerGetAttributes(&at, x) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    r->y_pinned = cudaPointerGetAttributes(&at, y) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+  }
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) return fail(MSREP_ERR_SHUTDOWN, "server is stopping");
   auto it = s->mats.find(id);

@@ -471,7 +471,15 @@ class ServeTicket:
 
     @property
     def result(self) -> np.ndarray:
-        return self.y.reshape(self.k, self.m)
+        return self.y[: self.k * self.m].reshape(self.k, self.m)
+
+
+def pinned_empty(shape, dtype=np.float32) -> np.ndarray:
+    """A page-locked host numpy array (the server DMAs these directly)."""
+    import torch
+    t = torch.empty(int(np.prod(shape)), dtype=torch.from_numpy(np.empty(0, dtype)).dtype,
+                    pin_memory=True)
+    return t.numpy().reshape(shape)
 
 
 class Server:
