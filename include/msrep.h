@@ -328,6 +328,37 @@ msrep_status msrep_serve_stats(msrep_server *s, msrep_serve_counters *out, int32
 /* Stops the threads after finishing queued work, frees everything. */
 msrep_status msrep_serve_destroy(msrep_server *s);
 
+/* ---------------------------------------------------------------------- */
+/* SpMV without any allocation (the paper has no counterpart).            */
+/* ---------------------------------------------------------------------- */
+
+/* Bytes of the library's built-in scratch array: every GPU that loads the
+ * library holds this much device memory until the process exits. */
+#define MSREP_NOALLOC_SCRATCH_BYTES (1u << 20)
+
+/* Same result as msrep_spmv, for callers that cannot allocate device
+ * memory: code that only receives the matrix and vector buffers from a host
+ * framework which owns all device memory, or a latency-critical loop where
+ * a cudaMalloc is not acceptable.  Instead of a caller workspace it uses
+ * one scratch array compiled into the library (MSREP_NOALLOC_SCRATCH_BYTES,
+ * a static device array), so this call allocates nothing.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (with that device current) and caches it; make
+ *    that first call before any stream capture.
+ *  - Problems whose workspace (msrep_spmv_workspace_size) exceeds the
+ *    array are rejected with MSREP_ERR_WORKSPACE and nothing is queued; for
+ *    CSR and COO that is about 65,000 tiles (e.g. m + nnz up to about 64
+ *    million at tile 1024); CSC with FP32/BF16 values needs m doubles.
+ *  - Every call shares the one array and leaves its contents behind: two
+ *    calls whose work overlaps on the GPU (different streams, or several
+ *    host threads) race on it and give wrong results; serialise them.
+ *    Nothing in the array needs to start at zero: each call writes every
+ *    value it later reads.
+ * Arguments and errors as for msrep_spmv, minus the workspace. */
+msrep_status msrep_spmv_noalloc(const msrep_matrix *A, const msrep_partition *part,
+                                double alpha, const void *x, double beta, void *y,
+                                int32_t xy_dtype, unsigned flags, void *stream);
+
 /* Host; syncs `stream`.  Reads and clears the device error word that the
  * streaming kernels set when a bounded wait on one of their bulk copies
  * expires (which means the copy engine stalled or an argument was wrong).

@@ -1,0 +1,67 @@
+// msrep_spmv_noalloc: msrep_spmv with its workspace taken from a scratch
+// array compiled into the library, for callers that cannot allocate device
+// memory (see include/msrep.h).  The SpMV itself is msrep_spmv unchanged.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace msrep {
+
+// The scratch array: one per GPU that loads the library, alive until exit.
+// Host code must not take its address directly (on the host the name is
+// only a stand-in); the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[MSREP_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[128] = {nullptr};
+
+// Device address of the scratch array on the current device, looked up on
+// the first call with that device current and cached afterwards.
+static msrep_status noalloc_scratch(void **out) {
+  int dev = 0;
+  MSREP_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(MSREP_ERR_CUDA, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(MSREP_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return MSREP_OK;
+}
+
+}  // namespace msrep
+
+using namespace msrep;
+
+extern "C" {
+
+msrep_status msrep_spmv_workspace_size(const msrep_matrix *A, const msrep_partition *part,
+                                       size_t *bytes);
+msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part, double alpha,
+                        const void *x, double beta, void *y, int32_t xy_dtype, unsigned flags,
+                        void *workspace, void *stream);
+
+msrep_status msrep_spmv_noalloc(const msrep_matrix *A, const msrep_partition *part,
+                                double alpha, const void *x, double beta, void *y,
+                                int32_t xy_dtype, unsigned flags, void *stream) {
+  size_t need = 0;
+  MSREP_TRY(msrep_spmv_workspace_size(A, part, &need));
+  if (need > MSREP_NOALLOC_SCRATCH_BYTES)
+    return fail(MSREP_ERR_WORKSPACE,
+                "this SpMV needs %zu bytes of scratch; the built-in array holds %u "
+                "(use msrep_spmv with a caller workspace, or a larger tile)",
+                need, MSREP_NOALLOC_SCRATCH_BYTES);
+  void *scratch = nullptr;
+  MSREP_TRY(noalloc_scratch(&scratch));
+  return msrep_spmv(A, part, alpha, x, beta, y, xy_dtype, flags, scratch, stream);
+}
+
+}  // extern "C"

@@ -105,6 +105,8 @@ SIGNATURES = {
     "msrep_spmv": (ctypes.c_int, [_M, _P, ctypes.c_double, _vp, ctypes.c_double,
                                   _vp, ctypes.c_int32, ctypes.c_uint, _vp, _vp]),
     "msrep_profile_events": (ctypes.c_int, [_vp, _vp]),
+    "msrep_spmv_noalloc": (ctypes.c_int, [_M, _P, ctypes.c_double, _vp, ctypes.c_double,
+                                          _vp, ctypes.c_int32, ctypes.c_uint, _vp]),
     "msrep_device_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "msrep_tune_default": (ctypes.c_int, [ctypes.POINTER(c_msrep_tune_table)]),
     "msrep_batch_plan_size": (ctypes.c_int, [ctypes.c_int32, _M,
@@ -351,6 +353,18 @@ def msrep_spmv(A: DeviceMatrix, part: DevicePartition, alpha: float, x,
     _check(lib().msrep_spmv(ctypes.byref(A.c), ctypes.byref(part.c),
                             float(alpha), _ptr(x), float(beta), _ptr(y), xy,
                             flags, _ptr(workspace), _stream(stream)))
+
+
+def msrep_spmv_noalloc(A: DeviceMatrix, part: DevicePartition, alpha: float, x,
+                       beta: float, y, flags: int = 0, stream=None):
+    """msrep_spmv without a workspace: the library's built-in scratch array
+    is used instead, so nothing is allocated (see include/msrep.h for the
+    size limit and the rule that such calls must not overlap)."""
+    import torch
+    xy = MSREP_F64 if y.dtype == torch.float64 else MSREP_F32
+    _check(lib().msrep_spmv_noalloc(ctypes.byref(A.c), ctypes.byref(part.c), float(alpha),
+                                    _ptr(x), float(beta), _ptr(y), xy, flags,
+                                    _stream(stream)))
 
 
 def msrep_profile_events(start=None, stop=None):

@@ -1,0 +1,54 @@
+"""msrep_spmv_noalloc: the SpMV entry point that allocates nothing.
+
+Some callers cannot allocate device memory: code that only receives the
+matrix and vector buffers from a host framework that owns all device memory,
+or a loop where a cudaMalloc is not acceptable.  For them the library offers
+msrep_spmv_noalloc, which takes its scratch from an array compiled into the
+library instead of a caller workspace.  These tests call it through the C ABI
+and check it against msrep_spmv (with an allocated workspace) on the same
+inputs, on two calls in a row, since the calls share and reuse that array.
+The file is named to be collected last."""
+import numpy as np
+import pytest
+
+from helpers import normwise
+from paper_2209_07552_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.mark.parametrize("fmt", ["csr", "coo"])
+def test_noalloc_matches_workspace_entry_point_twice(fmt):
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    a = I.rmat(scale=14, nnz=200_000, seed=61)
+    A = M.DeviceMatrix.from_host(a, fmt, "f64")
+    part = M.DevicePartition(A, 148)
+    M.msrep_partition(A, part)
+    ws = M.alloc_workspace(A, part)
+    for call in range(2):
+        x = torch.from_numpy(I.vector(a.n, 62 + call)).cuda()
+        y_ref = torch.empty(a.m, dtype=torch.float64, device="cuda")
+        M.msrep_spmv(A, part, 1.0, x, 0.0, y_ref, workspace=ws)
+        y = torch.full((a.m,), float("nan"), dtype=torch.float64, device="cuda")
+        M.native.msrep_spmv_noalloc(A, part, 1.0, x, 0.0, y)
+        torch.cuda.synchronize()
+        assert normwise(y.cpu().numpy(), y_ref.cpu().numpy()) <= TOL64
+
+
+def test_noalloc_rejects_problems_larger_than_its_scratch():
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    a = I.laplace_full()                   # 25.2 million rows + nonzeros
+    A = M.DeviceMatrix.from_host(a, "csr", "f64")
+    part = M.DevicePartition(A, 148, tile=256)  # about 98,000 tiles
+    x = torch.zeros(a.n, dtype=torch.float64, device="cuda")
+    y = torch.zeros(a.m, dtype=torch.float64, device="cuda")
+    with pytest.raises(M.MsrepError) as e:
+        M.native.msrep_spmv_noalloc(A, part, 1.0, x, 0.0, y)
+    assert e.value.status == 9             # MSREP_ERR_WORKSPACE
+    assert "scratch" in str(e.value)
