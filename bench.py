@@ -299,7 +299,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded R-MAT and 2D Laplacian)",
         "config": {"workload": "rmat20_16Mnnz+laplace2048", "formats": list(FORMATS),
-                   "P": P, "tile": args.tile or 2048, "alpha": 1.0, "beta": 0.0,
+                   "P": P, "tile": args.tile or 1024, "alpha": 1.0, "beta": 0.0,
                    "l2": "inputs larger than L2 (each matrix 222-403 MB); no flush",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roof,
@@ -550,11 +550,11 @@ def run_profile_case(args):
     x = torch.from_numpy(I.vector(a.n, I.SEED_BASE + 1)).to(dev, xt)
     y = torch.empty(a.m, dtype=xt, device=dev)
     ws = M.alloc_workspace(A, part, device=dev)
-    flags = 0 if args.direct else M.MSREP_STREAM_TMA
+    flags = M.MSREP_STREAM_TMA if args.stream_tma else 0
     for _ in range(args.reps):
         M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_case": args.profile, "direct": args.direct, "matrix": args.profile_matrix,
+    print(json.dumps({"profile_case": args.profile, "stream_tma": args.stream_tma, "matrix": args.profile_matrix,
                       "dtype": dt, "reps": args.reps, "P": args.P,
                       "y_norm": float(torch.linalg.norm(y.double()))}))
 
@@ -623,7 +623,8 @@ def main():
     ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")
     ap.add_argument("--profile-dtype", choices=["f64", "f32", "bf16"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
-    ap.add_argument("--direct", action="store_true", help="direct-load kernels (profile case)")
+    ap.add_argument("--stream-tma", action="store_true",
+                    help="bulk-copy staging kernels (MSREP_STREAM_TMA) in the profile case")
     ap.add_argument("--sweep", action="store_true", help="time every (format, tile, P)")
     ap.add_argument("--sweep-formats", default="csr,csc,coo")
     ap.add_argument("--sweep-tiles", default="256,512,1024")
