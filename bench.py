@@ -124,6 +124,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(value: float) -> float:
+    """Largest `value` over all ranks of the default process group (the
+    bench reports the slowest rank's step time); the value itself when no
+    group is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -266,11 +280,10 @@ def run_ours(args):
             kern[f"{name}/{fmt}"] = {"kernel_us": 1e3 * tot / reps,
                                      "call_us": 1e3 * e0.elapsed_time(e1) / reps,
                                      "bytes": nb, "nnz": nnz}
-    ms_step = ev0.elapsed_time(ev1) / args.steps
     if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
     value = flops_step * world / (ms_step * 1e-3) / 1e9
 
     # roofline of the dominant kernel (largest kernel time in the step)
@@ -299,9 +312,10 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded R-MAT and 2D Laplacian)",
         "config": {"workload": "rmat20_16Mnnz+laplace2048", "formats": list(FORMATS),
-                   "P": P, "tile": args.tile or 1024, "alpha": 1.0, "beta": 0.0,
+                   "P": P, "tile": args.tile or 512, "alpha": 1.0, "beta": 0.0,
                    "l2": "inputs larger than L2 (each matrix 222-403 MB); no flush",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                   "parallelism": (f"{world} replicas, one per GPU, no data-path collective"
+                        if world > 1 else "single GPU")},
         "roofline": roof,
         "per_kernel": kern,
         "partition_ms": part_ms,

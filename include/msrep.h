@@ -219,7 +219,7 @@ typedef struct {
   int64_t toff_off;
 } msrep_batch;
 
-/* Host only: the library's default table (tile 1024, one partition). */
+/* Host only: the library's default table (default tile, one partition). */
 msrep_status msrep_tune_default(msrep_tune_table *tune);
 
 /* Host only: device bytes msrep_batch_prepare needs for As[0..count). */
@@ -347,8 +347,8 @@ msrep_status msrep_serve_destroy(msrep_server *s);
  *    that first call before any stream capture.
  *  - Problems whose workspace (msrep_spmv_workspace_size) exceeds the
  *    array are rejected with MSREP_ERR_WORKSPACE and nothing is queued; for
- *    CSR and COO that is about 65,000 tiles (e.g. m + nnz up to about 64
- *    million at tile 1024); CSC with FP32/BF16 values needs m doubles.
+ *    CSR and COO that is about 65,000 tiles (e.g. m + nnz up to about 32
+ *    million at the default tile of 512); CSC with FP32/BF16 values needs m doubles.
  *  - Every call shares the one array and leaves its contents behind: two
  *    calls whose work overlaps on the GPU (different streams, or several
  *    host threads) race on it and give wrong results; serialise them.

@@ -49,7 +49,7 @@ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // A tile is 32 * IPT merge-path items (rows + nonzeros for CSR/CSC,
 // nonzeros for COO), processed by one warp.  The supported shapes are
 // instantiated in spmv.cu.
-constexpr int kDefaultTile = 1024;
+constexpr int kDefaultTile = 512;
 inline bool tile_supported(int t) {
   return t == 256 || t == 512 || t == 1024;
 }

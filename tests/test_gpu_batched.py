@@ -44,7 +44,7 @@ def _tuned(tune, nnz):
     b = 0
     while b + 1 < 32 and (1 << (b + 1)) <= nnz:
         b += 1
-    tile = tune.tile[b] or 1024
+    tile = tune.tile[b] or 512
     pn = tune.part_nnz[b]
     return (max(1, -(-nnz // pn)) if pn > 0 else 1), tile
 
@@ -123,5 +123,5 @@ def test_batched_graph_capture_replay():
         g.replay()
         torch.cuda.synchronize()
         for a, v, y in zip(mats, new, Y):
-            want = _solo(M, a, "f32", v, 1, 1024)
+            want = _solo(M, a, "f32", v, 1, 512)
             assert np.array_equal(y.cpu().numpy(), want)
