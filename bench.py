@@ -65,7 +65,7 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons (every 200 ms)."""
+    """nvidia-smi samples of SM clock and throttle reasons (every 100 ms)."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,"
@@ -82,7 +82,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -136,6 +136,80 @@ def max_over_ranks(value: float) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.json")
+_UNIT = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9,
+         "nsecond": 1e-9, "usecond": 1e-6, "msecond": 1e-3, "second": 1.0,
+         "ns": 1e-9, "us": 1e-6, "ms": 1e-3}
+
+
+def source_stamp() -> str:
+    """Hash of the CUDA sources, the public header and the code-generation
+    flags of libmsrep.so (independent of where the repository lives)."""
+    import hashlib
+    from paper_2209_07552_gb300 import build as B
+    h = hashlib.sha1(" ".join(B.ARCH + [f for f in B.NVCC_FLAGS if not f.startswith("-I")]).encode())
+    for d in (B.CSRC, B.INCLUDE):
+        for name in sorted(os.listdir(d)):
+            path = os.path.join(d, name)
+            if os.path.isfile(path) and name.endswith((".cu", ".cuh", ".cpp", ".h")):
+                h.update(name.encode())
+                with open(path, "rb") as f:
+                    h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(key: str):
+    """DRAM bytes (read + write) of one launch of the main kernel of `key`
+    ("matrix/format"), from the committed ncu record; None when there is no
+    record or the kernels have changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get("kernels", {}).get(key)
+    if e is None or e.get("source_stamp") != source_stamp():
+        return None
+    return e["dram_read_bytes"] + e["dram_write_bytes"]
+
+
+def record_traffic(csv_path: str, key: str, command: str) -> dict:
+    """Adds the DRAM bytes per launch measured by an ncu capture (CSV from
+    `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
+    gpu__time_duration.sum --csv --log-file ...`) to the traffic record,
+    stamped with the current kernel sources.  With several captured launches
+    the last one counts."""
+    import csv
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    per = {}
+    name = None
+    for r in csv.DictReader(lines):
+        v = float(r["Metric Value"].replace(",", ""))
+        v *= _UNIT.get(r["Metric Unit"].strip().lower(), 1.0)
+        per.setdefault(r["ID"], {})[r["Metric Name"]] = v
+        name = r["Kernel Name"]
+    last = per[max(per, key=int)]
+    entry = {"kernel": name.split("(")[0] if name else None,
+             "dram_read_bytes": last["dram__bytes_read.sum"],
+             "dram_write_bytes": last["dram__bytes_write.sum"],
+             "duration_us_under_ncu": last.get("gpu__time_duration.sum", 0.0) * 1e6,
+             "source_stamp": source_stamp(), "command": command}
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        d = {"note": "DRAM bytes per launch of each main SpMV kernel, from one ncu "
+                     "capture of the profile case; a record counts only while its "
+                     "source_stamp matches the kernel sources.", "kernels": {}}
+    d["kernels"][key] = entry
+    os.makedirs(os.path.dirname(TRAFFIC_FILE), exist_ok=True)
+    with open(TRAFFIC_FILE, "w") as f:
+        json.dump(d, f, indent=1, sort_keys=True)
+        f.write("\n")
+    return entry
 
 
 def dist_env():
@@ -261,7 +335,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         # per-kernel timing of the main SpMV kernels (profiling events)
         kern = {}
-        reps = max(5, args.steps)
+        reps = max(20, min(args.steps, 200))
         for (name, fmt, A, part, x, y, ws, nnz, nb) in pairs:
             s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             M.native.msrep_profile_events(s0, s1)
@@ -293,7 +367,7 @@ def run_ours(args):
     achieved = d["bytes"] / (d["kernel_us"] * 1e-6) / 1e9
     roof = {"bound": "hbm", "kernel": dom_key, "achieved": achieved, "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None}
+            "traffic": recorded_traffic(dom_key)}
     for k, v in kern.items():
         v["gbs"] = v["bytes"] / (v["kernel_us"] * 1e-6) / 1e9
         v["frac"] = v["gbs"] / peak
@@ -320,8 +394,9 @@ def run_ours(args):
         "per_kernel": kern,
         "partition_ms": part_ms,
         "e2e": e2e,
-        # CSR and COO: main kernel + fix-up kernel; CSC (beta = 0): memset + main kernel
-        "gpu_launches": args.steps * sum(2 if p[1] != "csc" else 1 for p in pairs),
+        # CSR and COO: main kernel + fix-up kernel; CSC: prepare (zero y or
+        # the permuted accumulator) + main kernel + gather of y
+        "gpu_launches": args.steps * sum(2 if p[1] != "csc" else 3 for p in pairs),
         "clocks": clk.summary(),
     }
     if prec:
@@ -619,7 +694,7 @@ def run_sweep(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--P", type=int, default=148 * 16)
@@ -639,12 +714,21 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--stream-tma", action="store_true",
                     help="bulk-copy staging kernels (MSREP_STREAM_TMA) in the profile case")
+    ap.add_argument("--record-traffic", metavar="NCU_CSV", default=None,
+                    help="store the DRAM bytes of an ncu capture of the profile case "
+                         "(--profile, --profile-matrix select the key)")
+    ap.add_argument("--record-command", default="",
+                    help="the ncu command line that wrote NCU_CSV (kept with the record)")
     ap.add_argument("--sweep", action="store_true", help="time every (format, tile, P)")
     ap.add_argument("--sweep-formats", default="csr,csc,coo")
     ap.add_argument("--sweep-tiles", default="256,512,1024")
     ap.add_argument("--sweep-P", default="148,2368")
     ap.add_argument("--sweep-direct-only", action="store_true")
     args = ap.parse_args()
+    if args.record_traffic:
+        key = f"{args.profile_matrix}/{args.profile or 'csr'}"
+        print(json.dumps({key: record_traffic(args.record_traffic, key, args.record_command)}))
+        return
     if args.sweep:
         run_sweep(args)
         return

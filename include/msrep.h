@@ -142,7 +142,13 @@ msrep_status msrep_plan_size(const msrep_matrix *A, int32_t np, int32_t tile,
 msrep_status msrep_partition_csr(const msrep_matrix *A, msrep_partition *part,
                                  unsigned flags, void *stream);
 
-/* CSC -> pCSC, Alg. 4 (Sec. 3.2.2): Alg. 2 over col_ptr. */
+/* CSC -> pCSC, Alg. 4 (Sec. 3.2.2): Alg. 2 over col_ptr.  With a plan, it
+ * also records up to four hub rows (rows holding about 0.1% or more of the
+ * nonzeros, found from 4096 evenly spaced samples of row_idx): msrep_spmv
+ * sums their products privately per thread block instead of with one
+ * atomic add per nonzero on the same y entry.  The result is the same up
+ * to the order of FP64 additions, which CSC's atomic scatter leaves open
+ * anyway. */
 msrep_status msrep_partition_csc(const msrep_matrix *A, msrep_partition *part,
                                  unsigned flags, void *stream);
 
@@ -154,7 +160,10 @@ msrep_status msrep_partition_csc(const msrep_matrix *A, msrep_partition *part,
 msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *part,
                                  unsigned flags, void *stream);
 
-/* Host only.  Device workspace bytes msrep_spmv needs for (A, part). */
+/* Host only.  Device workspace bytes msrep_spmv needs for (A, part): two
+ * FP64 partials per tile, and for CSC an FP64 accumulator of 2^k >= m
+ * entries (the permuted accumulator of matrices with hub rows, see
+ * msrep_partition_csc; the low-precision path also accumulates there). */
 msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
                                        const msrep_partition *part,
                                        size_t *bytes);
@@ -179,8 +188,10 @@ msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
  * Merge: every row split by a partition (or tile) boundary gets
  * alpha * (sum of its partials, in partition order) + beta * y_in, beta
  * applied once (Sec. 3.2.1, Sec. 4.3).  CSR and COO merge without atomics;
- * CSC scatters into y with atomic adds (the column merge of Alg. 5), so its
- * rounding order varies from run to run.
+ * CSC scatters with atomic adds (the column merge of Alg. 5), so its
+ * rounding order varies from run to run; when the plan found hub rows it
+ * scatters into a permuted accumulator in the workspace (which spreads the
+ * hub rows' cache lines over all L2 slices) and gathers y from it after.
  * `workspace` must hold msrep_spmv_workspace_size() bytes, 16-byte
  * aligned.  idx, idx2 and val must be 32-byte aligned and ptr 16-byte
  * aligned (the kernels bulk-copy them in aligned segments and read groups
@@ -345,10 +356,13 @@ msrep_status msrep_serve_destroy(msrep_server *s);
  *  - The first call on a device looks up the array's device address with
  *    cudaGetSymbolAddress (with that device current) and caches it; make
  *    that first call before any stream capture.
- *  - Problems whose workspace (msrep_spmv_workspace_size) exceeds the
- *    array are rejected with MSREP_ERR_WORKSPACE and nothing is queued; for
- *    CSR and COO that is about 65,000 tiles (e.g. m + nnz up to about 32
- *    million at the default tile of 512); CSC with FP32/BF16 values needs m doubles.
+ *  - Problems whose workspace exceeds the array are rejected with
+ *    MSREP_ERR_WORKSPACE and nothing is queued; for CSR and COO that is
+ *    about 65,000 tiles (e.g. m + nnz up to about 32 million at the default
+ *    tile of 512); CSC with FP32/BF16 values also needs m doubles.  A CSC
+ *    SpMV whose permuted accumulator does not fit scatters into y directly
+ *    (same result up to the order of additions, slower on matrices with hub
+ *    rows). 
  *  - Every call shares the one array and leaves its contents behind: two
  *    calls whose work overlaps on the GPU (different streams, or several
  *    host threads) race on it and give wrong results; serialise them.

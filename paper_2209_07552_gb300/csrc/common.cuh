@@ -62,10 +62,47 @@ inline bool tile_supported(int t) {
 //   int32  tile_off[np+1] first tile of each partition; tile_off[np] = T
 //   int32  tile_row[Tmax+1], tile_k[Tmax+1]  tile start coordinates; the
 //                         entry after the last tile is (n_major, nnz).
+//   int32  hot[1+kMaxHot] CSC only: count, then the hub rows (-1 = none)
 struct PlanLayout {
   int64_t tmax;
-  size_t off_D, off_R, off_toff, off_row, off_k, bytes;
+  size_t off_D, off_R, off_toff, off_row, off_k, off_hot, bytes;
 };
+
+// Hub rows of a CSC matrix: rows holding a large share of the nonzeros, so
+// that their atomic adds to one y entry serialise in L2.  At most kMaxHot
+// of them are found at partition time, from kHotSample evenly spaced
+// nonzeros; a row needs at least kHotMin samples (about 0.1% of the
+// nonzeros) to qualify.
+constexpr int kMaxHot = 4;
+constexpr int kHotSample = 4096;
+constexpr int kHotMin = 4;
+
+// When a CSC matrix has hub rows, its scatter accumulates into a workspace
+// vector whose entry for row r is slot(r) = (r * kPermMul) mod 2^k, a
+// bijection of [0, 2^k) for the odd multiplier, with 2^k >= m (perm_extent).
+// A power-law matrix's heavy rows crowd a few cache lines of y (in the R-MAT
+// workload the rows 0..15 of one 128-byte line take 150,000 atomic adds), so
+// the L2 slices holding those lines serialise the scatter; the permuted
+// layout spreads them over all slices.  y is gathered back afterwards.
+constexpr uint32_t kPermMul = 0x9E3779B1u;
+inline int64_t perm_extent(int64_t m) {
+  int64_t e = 1;
+  while (e < m) e <<= 1;
+  return e;
+}
+__host__ __device__ __forceinline__ uint32_t perm_slot(int32_t r, uint32_t mask) {
+  return (static_cast<uint32_t>(r) * kPermMul) & mask;
+}
+
+// Internal entry of msrep_spmv.  perm_ok: the workspace holds the permuted
+// CSC accumulator (msrep_spmv_workspace_size counts it); without it a CSC
+// SpMV scatters into y directly (msrep_spmv_noalloc when its scratch array
+// is too small for the accumulator).
+msrep_status spmv_workspace_bytes(const msrep_matrix *A, const msrep_partition *part,
+                                  bool perm_ok, size_t *bytes);
+msrep_status spmv_run(const msrep_matrix *A, const msrep_partition *part, double alpha,
+                      const void *x, double beta, void *y, int32_t xy_dtype, unsigned flags,
+                      void *workspace, void *stream, bool perm_ok);
 
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
@@ -80,6 +117,7 @@ inline PlanLayout plan_layout(int64_t n_major, int64_t nnz, int32_t np,
   L.off_toff = o; o = align256(o + sizeof(int32_t) * (np + 1));
   L.off_row = o;  o = align256(o + sizeof(int32_t) * (L.tmax + 1));
   L.off_k = o;    o = align256(o + sizeof(int32_t) * (L.tmax + 1));
+  L.off_hot = o;  o = align256(o + sizeof(int32_t) * (1 + kMaxHot));
   L.bytes = o;
   return L;
 }

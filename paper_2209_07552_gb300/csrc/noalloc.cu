@@ -1,6 +1,6 @@
 // msrep_spmv_noalloc: msrep_spmv with its workspace taken from a scratch
 // array compiled into the library, for callers that cannot allocate device
-// memory (see include/msrep.h).  The SpMV itself is msrep_spmv unchanged.
+// memory (see include/msrep.h).  The SpMV itself is msrep_spmv's.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -43,17 +43,16 @@ using namespace msrep;
 
 extern "C" {
 
-msrep_status msrep_spmv_workspace_size(const msrep_matrix *A, const msrep_partition *part,
-                                       size_t *bytes);
-msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part, double alpha,
-                        const void *x, double beta, void *y, int32_t xy_dtype, unsigned flags,
-                        void *workspace, void *stream);
-
 msrep_status msrep_spmv_noalloc(const msrep_matrix *A, const msrep_partition *part,
                                 double alpha, const void *x, double beta, void *y,
                                 int32_t xy_dtype, unsigned flags, void *stream) {
-  size_t need = 0;
-  MSREP_TRY(msrep_spmv_workspace_size(A, part, &need));
+  // The permuted CSC accumulator is used when it fits in the scratch array;
+  // otherwise a CSC SpMV scatters into y directly (same result up to the
+  // order of additions), so the limit below is the one without it.
+  size_t full = 0, need = 0;
+  MSREP_TRY(spmv_workspace_bytes(A, part, true, &full));
+  const bool perm_ok = full <= MSREP_NOALLOC_SCRATCH_BYTES;
+  MSREP_TRY(spmv_workspace_bytes(A, part, perm_ok, &need));
   if (need > MSREP_NOALLOC_SCRATCH_BYTES)
     return fail(MSREP_ERR_WORKSPACE,
                 "this SpMV needs %zu bytes of scratch; the built-in array holds %u "
@@ -61,7 +60,7 @@ msrep_status msrep_spmv_noalloc(const msrep_matrix *A, const msrep_partition *pa
                 need, MSREP_NOALLOC_SCRATCH_BYTES);
   void *scratch = nullptr;
   MSREP_TRY(noalloc_scratch(&scratch));
-  return msrep_spmv(A, part, alpha, x, beta, y, xy_dtype, flags, scratch, stream);
+  return spmv_run(A, part, alpha, x, beta, y, xy_dtype, flags, scratch, stream, perm_ok);
 }
 
 }  // extern "C"

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <unordered_map>
 
 #include "common.cuh"
@@ -59,8 +60,13 @@ int *kernel_err_ptr() {
 // direct variant keeps twice as many warps resident and all of L1 for x.
 // ---------------------------------------------------------------------------
 
+// Minimum resident blocks per SM asked of the register allocator for the
+// CSR and COO direct-load kernels: 3 (85 registers a thread, 24 warps per
+// SM) was measured fastest at the default tile of 512 on GB300 (R-MAT and
+// Laplacian CSR 108 / 99 us, COO 120 / 114 us; 1 block cap: 121 / 122 and
+// 125 / 134 us; 4: 112 / 95 and 127 / 121 us).
 #ifndef MSREP_MINB
-#define MSREP_MINB 1  // minimum resident blocks per SM asked of the register allocator
+#define MSREP_MINB 3
 #endif
 constexpr int kWarps = 8;  // warps per block; each warp owns whole tiles
 constexpr int kThreads = 32 * kWarps;
@@ -276,7 +282,9 @@ __global__ void __launch_bounds__(kThreads) coo_stream(CooArgs<Pol> a) {
 }
 
 template <class Pol, int IPT>
-__global__ void __launch_bounds__(kThreads, MSREP_MINB) csc_direct(CscArgs<Pol> a, const int32_t *n_tiles,
+// Four resident blocks (64 registers a thread) match the shared-memory
+// budget of the x and column-pointer stages.
+__global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
   // dynamic shared memory: per warp, x values then column pointers
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -285,16 +293,28 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) csc_direct(CscArgs<Pol> 
   double *s_x = reinterpret_cast<double *>(dsm) + wid * CAP;
   int32_t *s_cp = reinterpret_cast<int32_t *>(reinterpret_cast<double *>(dsm) + kWarps * CAP) +
                   wid * CAP;
-  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
-    const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
-    const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
-    const int32_t cend = min(c1 + 1, a.n + 1);
-    for (int32_t c = c0 + lane; c < cend; c += 32) s_cp[c - c0] = __ldg(a.col_ptr + c);
-    csc_stage_x(a, c0, c1, s_x);
-    __syncwarp();
-    csc_tile_compute<Pol>(a, c0, k0, c1, k1, s_cp, s_x, Seg<int32_t>{a.row_idx, 0},
-                          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{});
-    __syncwarp();
+  __shared__ double s_hot[kWarps][kMaxHot];
+  HotRows hot;
+  hot.load(a.hot, s_hot);
+  auto tiles = [&](auto with_hot) {
+    for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
+      const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
+      const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
+      const int32_t cend = min(c1 + 1, a.n + 1);
+      for (int32_t c = c0 + lane; c < cend; c += 32) s_cp[c - c0] = __ldg(a.col_ptr + c);
+      csc_stage_x(a, c0, c1, s_x);
+      __syncwarp();
+      csc_tile_compute<Pol, decltype(with_hot)::value>(
+          a, c0, k0, c1, k1, s_cp, s_x, Seg<int32_t>{a.row_idx, 0},
+          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{}, hot);
+      __syncwarp();
+    }
+  };
+  if (csc_skewed(a.hot, a.yperm)) {
+    tiles(std::true_type{});
+    hot.flush(a.yperm, a.pmask, s_hot);
+  } else {
+    tiles(std::false_type{});
   }
 }
 
@@ -339,6 +359,10 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
     if (r.bytes) bulk_g2s(row_s(s), a.row_idx + r.base, r.bytes, bar + s);
     if (v.bytes) bulk_g2s(val_s(s), a.val + v.base, v.bytes, bar + s);
   };
+  __shared__ double s_hot[kWarps][kMaxHot];
+  HotRows hot;
+  hot.load(a.hot, s_hot);
+  const bool skew = csc_skewed(a.hot, a.yperm);
   int4 pending = make_int4(0, 0, 0, 0);
   if (lane == 0) {
     for (int s = 0; s < S; ++s)
@@ -363,9 +387,14 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
     fill_tail(val_s(s), a.val, v, v.base, g_end);
     csc_stage_x(a, c.x, c.z, xs);
     __syncwarp();
-    csc_tile_compute<Pol>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xs,
-                          Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base}, nnz,
-                          SharedSrc{});
+    if (skew)
+      csc_tile_compute<Pol, true>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xs,
+                                  Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base},
+                                  nnz, SharedSrc{}, hot);
+    else
+      csc_tile_compute<Pol, false>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xs,
+                                   Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base},
+                                   nnz, SharedSrc{}, hot);
     __syncwarp();
     if (lane == 0 && b + S * W < T) {
       fence_proxy_async();
@@ -376,32 +405,61 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
   }
   if (!ok)
     for (int j = i + 1; j < i + S && first + j * W < T; ++j) mbar_wait(bar + j % S, (j / S) & 1, a.err);
+  if (skew) hot.flush(a.yperm, a.pmask, s_hot);
 }
 
 // ---------------------------------------------------------------------------
 // fix-up: rows split between tiles, merged in tile (= partition) order
 // ---------------------------------------------------------------------------
 
+// One warp per 32 consecutive tiles (grid-stride over warps).
 template <class X, class View>
 __global__ void fixup_split_rows(View v, const double *head, const double *tail,
                                  X *y, double alpha, double beta) {
   const int T = v.count();
-  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < T;
-       b += gridDim.x * blockDim.x)
-    fixup_tile(v, T, b, head, tail, y, alpha, beta);
+  const int64_t warp = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < T; base += nwarps * 32)
+    fixup_warp(v, T, static_cast<int>(base), head, tail, y, alpha, beta);
 }
 
-__global__ void scale_f64(double *y, int64_t m, double beta) {
-  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < m;
-       r += int64_t(gridDim.x) * blockDim.x)
-    y[r] = beta * y[r];
+// Before a CSC scatter: a skewed matrix zeroes the permuted accumulator
+// (beta is applied when y is gathered back); otherwise the row-ordered
+// target is prepared: y = beta * y on the FP64 path (nothing for beta = 1),
+// the FP64 accumulator zeroed on the low-precision path.
+__global__ void csc_prepare(const int32_t *hot, double *yperm, int64_t perm_n, double *yrow,
+                            int64_t m, double beta, int row_is_y) {
+  const int64_t i0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  const int64_t step = int64_t(gridDim.x) * blockDim.x;
+  if (csc_skewed(hot, yperm)) {
+    for (int64_t i = i0; i < perm_n; i += step) yperm[i] = 0.0;
+  } else if (!row_is_y || beta != 1.0) {
+    for (int64_t r = i0; r < m; r += step)
+      yrow[r] = (!row_is_y || beta == 0.0) ? 0.0 : __dmul_rn(beta, yrow[r]);
+  }
 }
 
-__global__ void finish_csc_f32(const double *yacc, float *y, int64_t m,
-                               double alpha, double beta) {
+// FP64 CSC, skewed matrix: y[r] = acc[slot(r)] + beta * y[r].
+__global__ void csc_unpermute(const int32_t *hot, const double *yperm, uint32_t pmask,
+                              double *y, int64_t m, double beta) {
+  if (!csc_skewed(hot, yperm)) return;
   for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < m;
        r += int64_t(gridDim.x) * blockDim.x) {
-    double v = alpha * yacc[r];
+    const double acc = yperm[perm_slot(static_cast<int32_t>(r), pmask)];
+    y[r] = beta == 0.0 ? acc : __dadd_rn(acc, __dmul_rn(beta, y[r]));
+  }
+}
+
+// Low-precision CSC: y = alpha * acc + beta * y in FP64, rounded to FP32
+// once; acc is read through the permutation for a skewed matrix.
+__global__ void finish_csc_f32(const int32_t *hot, const double *yperm, uint32_t pmask,
+                               const double *yacc, float *y, int64_t m, double alpha,
+                               double beta) {
+  const bool skew = csc_skewed(hot, yperm);
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < m;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    const double acc = skew ? yperm[perm_slot(static_cast<int32_t>(r), pmask)] : yacc[r];
+    double v = alpha * acc;
     if (beta != 0.0) v += beta * double(y[r]);
     y[r] = float(v);
   }
@@ -432,8 +490,18 @@ static int resident_blocks(K kernel, size_t smem) {
 }
 
 struct Workspace {
-  double *head, *tail, *yacc;
+  double *head, *tail, *yacc;  // yacc: the CSC accumulator (see csc_acc_len)
+  bool perm;                   // yacc is the permuted accumulator (CSC)
 };
+
+// Entries of the CSC accumulator in the workspace: the permuted accumulator
+// (perm_extent(m) entries, also used in row order by the low-precision
+// path) when perm_ok, else the low-precision path's row-ordered FP64 sums.
+static int64_t csc_acc_len(const msrep_matrix *A, bool perm_ok) {
+  if (A->fmt != MSREP_CSC) return 0;
+  if (perm_ok) return perm_extent(A->m);
+  return A->val_dtype == MSREP_F64 ? 0 : A->m;
+}
 
 static size_t ws_layout(int64_t tiles, int64_t m_acc, Workspace *w, void *base) {
   size_t o = 0;
@@ -596,23 +664,25 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   a.n = A->n;
   a.err = kernel_err_ptr();
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
+  a.hot = reinterpret_cast<const int32_t *>(plan + L.off_hot);
   const int64_t m = A->m;
   const int sg = 4 * sm_count();
+  const int64_t pn = w.perm ? perm_extent(m) : 0;
+  a.yperm = w.perm ? w.yacc : nullptr;
+  a.pmask = w.perm ? static_cast<uint32_t>(pn - 1) : 0u;
+  // y (or the accumulator) is prepared on the device, which alone knows
+  // whether the plan found hub rows
   if (kF64) {
     a.yacc = static_cast<double *>(y);
     a.scale = alpha;
     a.scaled = alpha != 1.0;
-    if (m > 0) {
-      if (beta == 0.0)
-        MSREP_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(double) * m, st));
-      else if (beta != 1.0)
-        scale_f64<<<sg, 256, 0, st>>>(a.yacc, m, beta);
-    }
+    if (w.perm || beta != 1.0)
+      csc_prepare<<<sg, 256, 0, st>>>(a.hot, a.yperm, pn, a.yacc, m, beta, 1);
   } else {
     a.yacc = w.yacc;
     a.scale = 1.0;
     a.scaled = false;
-    if (m > 0) MSREP_CUDA_TRY(cudaMemsetAsync(w.yacc, 0, sizeof(double) * m, st));
+    csc_prepare<<<sg, 256, 0, st>>>(a.hot, a.yperm, pn, w.yacc, m, 0.0, 0);
   }
   MSREP_CUDA_TRY(cudaGetLastError());
   MSREP_TRY(launch_tiles(csc_stream<Pol, IPT>, csc_direct<Pol, IPT>,
@@ -620,8 +690,15 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
                              sizeof(double) * kWarps * (32 * IPT + 8),
                          (sizeof(double) + sizeof(int32_t)) * kWarps * (32 * IPT + 8),
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
-  if (!kF64 && m > 0) {
-    finish_csc_f32<<<sg, 256, 0, st>>>(w.yacc, static_cast<float *>(y), m, alpha, beta);
+  if (kF64) {
+    if (w.perm) {
+      csc_unpermute<<<sg, 256, 0, st>>>(a.hot, a.yperm, a.pmask, static_cast<double *>(y), m,
+                                        beta);
+      MSREP_CUDA_TRY(cudaGetLastError());
+    }
+  } else {
+    finish_csc_f32<<<sg, 256, 0, st>>>(a.hot, a.yperm, a.pmask, w.yacc, static_cast<float *>(y),
+                                       m, alpha, beta);
     MSREP_CUDA_TRY(cudaGetLastError());
   }
   return MSREP_OK;
@@ -690,21 +767,35 @@ msrep_status msrep_profile_events(void *start, void *stop) {
 msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
                                        const msrep_partition *part,
                                        size_t *bytes) {
-  MSREP_TRY(check_matrix(A));
-  if (!part || part->np < 1 || !bytes)
-    return fail(MSREP_ERR_INVALID_ARG, "bad partition or bytes pointer");
-  const int32_t tile = effective_tile(part->tile);
-  if (!tile_supported(tile)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", part->tile);
-  const int64_t tiles = tiles_for(A, part, tile);
-  const int64_t m_acc = (A->fmt == MSREP_CSC && A->val_dtype != MSREP_F64) ? A->m : 0;
-  *bytes = ws_layout(tiles, m_acc, nullptr, nullptr);
-  return ok();
+  return spmv_workspace_bytes(A, part, true, bytes);
 }
 
 msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
                         double alpha, const void *x, double beta, void *y,
                         int32_t xy_dtype, unsigned flags, void *workspace,
                         void *stream) {
+  return spmv_run(A, part, alpha, x, beta, y, xy_dtype, flags, workspace, stream, true);
+}
+
+}  // extern "C"
+
+namespace msrep {
+
+msrep_status spmv_workspace_bytes(const msrep_matrix *A, const msrep_partition *part,
+                                  bool perm_ok, size_t *bytes) {
+  MSREP_TRY(check_matrix(A));
+  if (!part || part->np < 1 || !bytes)
+    return fail(MSREP_ERR_INVALID_ARG, "bad partition or bytes pointer");
+  const int32_t tile = effective_tile(part->tile);
+  if (!tile_supported(tile)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", part->tile);
+  const int64_t tiles = tiles_for(A, part, tile);
+  *bytes = ws_layout(tiles, csc_acc_len(A, perm_ok), nullptr, nullptr);
+  return ok();
+}
+
+msrep_status spmv_run(const msrep_matrix *A, const msrep_partition *part, double alpha,
+                      const void *x, double beta, void *y, int32_t xy_dtype, unsigned flags,
+                      void *workspace, void *stream, bool perm_ok) {
   MSREP_TRY(check_matrix(A));
   if (!part || part->np < 1 || !part->start_idx || !part->end_idx)
     return fail(MSREP_ERR_INVALID_ARG, "bad partition");
@@ -751,9 +842,9 @@ msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
   if (reinterpret_cast<uintptr_t>(workspace) & 15)
     return fail(MSREP_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
   const int64_t tiles = tiles_for(A, part, tile);
-  const int64_t m_acc = (A->fmt == MSREP_CSC && !f64) ? A->m : 0;
   Workspace w;
-  ws_layout(tiles, m_acc, &w, workspace);
+  ws_layout(tiles, csc_acc_len(A, perm_ok), &w, workspace);
+  w.perm = perm_ok && A->fmt == MSREP_CSC;
   msrep_status s;
   switch (A->val_dtype) {
     case MSREP_F64:
@@ -770,4 +861,5 @@ msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
   return ok();
 }
 
-}  // extern "C"
+}  // namespace msrep
+

@@ -566,21 +566,74 @@ struct CscArgs {
   const int32_t *row_idx;
   const typename Pol::V *val;
   const typename Pol::X *x;
-  double *yacc;
+  double *yacc;  // scatter target by row: y (FP64) or the FP64 accumulator
+  double *yperm;  // permuted accumulator (pmask + 1 entries), or null
+  uint32_t pmask;
   double scale;  // alpha on the FP64 path, 1 when a finishing pass follows
   bool scaled;   // scale != 1
   const int32_t *tile_row, *tile_k;
+  const int32_t *hot;  // hub rows: count, then kMaxHot rows (-1 = none)
   int32_t n;
   int *err;
 };
 
+// A skewed CSC matrix (hub rows found and a permuted accumulator given)
+// takes the hub-row sums and the permuted scatter.
+__device__ __forceinline__ bool csc_skewed(const int32_t *hot, const double *yperm) {
+  return yperm != nullptr && __ldg(hot) > 0;
+}
+
+// Private sums of the hub rows of a CSC matrix.  Every nonzero of a hub row
+// is an atomic add to the same y entry, and same-address atomics serialise
+// in L2 (about 40,000 of them on one row of the R-MAT workload cost some
+// 100 us).  A warp adds its products for the hub rows to its own slots in
+// shared memory instead (shared-memory atomics, rarely contended: hub
+// nonzeros are a small fraction of all); the block adds its slots to y once,
+// at the end.
+struct HotRows {
+  static_assert(kMaxHot == 4, "HotRows holds four rows");
+  int32_t r0, r1, r2, r3;
+  int n;
+  double *slot;  // this warp's kMaxHot sums in shared memory
+  __device__ __forceinline__ void load(const int32_t *hot, double (*s_hot)[kMaxHot]) {
+    n = __ldg(hot);
+    r0 = __ldg(hot + 1);
+    r1 = __ldg(hot + 2);
+    r2 = __ldg(hot + 3);
+    r3 = __ldg(hot + 4);
+    slot = s_hot[threadIdx.x >> 5];
+    if ((threadIdx.x & 31) < kMaxHot) slot[threadIdx.x & 31] = 0.0;
+    __syncwarp();
+  }
+  // adds v to the warp's sum of `row` if it is a hub row
+  __device__ __forceinline__ bool take(int32_t row, double v) {
+    const int j = row == r0 ? 0 : row == r1 ? 1 : row == r2 ? 2 : row == r3 ? 3 : -1;
+    if (j < 0) return false;
+    atomicAdd(slot + j, v);
+    return true;
+  }
+  // Called by every thread of the block after its last tile: adds the
+  // block's sums to the permuted accumulator.
+  __device__ __forceinline__ void flush(double *yperm, uint32_t pmask, double (*s_hot)[kMaxHot]) {
+    __syncthreads();
+    const int j = threadIdx.x;
+    const int32_t row = j == 0 ? r0 : j == 1 ? r1 : j == 2 ? r2 : j == 3 ? r3 : -1;
+    if (row >= 0) {
+      double t = 0.0;
+      for (int w = 0; w < static_cast<int>(blockDim.x >> 5); ++w) t = __dadd_rn(t, s_hot[w][j]);
+      atomicAdd(yperm + perm_slot(row, pmask), t);
+    }
+  }
+};
+
 // cp[j] = col_ptr[c0 + j], j = 0..c1-c0, and xs[j] = scale * x[c0 + j] for
 // the columns that hold nonzeros of the tile, both in shared memory.
-template <class Pol, class Src>
+template <class Pol, bool kSkew, class Src>
 __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t c0, int32_t k0,
                                                  int32_t c1, int32_t k1, const int32_t *cp,
                                                  const double *xs, Seg<int32_t> row,
-                                                 Seg<typename Pol::V> val, int64_t nnz, Src src) {
+                                                 Seg<typename Pol::V> val, int64_t nnz, Src src,
+                                                 HotRows &hot) {
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
   const int ncols = c1 - c0;
@@ -604,7 +657,12 @@ __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t 
         cend = c < ncols ? s_end[c] : INT32_MAX;
       }
       const double prod = __dmul_rn(double(v[u]), in ? xs[c] : 0.0);
-      if (in) atomicAdd(a.yacc + rw[u], prod);
+      if (in) {
+        if (!kSkew)
+          atomicAdd(a.yacc + rw[u], prod);
+        else if (!hot.take(rw[u], prod))
+          atomicAdd(a.yperm + perm_slot(rw[u], a.pmask), prod);
+      }
     }
   }
 }
@@ -658,33 +716,115 @@ struct CooTileView {
   }
 };
 
-// Merge of one row split between tiles (Sec. 3.2.1 / Sec. 4.3): the thread
-// of the first tile whose first row started earlier sums, in tile order, the
-// tail partial of the previous tile and the head partials of the run of
-// tiles that continue the row, then applies alpha and beta once, in FP64.
+// Merge of one row split between tiles (Sec. 3.2.1 / Sec. 4.3): the first
+// tile whose first row started earlier sums, in tile order, the tail partial
+// of the previous tile and the head partials of the run of tiles that
+// continue the row, then applies alpha and beta once, in FP64.
+
+// Is tile b the first of a run continuing row r from tile b - 1?
+template <class View>
+__device__ __forceinline__ bool fixup_run_start(const View &v, int T, int b, int32_t &r) {
+  if (b <= 0 || b >= T) return false;
+  bool f;
+  v.row_flag(b, r, f);
+  if (!f) return false;
+  int32_t rp;
+  bool fp;
+  v.row_flag(b - 1, rp, fp);
+  return !(fp && rp == r);  // else not the first flagged tile of the run
+}
+
+// Adds, in order, the head partials of tiles j0 .. j0+7 that continue row r
+// to s; returns how many continued it (8: the run may go on).  The flags
+// and partials of the 8 tiles are loaded together (a hub row spans dozens
+// of tiles; one dependent load chain per tile made the walk latency-bound).
+template <class View>
+__device__ __forceinline__ int fixup_chunk(const View &v, int T, int j0, int32_t r,
+                                           const double *head, double &s) {
+  int32_t rj[8];
+  bool fj[8];
+  double hj[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    fj[u] = false;
+    if (j0 + u < T) {
+      v.row_flag(j0 + u, rj[u], fj[u]);
+      hj[u] = head[j0 + u];
+    }
+  }
+  int run = 8;
+#pragma unroll
+  for (int u = 7; u >= 0; --u)
+    if (!(fj[u] && rj[u] == r)) run = u;
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    if (u < run) s += hj[u];
+  return run;
+}
+
+template <class X>
+__device__ __forceinline__ void fixup_write(X *y, int32_t r, double s, double alpha,
+                                            double beta) {
+  const double yo = beta == 0.0 ? 0.0 : double(y[r]);
+  y[r] = static_cast<X>(beta == 0.0 ? alpha * s : alpha * s + beta * yo);
+}
+
+// One thread, tile b.
 template <class X, class View>
 __device__ __forceinline__ void fixup_tile(const View &v, int T, int b, const double *head,
                                            const double *tail, X *y, double alpha,
                                            double beta) {
   int32_t r;
-  bool f;
-  v.row_flag(b, r, f);
-  if (!f || b == 0) return;
-  int32_t rp;
-  bool fp;
-  v.row_flag(b - 1, rp, fp);
-  if (fp && rp == r) return;  // not the first flagged tile of the run
+  if (!fixup_run_start(v, T, b, r)) return;
   double s = tail[b - 1];
-  for (int j = b; j < T; ++j) {
-    int32_t rj;
-    bool fj;
-    v.row_flag(j, rj, fj);
-    if (!fj || rj != r) break;
-    s += head[j];
+  for (int j0 = b; fixup_chunk(v, T, j0, r, head, s) == 8; j0 += 8) {
   }
-  double yo = beta == 0.0 ? 0.0 : double(y[r]);
-  y[r] = static_cast<X>(beta == 0.0 ? alpha * s : alpha * s + beta * yo);
+  fixup_write(y, r, s, alpha, beta);
 }
 
+// One warp, tiles base .. base+31 (one per lane).  A run longer than one
+// chunk is continued by the whole warp, 32 tiles per step, its partials
+// added in tile order by every lane, so the sum (and y) is bit-identical to
+// fixup_tile's.
+template <class X, class View>
+__device__ __forceinline__ void fixup_warp(const View &v, int T, int base, const double *head,
+                                           const double *tail, X *y, double alpha,
+                                           double beta) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int b = base + lane;
+  int32_t r = -1;
+  double s = 0.0;
+  bool more = false;
+  if (fixup_run_start(v, T, b, r)) {
+    s = tail[b - 1];
+    more = fixup_chunk(v, T, b, r, head, s) == 8;
+    if (!more) fixup_write(y, r, s, alpha, beta);
+  }
+  unsigned pend = __ballot_sync(full, more);
+  while (pend) {
+    const int src = __ffs(pend) - 1;
+    pend &= pend - 1;
+    const int32_t rr = __shfl_sync(full, r, src);
+    double ss = __shfl_sync(full, s, src);
+    for (int j0 = __shfl_sync(full, b, src) + 8;; j0 += 32) {
+      const int j = j0 + lane;
+      bool in = false;
+      double h = 0.0;
+      if (j < T) {
+        int32_t rj;
+        bool fj;
+        v.row_flag(j, rj, fj);
+        in = fj && rj == rr;
+        if (in) h = head[j];
+      }
+      const unsigned im = __ballot_sync(full, in);
+      const int cnt = im == full ? 32 : __ffs(~im) - 1;
+      for (int u = 0; u < cnt; ++u) ss += __shfl_sync(full, h, u);
+      if (cnt < 32) break;
+    }
+    if (lane == src) fixup_write(y, rr, ss, alpha, beta);
+  }
+}
 
 }  // namespace msrep

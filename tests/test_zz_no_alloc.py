@@ -52,3 +52,33 @@ def test_noalloc_rejects_problems_larger_than_its_scratch():
         M.native.msrep_spmv_noalloc(A, part, 1.0, x, 0.0, y)
     assert e.value.status == 9             # MSREP_ERR_WORKSPACE
     assert "scratch" in str(e.value)
+
+
+@pytest.mark.parametrize("scale", [14, 18])
+def test_noalloc_csc_with_and_without_the_permuted_accumulator(scale):
+    """CSC on a power-law matrix (hub rows found): at 2^14 rows the permuted
+    accumulator fits in the scratch array, at 2^18 rows (2 MiB) it does not
+    and the call scatters into y directly.  Integer-valued data make every
+    sum exact, so both entry points must match the oracle bit for bit, with
+    beta != 0 applied once."""
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    from helpers import oracle_spmv
+    a0 = I.rmat(scale=scale, nnz=16 * (1 << scale), seed=63)
+    a, x = I.integer_twin(a0, seed=64)
+    y0 = np.round(I.y_vector(a.m, 65) * 4)
+    want = oracle_spmv(a, "csc", x, 1.0, 2.0, y0)
+    A = M.DeviceMatrix.from_host(a, "csc", "f64")
+    part = M.DevicePartition(A, 148)
+    M.msrep_partition(A, part)
+    ws = M.alloc_workspace(A, part)
+    xd = torch.from_numpy(x).cuda()
+    for call in range(2):
+        y_ref = torch.from_numpy(y0).cuda()
+        M.msrep_spmv(A, part, 1.0, xd, 2.0, y_ref, workspace=ws)
+        y = torch.from_numpy(y0).cuda()
+        M.native.msrep_spmv_noalloc(A, part, 1.0, xd, 2.0, y)
+        torch.cuda.synchronize()
+        assert np.array_equal(y_ref.cpu().numpy(), want), call
+        assert np.array_equal(y.cpu().numpy(), want), call
