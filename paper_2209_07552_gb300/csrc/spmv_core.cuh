@@ -642,6 +642,10 @@ __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t 
   const int64_t ka = lr.ka, kb = lr.kb;
   int c = upper_bound_smem(s_end, ncols, static_cast<int32_t>(ka));
   int32_t cend = c < ncols ? s_end[c] : INT32_MAX;
+  // x of the current column, reloaded from shared memory only when the
+  // column changes (xs has an entry for every column index c <= ncols that
+  // holds nonzeros of the tile)
+  double xc = xs[c];
   for (int64_t gg = lr.glo; gg < lr.ghi; ++gg) {
     const int64_t g8 = gg << 3;
     int32_t rw[8];
@@ -652,11 +656,14 @@ __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t 
     for (int u = 0; u < 8; ++u) {
       const int64_t e = g8 + u;
       const bool in = e >= ka && e < kb;
-      while (in && cend <= e) {  // integer-only column advance
-        ++c;
-        cend = c < ncols ? s_end[c] : INT32_MAX;
+      if (in && cend <= e) {  // integer-only column advance
+        do {
+          ++c;
+          cend = c < ncols ? s_end[c] : INT32_MAX;
+        } while (cend <= e);
+        xc = xs[c];
       }
-      const double prod = __dmul_rn(double(v[u]), in ? xs[c] : 0.0);
+      const double prod = __dmul_rn(double(v[u]), in ? xc : 0.0);
       if (in) {
         if (!kSkew)
           atomicAdd(a.yacc + rw[u], prod);
