@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -37,8 +39,10 @@ __device__ __forceinline__ int owner_item(const int64_t *toff, int count, int64_
   return lo;
 }
 
+// Three resident blocks per SM (80 registers a thread), as for the
+// single-matrix CSR kernel.
 template <class Pol>
-__global__ void __launch_bounds__(kBThreads) batched_csr(const BatchItem *items,
+__global__ void __launch_bounds__(kBThreads, 3) batched_csr(const BatchItem *items,
                                                          const int64_t *toff, int count,
                                                          const void *const *xs, void *const *ys,
                                                          double *head, double *tail, double alpha,
@@ -47,9 +51,17 @@ __global__ void __launch_bounds__(kBThreads) batched_csr(const BatchItem *items,
   __shared__ int32_t s_rp[kBWarps][32 * kBMaxIPT + 8];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t total = __ldg(toff + count);
+  int j = 0;
   for (int64_t g = int64_t(blockIdx.x) * kBWarps + wid; g < total;
        g += int64_t(gridDim.x) * kBWarps) {
-    const int j = owner_item(toff, count, g);
+    // a warp's tiles increase: step forward from the previous owner, and
+    // search only when the tile is more than a few matrices ahead
+    int step = 0;
+    while (step < 4 && j + 1 < count && __ldg(toff + j + 1) <= g) {
+      ++j;
+      ++step;
+    }
+    if (step == 4) j = owner_item(toff, count, g);
     const BatchItem it = items[j];
     const int64_t base = __ldg(toff + j);
     const int b = static_cast<int>(g - base);
@@ -173,10 +185,22 @@ msrep_status launch_batched(const BatchItem *items, const int64_t *toff, int cou
   if (T == 0) return MSREP_OK;
   const int sms = sm_count();
   auto launch = [&](auto kern, auto fix) -> msrep_status {
-    static int nb = -1;
-    if (nb < 0) {
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBThreads, 0) != cudaSuccess || nb < 1)
-        nb = 1;
+    // resident blocks per device, after the smallest carveout for 3 blocks
+    static std::mutex mu;
+    static std::map<int, int> blocks;
+    int dev = 0, nb = 1;
+    MSREP_CUDA_TRY(cudaGetDevice(&dev));
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = blocks.find(dev);
+      if (it == blocks.end()) {
+        MSREP_TRY(set_min_carveout(reinterpret_cast<const void *>(kern), 0, 3));
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBThreads, 0) != cudaSuccess || nb < 1)
+          nb = 1;
+        blocks[dev] = nb;
+      } else {
+        nb = it->second;
+      }
     }
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(T, kBWarps), int64_t(nb) * sms));
     kern<<<static_cast<int>(grid), kBThreads, 0, st>>>(items, toff, count, xs, ys, head, tail,

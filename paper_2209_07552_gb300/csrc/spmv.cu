@@ -17,9 +17,9 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <type_traits>
-#include <unordered_map>
 
 #include "common.cuh"
 #include "spmv_core.cuh"
@@ -526,17 +526,39 @@ static int64_t tiles_for(const msrep_matrix *A, const msrep_partition *p, int32_
   return plan_layout(n_major, A->nnz, p->np, tile).tmax;
 }
 
-// Launches the streaming kernel (dynamic shared-memory stages) unless the
-// caller asked for direct loads.  Grid: resident blocks x SMs, capped by the
-// number of tiles.
-// resident blocks per SM of a kernel (keyed by its address), after the
-// dynamic shared-memory opt-in it needs
+}  // namespace msrep
+
+msrep_status msrep::set_min_carveout(const void *kernel, size_t dyn_smem, int blocks) {
+  int dev = 0;
+  MSREP_CUDA_TRY(cudaGetDevice(&dev));
+  cudaFuncAttributes fa;
+  MSREP_CUDA_TRY(cudaFuncGetAttributes(&fa, kernel));
+  int per_sm = 0, reserved = 0;
+  MSREP_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  MSREP_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  const size_t per_block = fa.sharedSizeBytes + dyn_smem;
+  if (per_block == 0 || per_sm <= 0 || blocks <= 0) return MSREP_OK;
+  const size_t need = size_t(blocks) * (per_block + size_t(reserved));
+  const int pct = static_cast<int>(std::min<size_t>(100, (100 * need + per_sm - 1) / per_sm));
+  MSREP_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct));
+  return MSREP_OK;
+}
+
+namespace msrep {
+
+// Resident blocks per SM of a kernel on the current device, after the
+// dynamic shared-memory opt-in it needs.  With want_blocks > 0 the kernel's
+// shared-memory carveout is set to the smallest that holds that many blocks
+// (set_min_carveout).
 template <class K>
-static msrep_status kernel_occupancy(K kernel, size_t smem, int *nb) {
+static msrep_status kernel_occupancy(K kernel, size_t smem, int want_blocks, int *nb) {
   static std::mutex mu;
-  static std::unordered_map<const void *, int> cache;
+  // keyed by (device, kernel): function attributes are set per device
+  static std::map<std::pair<int, const void *>, int> cache;
+  int dev = 0;
+  MSREP_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(mu);
-  const void *key = reinterpret_cast<const void *>(kernel);
+  const auto key = std::make_pair(dev, reinterpret_cast<const void *>(kernel));
   auto it = cache.find(key);
   if (it != cache.end()) {
     *nb = it->second;
@@ -545,19 +567,25 @@ static msrep_status kernel_occupancy(K kernel, size_t smem, int *nb) {
   if (smem > 0)
     MSREP_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         static_cast<int>(smem)));
+  if (want_blocks > 0)
+    MSREP_TRY(set_min_carveout(reinterpret_cast<const void *>(kernel), smem, want_blocks));
   *nb = resident_blocks(kernel, smem);
   cache[key] = *nb;
   return MSREP_OK;
 }
 
+// Launches the streaming kernel (dynamic shared-memory stages) unless the
+// caller asked for direct loads.  Grid: resident blocks x SMs, capped by the
+// number of tiles.
 template <class KS, class KD, class... Args>
 static msrep_status launch_tiles(KS kstream, KD kdirect, size_t stream_smem, size_t direct_smem,
-                                 bool direct, int64_t tiles, cudaStream_t st, Args... args) {
+                                 int direct_blocks, bool direct, int64_t tiles, cudaStream_t st,
+                                 Args... args) {
   int nb = 1;
   if (direct)
-    MSREP_TRY(kernel_occupancy(kdirect, direct_smem, &nb));
+    MSREP_TRY(kernel_occupancy(kdirect, direct_smem, direct_blocks, &nb));
   else
-    MSREP_TRY(kernel_occupancy(kstream, stream_smem, &nb));
+    MSREP_TRY(kernel_occupancy(kstream, stream_smem, 0, &nb));
   int64_t grid = std::min<int64_t>(ceil_div(tiles, kWarps), int64_t(nb) * sm_count());
   if (grid < 1) grid = 1;
   prof_begin(st);
@@ -596,7 +624,7 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
   a.err = kernel_err_ptr();
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   MSREP_TRY(launch_tiles(csr_stream<Pol, IPT>, csr_direct<Pol, IPT>,
-                         StageGeom<typename Pol::V, IPT, 2>::BLOCK, 0,
+                         StageGeom<typename Pol::V, IPT, 2>::BLOCK, 0, MSREP_MINB,
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   int64_t fg = std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count());
@@ -634,7 +662,7 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   const int64_t T = int64_t(a.np) * a.G;
   MSREP_TRY(launch_tiles(coo_stream<Pol, IPT>, coo_direct<Pol, IPT>,
-                         StageGeom<typename Pol::V, IPT, 2>::BLOCK, 0,
+                         StageGeom<typename Pol::V, IPT, 2>::BLOCK, 0, MSREP_MINB,
                          (flags & MSREP_STREAM_TMA) == 0, T, st, a));
   CooTileView v{A->idx2, p->start_idx, p->end_idx, A->nnz, a.G, a.np, A->m};
   int64_t fg = std::min<int64_t>(ceil_div(T, 256), 4 * sm_count());
@@ -688,7 +716,7 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   MSREP_TRY(launch_tiles(csc_stream<Pol, IPT>, csc_direct<Pol, IPT>,
                          StageGeom<typename Pol::V, IPT, 2>::BLOCK +
                              sizeof(double) * kWarps * (32 * IPT + 8),
-                         (sizeof(double) + sizeof(int32_t)) * kWarps * (32 * IPT + 8),
+                         (sizeof(double) + sizeof(int32_t)) * kWarps * (32 * IPT + 8), 0,
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   if (kF64) {
     if (w.perm) {
