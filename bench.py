@@ -668,8 +668,32 @@ def run_precision(M, args, dev):
             rec["speedup_vs_f64"] = base / call_us
             rec["normwise_err_vs_f64"] = float(torch.linalg.norm(yv - y64) / torch.linalg.norm(y64))
         out[dt] = rec
+        if dt == "f32":
+            out["f32_k8"] = run_spmm_leg(M, A, part, a, xh, dev, call_us)
         del A, part, x, y, ws
     return out
+
+
+def run_spmm_leg(M, A, part, a, xh, dev, spmv_call_us, k=8):
+    """k = 8 right-hand sides on the FP32 R-MAT matrix with msrep_spmm (the
+    matrix read once, the 8 values of a column gathered together) against 8
+    separate msrep_spmv calls; effective GFLOP/s = 2 * nnz * k / time."""
+    import torch
+    X = torch.from_numpy(np.stack([np.roll(xh, v) for v in range(k)])).to(dev, torch.float32)
+    Y = torch.empty((k, a.m), dtype=torch.float32, device=dev)
+    ws = torch.empty(M.msrep_spmm_workspace_size(A, part, k), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        M.msrep_spmm(A, part, 1.0, X, 0.0, Y, workspace=ws)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        M.msrep_spmm(A, part, 1.0, X, 0.0, Y, workspace=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    us = 1e3 * e0.elapsed_time(e1) / reps
+    return {"k": k, "call_us": us, "gflops": 2.0 * a.nnz * k / (us * 1e-6) / 1e9,
+            "speedup_vs_k_spmv": k * spmv_call_us / us}
 
 
 def run_profile_case(args):
@@ -690,8 +714,18 @@ def run_profile_case(args):
     y = torch.empty(a.m, dtype=xt, device=dev)
     ws = M.alloc_workspace(A, part, device=dev)
     flags = M.MSREP_STREAM_TMA if args.stream_tma else 0
-    for _ in range(args.reps):
-        M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
+    if args.profile_k > 0:
+        # k right-hand sides (CSR): msrep_spmm on k shifted copies of x
+        X = torch.stack([torch.roll(x, v) for v in range(args.profile_k)])
+        Y = torch.empty((args.profile_k, a.m), dtype=xt, device=dev)
+        wk = torch.empty(M.msrep_spmm_workspace_size(A, part, args.profile_k),
+                         dtype=torch.uint8, device=dev)
+        for _ in range(args.reps):
+            M.msrep_spmm(A, part, 1.0, X, 0.0, Y, flags=flags, workspace=wk)
+        y = Y[0]
+    else:
+        for _ in range(args.reps):
+            M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.profile, "stream_tma": args.stream_tma, "matrix": args.profile_matrix,
                       "dtype": dt, "reps": args.reps, "P": args.P,
@@ -764,6 +798,8 @@ def main():
     ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")
     ap.add_argument("--profile-dtype", choices=["f64", "f32", "bf16"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--profile-k", type=int, default=0,
+                    help="profile case: msrep_spmm with this many vectors (CSR) instead of msrep_spmv")
     ap.add_argument("--stream-tma", action="store_true",
                     help="bulk-copy staging kernels (MSREP_STREAM_TMA) in the profile case")
     ap.add_argument("--record-traffic", metavar="NCU_CSV", default=None,

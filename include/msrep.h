@@ -202,6 +202,37 @@ msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
                         void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* k right-hand sides (no counterpart in the paper, which multiplies one  */
+/* vector; the served form's requests carry up to eight).                 */
+/* ---------------------------------------------------------------------- */
+
+#define MSREP_SPMM_MAX_K 8
+
+/* Host only.  Workspace bytes of msrep_spmm for (A, part, k): two FP64
+ * partials per tile and vector, and the interleaved copy of X (n rows of
+ * k rounded up to 1, 2, 4 or 8 values).  CSR only. */
+msrep_status msrep_spmm_workspace_size(const msrep_matrix *A, const msrep_partition *part,
+                                       int32_t k, size_t *bytes);
+
+/* Y = alpha*A*X + beta*Y for k <= 8 vectors at once, A in CSR over the
+ * tiles of `part` (from msrep_partition_csr, with its plan).  X holds the k
+ * x vectors one after another (x_v = X + v*ldx, n values each, ldx >= n);
+ * Y the k y vectors (y_v = Y + v*ldy, ldy >= m); device memory, types as
+ * for msrep_spmv.  The library first copies X into the workspace with its
+ * k values of each row side by side, so that each nonzero gathers one
+ * segment for all k vectors and A is read once.  Every column of Y is
+ * computed exactly as msrep_spmv computes y for that x (same order of
+ * operations, bit-identical results).  `flags`: MSREP_COMP_ALL /
+ * MSREP_COMP_NONE as for msrep_spmv.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (format not CSR, k outside 1..8, ldx < n, ldy < m,
+ * types, alignment as for msrep_spmv), WORKSPACE (no plan, NULL
+ * workspace), CUDA. */
+msrep_status msrep_spmm(const msrep_matrix *A, const msrep_partition *part, int32_t k,
+                        double alpha, const void *x, int64_t ldx, double beta, void *y,
+                        int64_t ldy, int32_t xy_dtype, unsigned flags, void *workspace,
+                        void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Batched form: many independent CSR matrices in one persistent launch.  */
 /* No counterpart in the paper beyond its partitions (Sec. 3.2); the      */
 /* per-matrix work is Alg. 3 exactly as msrep_spmv runs it.               */
@@ -276,14 +307,21 @@ msrep_status msrep_autotune(int32_t count, const msrep_matrix *As,
 /* batching.  No counterpart in the paper.                                */
 /* ---------------------------------------------------------------------- */
 
+/* A request with one x vector runs as an item of the batched SpMV kernel;
+ * a request with 2..8 vectors as one item of the batched k-vector kernel
+ * (see msrep_spmm), which reads the matrix once for all its vectors.  Each
+ * launch context holds: x and y arenas (arena_bytes each), an interleaved-x
+ * arena (4 * arena_bytes), two directories (max_items entries) and tile
+ * partials for both kernels (max_tiles and 8 * max_tiles doubles, twice);
+ * all of it counts against the budget. */
 typedef struct {
   int64_t budget_bytes;   /* device memory the server may hold in total  */
   int64_t arena_bytes;    /* per in-flight launch: x and y staging (each) */
   int32_t contexts;       /* launches in flight at once (>= 1)           */
-  int32_t max_items;      /* SpMV items (vectors) per launch             */
-  int32_t max_k;          /* vectors per request                         */
+  int32_t max_items;      /* requests per launch, for each kernel        */
+  int32_t max_k;          /* vectors per request (<= 8)                  */
   int32_t tile;           /* tile of every registered matrix (0 = def.)  */
-  int64_t max_tiles;      /* tiles per launch                            */
+  int64_t max_tiles;      /* tiles per launch, for each kernel           */
   int32_t device;         /* CUDA device ordinal                         */
 } msrep_serve_config;
 

@@ -12,6 +12,7 @@ from .native import (MSREP_BF16, MSREP_COMP_ALL, MSREP_COMP_NONE, MSREP_COO,
                      msrep_partition, msrep_partition_coo, msrep_partition_csc,
                      msrep_partition_csr, msrep_partition_local_bound,
                      msrep_plan_size, msrep_spmv, msrep_spmv_workspace_size,
+                     msrep_spmm, msrep_spmm_workspace_size, MSREP_SPMM_MAX_K,
                      msrep_tile_supported, msrep_version, DeviceBatch,
                      msrep_autotune, msrep_batch_plan_size, msrep_spmv_batched,
                      msrep_tune_default, Server, ServeTicket,

@@ -19,7 +19,14 @@ struct BatchItem {
   const int32_t *tile_k;
   int32_t m, n;
   int64_t nnz;
+  int32_t k;    // vectors of the item (the k-vector form; 1 for the SpMV form)
+  int32_t pad;
 };
+
+// Width of the interleaved x of the batched k-vector form (the server's
+// requests with 2..8 vectors): row c holds x_0[c] .. x_7[c], one 32-byte
+// segment per nonzero for FP32.
+constexpr int kBatchWidth = 8;
 
 // Persistent batched kernel + fix-up over `count` items whose tiles are
 // numbered toff[j] .. toff[j+1]-1 (toff has count+1 entries, device).
@@ -29,5 +36,16 @@ msrep_status launch_batched(const BatchItem *items, const int64_t *toff, int cou
                             int64_t total_tiles, int32_t val_dtype, const void *const *xs,
                             void *const *ys, double *head, double *tail, double alpha,
                             double beta, unsigned flags, cudaStream_t st);
+
+// Batched k-vector form (FP32 values and vectors): item j carries k_j <= 8
+// vectors, xin[j] = its k_j x vectors of n_j values each (device),
+// xt[j] = device space for n_j * kBatchWidth values (filled here with the
+// interleaved x), ys[j] = its k_j y vectors of m_j values.  Tiles numbered
+// by toff as for launch_batched; head, tail: total_tiles * kBatchWidth
+// doubles each.  y = A x for every vector (alpha 1, beta 0).  Asynchronous.
+msrep_status launch_batched_k(const BatchItem *items, const int64_t *toff, int count,
+                              int64_t total_tiles, const void *const *xin, void *const *xt,
+                              void *const *ys, double *head, double *tail, unsigned flags,
+                              cudaStream_t st);
 
 }  // namespace msrep

@@ -282,7 +282,7 @@ msrep_status msrep_batch_prepare(int32_t count, const msrep_matrix *As,
     items[j] = BatchItem{As[j].ptr, As[j].idx, As[j].val,
                          reinterpret_cast<const int32_t *>(plan + PL.off_row),
                          reinterpret_cast<const int32_t *>(plan + PL.off_k), As[j].m, As[j].n,
-                         As[j].nnz};
+                         As[j].nnz, 1, 0};
   }
   std::vector<int32_t> nt(count);
   for (int32_t j = 0; j < count; ++j)

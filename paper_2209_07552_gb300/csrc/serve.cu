@@ -1,5 +1,8 @@
 // Serving: device-resident matrices, HBM-budget admission and continuous
-// batching of SpMV requests onto the persistent batched kernel.
+// batching of SpMV requests onto the persistent batched kernels.  A request
+// with one x vector is an item of the batched SpMV kernel; a request with
+// 2..8 vectors is one item of the batched k-vector kernel, which streams the
+// matrix once and gathers all its vectors' values of a column together.
 //
 // Threads: the caller's threads submit and wait; a scheduler thread packs
 // queued requests into a launch whenever a context (stream + x/y arenas +
@@ -72,6 +75,12 @@ struct Context {
   size_t dir_bytes = 0;
   double *head = nullptr, *tail = nullptr;
   int64_t max_tiles = 0;
+  // k-vector requests: interleaved x arena, directory, partials (x8)
+  float *xt_dev = nullptr;
+  int64_t xt_floats = 0;
+  char *dirk_dev = nullptr, *dirk_pin = nullptr;
+  size_t dirk_bytes = 0;
+  double *head_k = nullptr, *tail_k = nullptr;
   bool busy = false;      // packed by the scheduler (launching or in flight)
   bool in_flight = false; // its event has been recorded for this launch
   std::vector<std::shared_ptr<Request>> reqs;  // in this launch
@@ -111,6 +120,12 @@ static size_t dir_size(int32_t max_items) {
          2 * align256(sizeof(void *) * max_items);
 }
 
+// k-vector directory: items | toff | xin | xt | ys
+static size_t dirk_size(int32_t max_items) {
+  return align256(sizeof(BatchItem) * max_items) + align256(sizeof(int64_t) * (max_items + 1)) +
+         3 * align256(sizeof(void *) * max_items);
+}
+
 static void free_context(Context &c) {
   if (c.stream) cudaStreamSynchronize(c.stream);
   cudaFree(c.x_dev);
@@ -118,6 +133,11 @@ static void free_context(Context &c) {
   cudaFree(c.dir_dev);
   cudaFree(c.head);
   cudaFree(c.tail);
+  cudaFree(c.xt_dev);
+  cudaFree(c.dirk_dev);
+  cudaFree(c.head_k);
+  cudaFree(c.tail_k);
+  cudaFreeHost(c.dirk_pin);
   cudaFreeHost(c.x_pin);
   cudaFreeHost(c.y_pin);
   cudaFreeHost(c.dir_pin);
@@ -127,26 +147,40 @@ static void free_context(Context &c) {
 }
 
 // Launch the requests in c.reqs (scheduler thread, server lock NOT held
-// while copying; the matrices they name are pinned by their refs).
+// while copying; the matrices they name are pinned by their refs).  ritem /
+// rtiles: each request's matrix and its tile count.
 static msrep_status launch_context(msrep_server *s, Context &c,
-                                   const std::vector<BatchItem> &items,
-                                   const std::vector<int64_t> &tiles) {
-  const int cnt = static_cast<int>(items.size());
-  // directory in pinned memory, then one copy
+                                   const std::vector<BatchItem> &ritem,
+                                   const std::vector<int64_t> &rtiles) {
+  const int N = s->cfg.max_items;
+  // SpMV directory (requests with one vector, one item per vector)
   char *dp = c.dir_pin;
   BatchItem *it = reinterpret_cast<BatchItem *>(dp);
-  size_t o = align256(sizeof(BatchItem) * s->cfg.max_items);
+  size_t o = align256(sizeof(BatchItem) * N);
   int64_t *toff = reinterpret_cast<int64_t *>(dp + o);
-  o += align256(sizeof(int64_t) * (s->cfg.max_items + 1));
+  o += align256(sizeof(int64_t) * (N + 1));
   const void **xs = reinterpret_cast<const void **>(dp + o);
-  o += align256(sizeof(void *) * s->cfg.max_items);
+  o += align256(sizeof(void *) * N);
   void **ys = reinterpret_cast<void **>(dp + o);
-  int64_t xo = 0, yo = 0, tt = 0;
-  int item = 0;
+  // k-vector directory
+  char *kp = c.dirk_pin;
+  BatchItem *itk = reinterpret_cast<BatchItem *>(kp);
+  size_t ok_ = align256(sizeof(BatchItem) * N);
+  int64_t *toffk = reinterpret_cast<int64_t *>(kp + ok_);
+  ok_ += align256(sizeof(int64_t) * (N + 1));
+  const void **xin = reinterpret_cast<const void **>(kp + ok_);
+  ok_ += align256(sizeof(void *) * N);
+  void **xtp = reinterpret_cast<void **>(kp + ok_);
+  ok_ += align256(sizeof(void *) * N);
+  void **ysk = reinterpret_cast<void **>(kp + ok_);
+
+  int64_t xo = 0, yo = 0, xto = 0, tt = 0, ttk = 0;
+  int n1 = 0, nk = 0;
   c.y_off.clear();
-  for (auto &r : c.reqs) {
+  for (size_t i = 0; i < c.reqs.size(); ++i) {
+    const auto &r = c.reqs[i];
+    const BatchItem &bi = ritem[i];
     c.y_off.push_back(yo);
-    const BatchItem &bi = items[item];
     const size_t xb = sizeof(float) * size_t(bi.n) * r->k;
     if (r->x_pinned) {
       MSREP_CUDA_TRY(cudaMemcpyAsync(c.x_dev + xo, r->x, xb, cudaMemcpyHostToDevice, c.stream));
@@ -154,30 +188,56 @@ static msrep_status launch_context(msrep_server *s, Context &c,
       std::memcpy(c.x_pin + xo, r->x, xb);
       MSREP_CUDA_TRY(cudaMemcpyAsync(c.x_dev + xo, c.x_pin + xo, xb, cudaMemcpyHostToDevice, c.stream));
     }
-    for (int v = 0; v < r->k; ++v, ++item) {
-      it[item] = items[item];
-      toff[item] = tt;
-      tt += tiles[item];
-      xs[item] = c.x_dev + xo + int64_t(v) * bi.n;
-      ys[item] = c.y_dev + yo + int64_t(v) * bi.m;
+    if (r->k == 1) {
+      it[n1] = bi;
+      toff[n1] = tt;
+      tt += rtiles[i];
+      xs[n1] = c.x_dev + xo;
+      ys[n1] = c.y_dev + yo;
+      ++n1;
+    } else {
+      itk[nk] = bi;
+      itk[nk].k = r->k;
+      toffk[nk] = ttk;
+      ttk += rtiles[i];
+      xin[nk] = c.x_dev + xo;
+      xtp[nk] = c.xt_dev + xto;
+      ysk[nk] = c.y_dev + yo;
+      xto += int64_t(bi.n) * kBatchWidth;
+      ++nk;
     }
     xo += int64_t(bi.n) * r->k;
     yo += int64_t(bi.m) * r->k;
   }
-  toff[cnt] = tt;
-  const size_t dir_used = align256(sizeof(BatchItem) * s->cfg.max_items) +
-                          align256(sizeof(int64_t) * (s->cfg.max_items + 1)) +
-                          2 * align256(sizeof(void *) * s->cfg.max_items);
-  MSREP_CUDA_TRY(cudaMemcpyAsync(c.dir_dev, c.dir_pin, dir_used, cudaMemcpyHostToDevice, c.stream));
-  const char *dd = c.dir_dev;
-  size_t q = align256(sizeof(BatchItem) * s->cfg.max_items);
-  const int64_t *dtoff = reinterpret_cast<const int64_t *>(dd + q);
-  q += align256(sizeof(int64_t) * (s->cfg.max_items + 1));
-  const void *const *dxs = reinterpret_cast<const void *const *>(dd + q);
-  q += align256(sizeof(void *) * s->cfg.max_items);
-  void *const *dys = reinterpret_cast<void *const *>(dd + q);
-  MSREP_TRY(launch_batched(reinterpret_cast<const BatchItem *>(dd), dtoff, cnt, tt, MSREP_F32,
-                           dxs, dys, c.head, c.tail, 1.0, 0.0, 0, c.stream));
+  toff[n1] = tt;
+  toffk[nk] = ttk;
+  if (n1 > 0) {
+    MSREP_CUDA_TRY(cudaMemcpyAsync(c.dir_dev, c.dir_pin, c.dir_bytes, cudaMemcpyHostToDevice, c.stream));
+    const char *dd = c.dir_dev;
+    size_t q = align256(sizeof(BatchItem) * N);
+    const int64_t *dtoff = reinterpret_cast<const int64_t *>(dd + q);
+    q += align256(sizeof(int64_t) * (N + 1));
+    const void *const *dxs = reinterpret_cast<const void *const *>(dd + q);
+    q += align256(sizeof(void *) * N);
+    void *const *dys = reinterpret_cast<void *const *>(dd + q);
+    MSREP_TRY(launch_batched(reinterpret_cast<const BatchItem *>(dd), dtoff, n1, tt, MSREP_F32,
+                             dxs, dys, c.head, c.tail, 1.0, 0.0, 0, c.stream));
+  }
+  if (nk > 0) {
+    MSREP_CUDA_TRY(cudaMemcpyAsync(c.dirk_dev, c.dirk_pin, c.dirk_bytes, cudaMemcpyHostToDevice,
+                                   c.stream));
+    const char *dd = c.dirk_dev;
+    size_t q = align256(sizeof(BatchItem) * N);
+    const int64_t *dtoff = reinterpret_cast<const int64_t *>(dd + q);
+    q += align256(sizeof(int64_t) * (N + 1));
+    const void *const *dxin = reinterpret_cast<const void *const *>(dd + q);
+    q += align256(sizeof(void *) * N);
+    void *const *dxt = reinterpret_cast<void *const *>(dd + q);
+    q += align256(sizeof(void *) * N);
+    void *const *dys = reinterpret_cast<void *const *>(dd + q);
+    MSREP_TRY(launch_batched_k(reinterpret_cast<const BatchItem *>(dd), dtoff, nk, ttk, dxin, dxt,
+                               dys, c.head_k, c.tail_k, 0, c.stream));
+  }
   for (size_t i = 0; i < c.reqs.size(); ++i) {
     const auto &r = c.reqs[i];
     const int64_t ylen = (i + 1 < c.reqs.size() ? c.y_off[i + 1] : yo) - c.y_off[i];
@@ -208,10 +268,12 @@ static void scheduler_loop(msrep_server *s) {
         break;
       }
     if (!c) continue;
-    // pack requests in arrival order while the context has room
-    std::vector<BatchItem> items;
-    std::vector<int64_t> tiles;
-    int64_t xf = 0, yf = 0, tt = 0;
+    // pack requests in arrival order while the context has room; one-vector
+    // requests fill the SpMV directory, the others the k-vector one
+    std::vector<BatchItem> ritem;
+    std::vector<int64_t> rtiles;
+    int64_t xf = 0, yf = 0, xtf = 0, tt = 0, ttk = 0;
+    int n1 = 0, nk = 0;
     double bytes = 0;
     c->reqs.clear();
     while (!s->queue.empty()) {
@@ -219,30 +281,39 @@ static void scheduler_loop(msrep_server *s) {
       auto mit = s->mats.find(r->matrix);
       const Resident &R = mit->second;
       const int64_t nx = int64_t(R.n) * r->k, ny = int64_t(R.m) * r->k;
-      if (!c->reqs.empty() &&
-          (int(items.size()) + r->k > s->cfg.max_items || xf + nx > c->arena_floats ||
-           yf + ny > c->arena_floats || tt + R.tiles * r->k > c->max_tiles))
-        break;
+      const bool one = r->k == 1;
+      const bool full =
+          xf + nx > c->arena_floats || yf + ny > c->arena_floats ||
+          (one ? (n1 + 1 > s->cfg.max_items || tt + R.tiles > c->max_tiles)
+               : (nk + 1 > s->cfg.max_items || ttk + R.tiles > c->max_tiles ||
+                  xtf + int64_t(R.n) * kBatchWidth > c->xt_floats));
+      if (!c->reqs.empty() && full) break;
       s->queue.pop_front();
       c->reqs.push_back(r);
-      for (int v = 0; v < r->k; ++v) {
-        items.push_back(R.item);
-        tiles.push_back(R.tiles);
-      }
+      ritem.push_back(R.item);
+      rtiles.push_back(R.tiles);
       xf += nx;
       yf += ny;
-      tt += R.tiles * r->k;
-      // algorithmic bytes: FP32 CSR formula per vector
-      bytes += double(r->k) * (8.0 * R.nnz + 4.0 * (R.m + 1) + 4.0 * R.n + 4.0 * R.m);
+      if (one) {
+        ++n1;
+        tt += R.tiles;
+      } else {
+        ++nk;
+        ttk += R.tiles;
+        xtf += int64_t(R.n) * kBatchWidth;
+      }
+      // algorithmic bytes (FP32 CSR): the matrix once per launch item, x and
+      // y once per vector
+      bytes += 8.0 * R.nnz + 4.0 * (R.m + 1) + double(r->k) * (4.0 * R.n + 4.0 * R.m);
     }
     c->busy = true;
     c->bytes = bytes;
     c->t_launch = Clock::now();
     if (s->inflight++ == 0) s->busy_since = c->t_launch;
     s->launches++;
-    s->items += items.size();
+    for (const auto &r : c->reqs) s->items += r->k;
     lk.unlock();
-    msrep_status st = launch_context(s, *c, items, tiles);
+    msrep_status st = launch_context(s, *c, ritem, rtiles);
     lk.lock();
     if (st == MSREP_OK) c->in_flight = true;  // only now may its event be polled
     if (st != MSREP_OK) {
@@ -337,11 +408,16 @@ msrep_status msrep_serve_config_default(msrep_serve_config *c) {
 
 msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **out) {
   if (!cfg || !out) return fail(MSREP_ERR_INVALID_ARG, "cfg or out is NULL");
-  if (cfg->contexts < 1 || cfg->max_items < 1 || cfg->max_k < 1 || cfg->max_k > cfg->max_items ||
+  if (cfg->contexts < 1 || cfg->max_items < 1 || cfg->max_k < 1 || cfg->max_k > kBatchWidth ||
       cfg->arena_bytes < 4096 || cfg->max_tiles < 1 || !tile_supported(effective_tile(cfg->tile)))
     return fail(MSREP_ERR_INVALID_ARG, "bad serve config");
-  const int64_t per_ctx = 2 * align256(cfg->arena_bytes) + int64_t(dir_size(cfg->max_items)) +
-                          2 * int64_t(align256(sizeof(double) * cfg->max_tiles));
+  // x, y arenas; interleaved-x arena (8 values per column: up to four times
+  // the x of a request with two vectors); directories; partials of both
+  // kernels
+  const int64_t per_ctx = 2 * align256(cfg->arena_bytes) + 4 * align256(cfg->arena_bytes) +
+                          int64_t(dir_size(cfg->max_items)) + int64_t(dirk_size(cfg->max_items)) +
+                          2 * int64_t(align256(sizeof(double) * cfg->max_tiles)) +
+                          2 * int64_t(align256(sizeof(double) * cfg->max_tiles * kBatchWidth));
   if (per_ctx * cfg->contexts > cfg->budget_bytes)
     return fail(MSREP_ERR_BUDGET, "the launch contexts alone exceed the budget");
   MSREP_CUDA_TRY(cudaSetDevice(cfg->device));
@@ -352,6 +428,8 @@ msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **ou
     c.arena_floats = cfg->arena_bytes / int64_t(sizeof(float));
     c.max_tiles = cfg->max_tiles;
     c.dir_bytes = dir_size(cfg->max_items);
+    c.dirk_bytes = dirk_size(cfg->max_items);
+    c.xt_floats = 4 * cfg->arena_bytes / int64_t(sizeof(float));
     bool okc = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) == cudaSuccess &&
                cudaEventCreateWithFlags(&c.done_ev, cudaEventDisableTiming) == cudaSuccess &&
                cudaMalloc(&c.x_dev, cfg->arena_bytes) == cudaSuccess &&
@@ -361,7 +439,12 @@ msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **ou
                cudaMalloc(&c.tail, sizeof(double) * cfg->max_tiles) == cudaSuccess &&
                cudaMallocHost(&c.x_pin, cfg->arena_bytes) == cudaSuccess &&
                cudaMallocHost(&c.y_pin, cfg->arena_bytes) == cudaSuccess &&
-               cudaMallocHost(&c.dir_pin, c.dir_bytes) == cudaSuccess;
+               cudaMallocHost(&c.dir_pin, c.dir_bytes) == cudaSuccess &&
+               cudaMalloc(&c.xt_dev, sizeof(float) * c.xt_floats) == cudaSuccess &&
+               cudaMalloc(&c.dirk_dev, c.dirk_bytes) == cudaSuccess &&
+               cudaMalloc(&c.head_k, sizeof(double) * cfg->max_tiles * kBatchWidth) == cudaSuccess &&
+               cudaMalloc(&c.tail_k, sizeof(double) * cfg->max_tiles * kBatchWidth) == cudaSuccess &&
+               cudaMallocHost(&c.dirk_pin, c.dirk_bytes) == cudaSuccess;
     if (!okc) {
       for (auto &cc : s->ctx) free_context(cc);
       cudaGetLastError();
@@ -475,7 +558,8 @@ msrep_status msrep_serve_register(msrep_server *s, const msrep_matrix *A, int64_
   R.mem = mem;
   R.bytes = bytes;
   R.item = BatchItem{D.ptr, D.idx, D.val, reinterpret_cast<const int32_t *>(b + o_plan + PL.off_row),
-                     reinterpret_cast<const int32_t *>(b + o_plan + PL.off_k), A->m, A->n, A->nnz};
+                     reinterpret_cast<const int32_t *>(b + o_plan + PL.off_k), A->m, A->n, A->nnz,
+                     1, 0};
   std::lock_guard<std::mutex> lk(s->mu);
   R.id = s->next_matrix++;
   *matrix_id = R.id;

@@ -26,6 +26,7 @@ MSREP_VALIDATE = 0x1
 MSREP_COMP_ALL = 0x10
 MSREP_COMP_NONE = 0x20
 MSREP_STREAM_TMA = 0x40
+MSREP_SPMM_MAX_K = 8
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_MATRIX", 3: "OOM", 4: "CUDA",
           5: "TIMEOUT", 6: "BUDGET", 7: "NOT_FOUND", 8: "SHUTDOWN",
@@ -105,6 +106,11 @@ SIGNATURES = {
     "msrep_spmv": (ctypes.c_int, [_M, _P, ctypes.c_double, _vp, ctypes.c_double,
                                   _vp, ctypes.c_int32, ctypes.c_uint, _vp, _vp]),
     "msrep_profile_events": (ctypes.c_int, [_vp, _vp]),
+    "msrep_spmm_workspace_size": (ctypes.c_int, [_M, _P, ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "msrep_spmm": (ctypes.c_int, [_M, _P, ctypes.c_int32, ctypes.c_double, _vp, ctypes.c_int64,
+                                  ctypes.c_double, _vp, ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.c_uint, _vp, _vp]),
     "msrep_spmv_noalloc": (ctypes.c_int, [_M, _P, ctypes.c_double, _vp, ctypes.c_double,
                                           _vp, ctypes.c_int32, ctypes.c_uint, _vp]),
     "msrep_device_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
@@ -353,6 +359,28 @@ def msrep_spmv(A: DeviceMatrix, part: DevicePartition, alpha: float, x,
     _check(lib().msrep_spmv(ctypes.byref(A.c), ctypes.byref(part.c),
                             float(alpha), _ptr(x), float(beta), _ptr(y), xy,
                             flags, _ptr(workspace), _stream(stream)))
+
+
+def msrep_spmm_workspace_size(A: DeviceMatrix, part: DevicePartition, k: int) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().msrep_spmm_workspace_size(ctypes.byref(A.c), ctypes.byref(part.c), int(k),
+                                           ctypes.byref(out)))
+    return out.value
+
+
+def msrep_spmm(A: DeviceMatrix, part: DevicePartition, alpha: float, X, beta: float, Y,
+               flags: int = 0, workspace=None, stream=None):
+    """Y = alpha*A*X + beta*Y for k <= 8 vectors: X is a (k, n) and Y a (k, m)
+    device tensor (row v = vector v, rows contiguous).  A must be CSR."""
+    import torch
+    k = X.shape[0]
+    if workspace is None:
+        workspace = torch.empty(max(256, msrep_spmm_workspace_size(A, part, k)),
+                                dtype=torch.uint8, device=X.device)
+    xy = MSREP_F64 if Y.dtype == torch.float64 else MSREP_F32
+    _check(lib().msrep_spmm(ctypes.byref(A.c), ctypes.byref(part.c), int(k), float(alpha),
+                            _ptr(X), int(X.stride(0)), float(beta), _ptr(Y), int(Y.stride(0)),
+                            xy, flags, _ptr(workspace), _stream(stream)))
 
 
 def msrep_spmv_noalloc(A: DeviceMatrix, part: DevicePartition, alpha: float, x,

@@ -52,3 +52,24 @@ def test_host_only_entry_points(so):
     A.c.fmt = 7
     with pytest.raises(N.MsrepError):
         N.msrep_plan_size(A, 4, 0)
+
+
+def test_spmm_workspace_size_host_checks(so):
+    from paper_2209_07552_gb300 import native as N
+    N.lib(so._name)
+    A = N.DeviceMatrix.__new__(N.DeviceMatrix)
+    A.c = N.c_msrep_matrix(N.MSREP_CSR, N.MSREP_F32, 1000, 800, 5000, 1, 1, None, 1)
+    A.fmt = N.MSREP_CSR
+    P = N.DevicePartition.__new__(N.DevicePartition)
+    P.c = N.c_msrep_partition()
+    P.c.np = 4
+    sizes = [N.msrep_spmm_workspace_size(A, P, k) for k in (1, 2, 3, 4, 8)]
+    # the interleaved copy of X grows with k rounded up to 1, 2, 4, 8
+    assert sizes[0] < sizes[1] < sizes[2] == sizes[3] < sizes[4]
+    for bad in (0, 9):
+        with pytest.raises(N.MsrepError) as e:
+            N.msrep_spmm_workspace_size(A, P, bad)
+        assert e.value.status == 1
+    A.c.fmt = N.MSREP_CSC
+    with pytest.raises(N.MsrepError):
+        N.msrep_spmm_workspace_size(A, P, 2)

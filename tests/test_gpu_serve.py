@@ -85,9 +85,10 @@ def test_serve_budget_admission_and_unregister():
     import paper_2209_07552_gb300 as M
     big = I.rmat(scale=14, nnz=400_000, seed=3)
     small = I.geometric_matrix(2000, 8.0, 4, np.float32)
-    ctx = 3 * (2 * (1 << 20) + 2 * 8 * (1 << 16) + 64 * 1024)
-    with M.Server(budget_bytes=ctx + 2_000_000, arena_bytes=1 << 20, contexts=3,
-                  max_tiles=1 << 16, max_items=64) as S:
+    cfg = dict(arena_bytes=1 << 20, contexts=3, max_tiles=1 << 16, max_items=64)
+    with M.Server(budget_bytes=1 << 30, **cfg) as S0:
+        ctx = S0.stats()["resident_bytes"]        # the launch contexts alone
+    with M.Server(budget_bytes=ctx + 2_000_000, **cfg) as S:
         sid = S.register(small)
         with pytest.raises(M.MsrepError) as e:
             S.register(big)               # about 3.3 MB does not fit
