@@ -372,6 +372,9 @@ def run_ours(args):
             kern[f"{name}/{fmt}"] = {"kernel_us": 1e3 * tot / reps,
                                      "call_us": 1e3 * e0.elapsed_time(e1) / reps,
                                      "bytes": nb, "nnz": nnz}
+            fl = access_floor_us(M, A, x, reps)
+            if fl is not None:
+                kern[f"{name}/{fmt}"].update(fl)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -386,6 +389,12 @@ def run_ours(args):
     roof = {"bound": "hbm", "kernel": dom_key, "achieved": achieved, "peak": peak,
             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
             "traffic": recorded_traffic(dom_key)}
+    if "floor_us" in d:
+        # the same arrays streamed with only the gathers / scatters, no row
+        # logic (msrep_access_floor): the bound the access pattern sets
+        roof["access_floor"] = {"us": d["floor_us"], "mode": d["floor_mode"],
+                                "gbs": d["bytes"] / (d["floor_us"] * 1e-6) / 1e9,
+                                "kernel_frac_of_floor": d["floor_us"] / d["kernel_us"]}
     for k, v in kern.items():
         v["gbs"] = v["bytes"] / (v["kernel_us"] * 1e-6) / 1e9
         v["frac"] = v["gbs"] / peak
@@ -433,6 +442,38 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def access_floor_us(M, A, x, reps):
+    """Time of msrep_access_floor over the matrix's own index and value
+    arrays: a gather of x per nonzero (CSR; COO also streams its row index)
+    or an atomic add per nonzero (CSC, the faster of scattering to y's rows
+    and to the permuted accumulator).  None when a vector length is not a
+    power of two."""
+    import torch
+    if A.fmt == M.MSREP_CSC:
+        n_vec, modes, idx2 = A.m, (2, 3), None
+    else:
+        n_vec, modes = A.n, ((1,) if A.fmt == M.MSREP_COO else (0,))
+        idx2 = A.idx2
+    if n_vec & (n_vec - 1):
+        return None
+    vec = x if A.fmt != M.MSREP_CSC else torch.zeros(n_vec, dtype=torch.float64, device=x.device)
+    sink = torch.zeros(1, dtype=torch.float64, device=x.device)
+    best = None
+    for mode in modes:
+        for _ in range(2):
+            M.native.msrep_access_floor(mode, A.idx, A.val, vec, idx2=idx2, sink=sink)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            M.native.msrep_access_floor(mode, A.idx, A.val, vec, idx2=idx2, sink=sink)
+        e1.record()
+        torch.cuda.synchronize()
+        us = 1e3 * e0.elapsed_time(e1) / reps
+        if best is None or us < best[0]:
+            best = (us, mode)
+    return {"floor_us": best[0], "floor_mode": best[1]}
 
 
 def run_e2e(M, pairs, args, dev):

@@ -417,6 +417,21 @@ msrep_status msrep_spmv_noalloc(const msrep_matrix *A, const msrep_partition *pa
  * *status = 0 and MSREP_OK when no kernel failed, else MSREP_ERR_TIMEOUT. */
 msrep_status msrep_device_status(void *stream, int *status);
 
+/* Measurement aid (no counterpart in the paper): the access-pattern floor
+ * of an SpMV.  One kernel that streams idx (and, mode 1, idx2) and val once
+ * and, per nonzero, gathers vec[idx] (modes 0, 1: CSR, COO) or atomically
+ * adds val into vec[idx] (mode 2) or into vec[slot(idx)] (mode 3: the
+ * permuted accumulator of msrep_spmv's CSC path, slot(r) = r * 0x9E3779B1
+ * mod vec_len), with no row logic.  Its time is what any SpMV kernel over
+ * the same arrays pays for its gathers or scatters.  nnz elements; idx,
+ * idx2, val 32-byte aligned device arrays; vec: vec_len doubles, vec_len a
+ * power of two (every index is reduced modulo vec_len, so any idx is in
+ * bounds); sink: one device double (written only to keep the gathers).
+ * Asynchronous on `stream`.  Errors: INVALID_ARG. */
+msrep_status msrep_access_floor(int32_t mode, const int32_t *idx, const int32_t *idx2,
+                                const double *val, double *vec, int64_t nnz,
+                                int64_t vec_len, double *sink, void *stream);
+
 /* Profiling aid (no counterpart in the paper).  While set, every msrep_spmv
  * call made on this host thread records `start` (a cudaEvent_t passed as
  * void*) on its stream just before its main SpMV kernel and `stop` just

@@ -1,0 +1,92 @@
+// Access-pattern floor of an SpMV (measurement aid): kernels that do only
+// the memory traffic of one SpMV over a given matrix -- stream the index
+// and value arrays once and gather x (CSR, COO) or scatter-add into an
+// accumulator (CSC) at the matrix's own indices -- with no row logic.  On
+// GB300 a random 8-byte gather or atomic add per nonzero, not HBM bandwidth,
+// bounds such kernels (about 2.5 TB/s of algorithmic traffic for uniform
+// random columns against 6.4 TB/s for the streams alone), so the time of
+// this kernel is the floor an SpMV kernel on the same arrays is judged by.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace msrep {
+
+// 8 consecutive elements per lane, 256-bit loads, one gather (MODE 0, 1)
+// or one atomic add (MODE 2, 3) per element.  MODE 1 also streams a second
+// index array (COO's row index); MODE 3 scatters to the permuted slot of
+// the index (the CSC kernels' accumulator for matrices with hub rows).
+template <int MODE>
+__global__ void __launch_bounds__(256) access_floor(const int32_t *__restrict__ idx,
+                                                   const int32_t *__restrict__ idx2,
+                                                   const double *__restrict__ val, double *vec,
+                                                   int64_t nnz, uint32_t mask, double *sink) {
+  const int64_t lanes = int64_t(gridDim.x) * blockDim.x;
+  double acc = 0.0;
+  int32_t other = 0;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t * 8 < nnz; t += lanes) {
+    const int64_t g8 = t * 8;
+    int32_t c[8];
+    double v[8];
+    const int nv = g8 + 8 <= nnz ? 8 : static_cast<int>(nnz - g8);
+    if (nv == 8) {
+      ld8(idx + g8, c);
+      ld8(val + g8, v);
+      if (MODE == 1) {
+        int32_t r[8];
+        ld8(idx2 + g8, r);
+        other ^= r[0] ^ r[7];
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        c[u] = u < nv ? idx[g8 + u] : 0;
+        v[u] = u < nv ? val[g8 + u] : 0.0;
+      }
+    }
+    // every index is masked to the power-of-two vector: in bounds whatever
+    // the arrays hold
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (u >= nv) continue;
+      if (MODE <= 1) {
+        acc = __fma_rn(v[u], __ldg(vec + (static_cast<uint32_t>(c[u]) & mask)), acc);
+      } else {
+        const uint32_t s = MODE == 3 ? perm_slot(c[u], mask) : static_cast<uint32_t>(c[u]) & mask;
+        atomicAdd(vec + s, v[u]);
+      }
+    }
+  }
+  // keeps the gathers live without a store per thread
+  if (MODE <= 1 && (acc == 1.2345e-300 || other == 0x7fffabcd)) sink[0] = acc;
+}
+
+}  // namespace msrep
+
+using namespace msrep;
+
+extern "C" msrep_status msrep_access_floor(int32_t mode, const int32_t *idx, const int32_t *idx2,
+                                           const double *val, double *vec, int64_t nnz,
+                                           int64_t vec_len, double *sink, void *stream) {
+  if (mode < 0 || mode > 3) return fail(MSREP_ERR_INVALID_ARG, "mode %d outside 0..3", mode);
+  if (nnz < 0 || vec_len < 1 || !sink || (nnz > 0 && (!idx || !val || !vec)) ||
+      (mode == 1 && nnz > 0 && !idx2))
+    return fail(MSREP_ERR_INVALID_ARG, "bad arrays or sizes");
+  if ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(idx2) |
+       reinterpret_cast<uintptr_t>(val)) & 31)
+    return fail(MSREP_ERR_INVALID_ARG, "idx, idx2 and val must be 32-byte aligned");
+  if (vec_len & (vec_len - 1)) return fail(MSREP_ERR_INVALID_ARG, "vec_len must be a power of two");
+  if (nnz == 0) return ok();
+  cudaStream_t st = as_stream(stream);
+  const int grid = 8 * sm_count();
+  const uint32_t mask = static_cast<uint32_t>(vec_len - 1);
+  switch (mode) {
+    case 0: access_floor<0><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
+    case 1: access_floor<1><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
+    case 2: access_floor<2><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
+    default: access_floor<3><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
+  }
+  MSREP_CUDA_TRY(cudaGetLastError());
+  return ok();
+}

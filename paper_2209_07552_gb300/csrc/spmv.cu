@@ -98,13 +98,31 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) csr_direct(CsrArgs<Pol> 
                                                        int64_t nnz) {
   __shared__ int32_t s_rp[kWarps][32 * IPT + 8];
   const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
-    const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
-    const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
+  const int stride = gridDim.x * kWarps;
+  // The next tile's coordinates and its first 64 row pointers are loaded
+  // while the current tile is processed, so a tile does not start with two
+  // dependent global round trips (coordinates, then row pointers).
+  int b = blockIdx.x * kWarps + wid;
+  int32_t r0 = 0, k0 = 0, r1 = 0, k1 = 0, p0 = 0, p1 = 0;
+  auto fetch = [&](int t) {
+    r0 = __ldg(a.tile_row + t);
+    k0 = __ldg(a.tile_k + t);
+    r1 = __ldg(a.tile_row + t + 1);
+    k1 = __ldg(a.tile_k + t + 1);
     const int32_t rend = min(r1 + 2, a.m + 1);
-    for (int32_t r = r0 + lane; r < rend; r += 32) s_rp[wid][r - r0] = __ldg(a.row_ptr + r);
+    p0 = r0 + lane < rend ? __ldg(a.row_ptr + r0 + lane) : 0;
+    p1 = r0 + 32 + lane < rend ? __ldg(a.row_ptr + r0 + 32 + lane) : 0;
+  };
+  if (b < T) fetch(b);
+  for (; b < T; b += stride) {
+    const int32_t cr0 = r0, ck0 = k0, cr1 = r1, ck1 = k1;
+    const int32_t rend = min(cr1 + 2, a.m + 1);
+    if (cr0 + lane < rend) s_rp[wid][lane] = p0;
+    if (cr0 + 32 + lane < rend) s_rp[wid][32 + lane] = p1;
+    for (int32_t r = cr0 + 64 + lane; r < rend; r += 32) s_rp[wid][r - cr0] = __ldg(a.row_ptr + r);
     __syncwarp();
-    csr_tile_compute<Pol>(a, b, r0, k0, r1, k1, s_rp[wid], Seg<int32_t>{a.col_idx, 0},
+    if (b + stride < T) fetch(b + stride);
+    csr_tile_compute<Pol>(a, b, cr0, ck0, cr1, ck1, s_rp[wid], Seg<int32_t>{a.col_idx, 0},
                           Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{});
     __syncwarp();
   }
@@ -195,10 +213,15 @@ __global__ void __launch_bounds__(kThreads) csr_stream(CsrArgs<Pol> a, const int
 template <class Pol, int IPT>
 __global__ void __launch_bounds__(kThreads, MSREP_MINB) coo_direct(CooArgs<Pol> a) {
   const int T = a.np * a.G, wid = threadIdx.x >> 5;
-  for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
-    int32_t k0, k1;
-    coo_tile_range(a, b, k0, k1);
-    coo_tile_compute<Pol>(a, b, k0, k1, Seg<int32_t>{a.row_idx, 0}, Seg<int32_t>{a.col_idx, 0},
+  const int stride = gridDim.x * kWarps;
+  // the next tile's range is loaded while the current one is processed
+  int b = blockIdx.x * kWarps + wid;
+  int32_t k0 = 0, k1 = 0;
+  if (b < T) coo_tile_range(a, b, k0, k1);
+  for (; b < T; b += stride) {
+    const int32_t ck0 = k0, ck1 = k1;
+    if (b + stride < T) coo_tile_range(a, b + stride, k0, k1);
+    coo_tile_compute<Pol>(a, b, ck0, ck1, Seg<int32_t>{a.row_idx, 0}, Seg<int32_t>{a.col_idx, 0},
                           Seg<typename Pol::V>{a.val, 0}, GlobalSrc{});
     __syncwarp();
   }

@@ -106,6 +106,8 @@ SIGNATURES = {
     "msrep_spmv": (ctypes.c_int, [_M, _P, ctypes.c_double, _vp, ctypes.c_double,
                                   _vp, ctypes.c_int32, ctypes.c_uint, _vp, _vp]),
     "msrep_profile_events": (ctypes.c_int, [_vp, _vp]),
+    "msrep_access_floor": (ctypes.c_int, [ctypes.c_int32, _vp, _vp, _vp, _vp, ctypes.c_int64,
+                                          ctypes.c_int64, _vp, _vp]),
     "msrep_spmm_workspace_size": (ctypes.c_int, [_M, _P, ctypes.c_int32,
                                                  ctypes.POINTER(ctypes.c_size_t)]),
     "msrep_spmm": (ctypes.c_int, [_M, _P, ctypes.c_int32, ctypes.c_double, _vp, ctypes.c_int64,
@@ -359,6 +361,18 @@ def msrep_spmv(A: DeviceMatrix, part: DevicePartition, alpha: float, x,
     _check(lib().msrep_spmv(ctypes.byref(A.c), ctypes.byref(part.c),
                             float(alpha), _ptr(x), float(beta), _ptr(y), xy,
                             flags, _ptr(workspace), _stream(stream)))
+
+
+def msrep_access_floor(mode: int, idx, val, vec, idx2=None, sink=None, stream=None):
+    """The access-pattern floor kernel (see include/msrep.h): mode 0 gather,
+    1 gather plus a second index stream, 2 scatter-add, 3 scatter-add to the
+    permuted slot.  vec.numel() must be a power of two."""
+    import torch
+    if sink is None:
+        sink = torch.zeros(1, dtype=torch.float64, device=vec.device)
+    _check(lib().msrep_access_floor(int(mode), _ptr(idx), _ptr(idx2) if idx2 is not None else None,
+                                    _ptr(val), _ptr(vec), int(val.numel()), int(vec.numel()),
+                                    _ptr(sink), _stream(stream)))
 
 
 def msrep_spmm_workspace_size(A: DeviceMatrix, part: DevicePartition, k: int) -> int:
