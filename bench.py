@@ -401,6 +401,7 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers: x up, SpMV, y down
     e2e = run_e2e(M, pairs, args, dev)
+    p_sweep = run_p_sweep(M, pairs, args) if not args.skip_p_sweep else None
 
     # low-precision form on the R-MAT matrix (CSR)
     prec = run_precision(M, args, dev) if not args.skip_precision else None
@@ -427,6 +428,8 @@ def run_ours(args):
         "gpu_launches": args.steps * sum(2 if p[1] != "csc" else 3 for p in pairs),
         "clocks": clk.summary(),
     }
+    if p_sweep:
+        line["p_sweep"] = p_sweep
     if prec:
         line["precision"] = prec
     if batched:
@@ -442,6 +445,33 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_p_sweep(M, pairs, args, Ps=(148, 148 * 4, 148 * 16, 148 * 64), reps=20):
+    """Main-kernel time of every (matrix, format) pair at P = 148 .. 148*64
+    partitions (the sweep of the partition count), FP64, default tile."""
+    import torch
+    out = {}
+    for (name, fmt, A, _, x, y, _, _, _) in pairs:
+        row = {}
+        for P in Ps:
+            part = M.DevicePartition(A, P, tile=args.tile, device=x.device)
+            M.msrep_partition(A, part)
+            ws = M.alloc_workspace(A, part, device=x.device)
+            for _ in range(3):
+                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            M.native.msrep_profile_events(s0, s1)
+            tot = 0.0
+            for _ in range(reps):
+                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+                s1.synchronize()
+                tot += s0.elapsed_time(s1)
+            M.native.msrep_profile_events(None, None)
+            row[str(P)] = 1e3 * tot / reps
+            del part, ws
+        out[f"{name}/{fmt}"] = row
+    return {"kernel_us": out, "P": list(Ps)}
 
 
 def access_floor_us(M, A, x, reps):
@@ -755,7 +785,13 @@ def run_profile_case(args):
     y = torch.empty(a.m, dtype=xt, device=dev)
     ws = M.alloc_workspace(A, part, device=dev)
     flags = M.MSREP_STREAM_TMA if args.stream_tma else 0
-    if args.profile_k > 0:
+    if args.profile_floor:
+        # the access-pattern floor kernel on the same arrays
+        vec = x if args.profile != "csc" else torch.zeros(a.m, dtype=torch.float64, device=dev)
+        mode = {"csr": 0, "coo": 1, "csc": 3}[args.profile]
+        for _ in range(args.reps):
+            M.native.msrep_access_floor(mode, A.idx, A.val, vec, idx2=A.idx2)
+    elif args.profile_k > 0:
         # k right-hand sides (CSR): msrep_spmm on k shifted copies of x
         X = torch.stack([torch.roll(x, v) for v in range(args.profile_k)])
         Y = torch.empty((args.profile_k, a.m), dtype=xt, device=dev)
@@ -829,6 +865,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-precision", action="store_true")
+    ap.add_argument("--skip-p-sweep", action="store_true",
+                    help="skip the P = 148 .. 148*64 sweep of the main kernels")
     ap.add_argument("--batched-count", type=int, default=512,
                     help="matrices in the batched-form measurement (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
@@ -839,6 +877,8 @@ def main():
     ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")
     ap.add_argument("--profile-dtype", choices=["f64", "f32", "bf16"], default="f64")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--profile-floor", action="store_true",
+                    help="profile case: the access-pattern floor kernel instead of the SpMV")
     ap.add_argument("--profile-k", type=int, default=0,
                     help="profile case: msrep_spmm with this many vectors (CSR) instead of msrep_spmv")
     ap.add_argument("--stream-tma", action="store_true",
