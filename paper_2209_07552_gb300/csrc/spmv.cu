@@ -435,10 +435,18 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
 // fix-up: rows split between tiles, merged in tile (= partition) order
 // ---------------------------------------------------------------------------
 
+// Kernels launched with launch_dependent may start while the kernel before
+// them on the stream drains; they wait here (a no-op without that launch
+// attribute) before reading what it wrote.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // One warp per 32 consecutive tiles (grid-stride over warps).
 template <class X, class View>
 __global__ void fixup_split_rows(View v, const double *head, const double *tail,
                                  X *y, double alpha, double beta) {
+  grid_dependency_wait();
   const int T = v.count();
   const int64_t warp = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
@@ -465,6 +473,7 @@ __global__ void csc_prepare(const int32_t *hot, double *yperm, int64_t perm_n, d
 // FP64 CSC, skewed matrix: y[r] = acc[slot(r)] + beta * y[r].
 __global__ void csc_unpermute(const int32_t *hot, const double *yperm, uint32_t pmask,
                               double *y, int64_t m, double beta) {
+  grid_dependency_wait();
   if (!csc_skewed(hot, yperm)) return;
   for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < m;
        r += int64_t(gridDim.x) * blockDim.x) {
@@ -478,6 +487,7 @@ __global__ void csc_unpermute(const int32_t *hot, const double *yperm, uint32_t 
 __global__ void finish_csc_f32(const int32_t *hot, const double *yperm, uint32_t pmask,
                                const double *yacc, float *y, int64_t m, double alpha,
                                double beta) {
+  grid_dependency_wait();
   const bool skew = csc_skewed(hot, yperm);
   for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < m;
        r += int64_t(gridDim.x) * blockDim.x) {
@@ -597,6 +607,27 @@ static msrep_status kernel_occupancy(K kernel, size_t smem, int want_blocks, int
   return MSREP_OK;
 }
 
+// Launches a kernel that depends on the previous one on the stream as a
+// programmatic dependent launch: its blocks may be scheduled while that
+// kernel's last blocks drain, hiding the launch gap; the kernel itself waits
+// (grid_dependency_wait) before touching the results.
+template <class... KArgs, class... Args>
+static msrep_status launch_dependent(void (*kernel)(KArgs...), int64_t grid, int block,
+                                     cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(std::max<int64_t>(grid, 1)));
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MSREP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+  return MSREP_OK;
+}
+
 // Launches the streaming kernel (dynamic shared-memory stages) unless the
 // caller asked for direct loads.  Grid: resident blocks x SMs, capped by the
 // number of tiles.
@@ -651,10 +682,8 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   int64_t fg = std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count());
-  fixup_split_rows<typename Pol::X, CsrTileView>
-      <<<static_cast<int>(std::max<int64_t>(fg, 1)), 256, 0, st>>>(
-          v, w.head, w.tail, a.y, alpha, beta);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_dependent(fixup_split_rows<typename Pol::X, CsrTileView>, fg, 256, st, v,
+                             w.head, w.tail, a.y, alpha, beta));
   return MSREP_OK;
 }
 
@@ -689,10 +718,8 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
                          (flags & MSREP_STREAM_TMA) == 0, T, st, a));
   CooTileView v{A->idx2, p->start_idx, p->end_idx, A->nnz, a.G, a.np, A->m};
   int64_t fg = std::min<int64_t>(ceil_div(T, 256), 4 * sm_count());
-  fixup_split_rows<typename Pol::X, CooTileView>
-      <<<static_cast<int>(std::max<int64_t>(fg, 1)), 256, 0, st>>>(
-          v, w.head, w.tail, a.y, alpha, beta);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_dependent(fixup_split_rows<typename Pol::X, CooTileView>, fg, 256, st, v,
+                             w.head, w.tail, a.y, alpha, beta));
   return MSREP_OK;
 }
 
@@ -742,15 +769,15 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
                          (sizeof(double) + sizeof(int32_t)) * kWarps * (32 * IPT + 8), 0,
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   if (kF64) {
-    if (w.perm) {
-      csc_unpermute<<<sg, 256, 0, st>>>(a.hot, a.yperm, a.pmask, static_cast<double *>(y), m,
-                                        beta);
-      MSREP_CUDA_TRY(cudaGetLastError());
-    }
+    if (w.perm)
+      MSREP_TRY(launch_dependent(csc_unpermute, sg, 256, st, a.hot,
+                                 static_cast<const double *>(a.yperm), a.pmask,
+                                 static_cast<double *>(y), m, beta));
   } else {
-    finish_csc_f32<<<sg, 256, 0, st>>>(a.hot, a.yperm, a.pmask, w.yacc, static_cast<float *>(y),
-                                       m, alpha, beta);
-    MSREP_CUDA_TRY(cudaGetLastError());
+    MSREP_TRY(launch_dependent(finish_csc_f32, sg, 256, st, a.hot,
+                               static_cast<const double *>(a.yperm), a.pmask,
+                               static_cast<const double *>(w.yacc), static_cast<float *>(y), m,
+                               alpha, beta));
   }
   return MSREP_OK;
 }
