@@ -85,6 +85,13 @@ struct StageGeom {
   static constexpr size_t BLOCK = kWarps * WARP;
 };
 
+// Kernels launched with launch_dependent may start while the kernel before
+// them on the stream drains; they wait here (a no-op without that launch
+// attribute) before reading what it wrote.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // loads the elements [e0, e1) of arr that the bulk copy could not cover
 template <class T>
 __device__ __forceinline__ void fill_tail(T *dst, const T *arr, const SegCopy &c, int64_t e0,
@@ -96,6 +103,7 @@ __device__ __forceinline__ void fill_tail(T *dst, const T *arr, const SegCopy &c
 template <class Pol, int IPT>
 __global__ void __launch_bounds__(kThreads, MSREP_MINB) csr_direct(CsrArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
+  grid_dependency_wait();
   __shared__ int32_t s_rp[kWarps][32 * IPT + 8];
   const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int stride = gridDim.x * kWarps;
@@ -131,6 +139,7 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) csr_direct(CsrArgs<Pol> 
 template <class Pol, int IPT>
 __global__ void __launch_bounds__(kThreads) csr_stream(CsrArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
+  grid_dependency_wait();
   using V = typename Pol::V;
   using G = StageGeom<V, IPT, 2>;
   constexpr int S = G::S;
@@ -212,6 +221,7 @@ __global__ void __launch_bounds__(kThreads) csr_stream(CsrArgs<Pol> a, const int
 
 template <class Pol, int IPT>
 __global__ void __launch_bounds__(kThreads, MSREP_MINB) coo_direct(CooArgs<Pol> a) {
+  grid_dependency_wait();
   const int T = a.np * a.G, wid = threadIdx.x >> 5;
   const int stride = gridDim.x * kWarps;
   // the next tile's range is loaded while the current one is processed
@@ -229,6 +239,7 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) coo_direct(CooArgs<Pol> 
 
 template <class Pol, int IPT>
 __global__ void __launch_bounds__(kThreads) coo_stream(CooArgs<Pol> a) {
+  grid_dependency_wait();
   using V = typename Pol::V;
   using G = StageGeom<V, IPT, 2>;
   constexpr int S = G::S;
@@ -309,6 +320,7 @@ template <class Pol, int IPT>
 // budget of the x and column-pointer stages.
 __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
+  grid_dependency_wait();
   // dynamic shared memory: per warp, x values then column pointers
   extern __shared__ __align__(16) unsigned char dsm[];
   constexpr int CAP = 32 * IPT + 8;
@@ -344,6 +356,7 @@ __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const 
 template <class Pol, int IPT>
 __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
+  grid_dependency_wait();
   using V = typename Pol::V;
   using G = StageGeom<V, IPT, 2>;
   constexpr int S = G::S;
@@ -434,13 +447,6 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
 // ---------------------------------------------------------------------------
 // fix-up: rows split between tiles, merged in tile (= partition) order
 // ---------------------------------------------------------------------------
-
-// Kernels launched with launch_dependent may start while the kernel before
-// them on the stream drains; they wait here (a no-op without that launch
-// attribute) before reading what it wrote.
-__device__ __forceinline__ void grid_dependency_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
 
 // One warp per 32 consecutive tiles (grid-stride over warps).
 template <class X, class View>
@@ -613,11 +619,11 @@ static msrep_status kernel_occupancy(K kernel, size_t smem, int want_blocks, int
 // (grid_dependency_wait) before touching the results.
 template <class... KArgs, class... Args>
 static msrep_status launch_dependent(void (*kernel)(KArgs...), int64_t grid, int block,
-                                     cudaStream_t st, Args... args) {
+                                     cudaStream_t st, size_t smem, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(std::max<int64_t>(grid, 1)));
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -644,11 +650,10 @@ static msrep_status launch_tiles(KS kstream, KD kdirect, size_t stream_smem, siz
   if (grid < 1) grid = 1;
   prof_begin(st);
   if (direct)
-    kdirect<<<static_cast<int>(grid), kThreads, direct_smem, st>>>(args...);
+    MSREP_TRY(launch_dependent(kdirect, grid, kThreads, st, direct_smem, args...));
   else
-    kstream<<<static_cast<int>(grid), kThreads, stream_smem, st>>>(args...);
+    MSREP_TRY(launch_dependent(kstream, grid, kThreads, st, stream_smem, args...));
   prof_end(st);
-  MSREP_CUDA_TRY(cudaGetLastError());
   return MSREP_OK;
 }
 
@@ -682,7 +687,7 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   int64_t fg = std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count());
-  MSREP_TRY(launch_dependent(fixup_split_rows<typename Pol::X, CsrTileView>, fg, 256, st, v,
+  MSREP_TRY(launch_dependent(fixup_split_rows<typename Pol::X, CsrTileView>, fg, 256, st, 0, v,
                              w.head, w.tail, a.y, alpha, beta));
   return MSREP_OK;
 }
@@ -718,7 +723,7 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
                          (flags & MSREP_STREAM_TMA) == 0, T, st, a));
   CooTileView v{A->idx2, p->start_idx, p->end_idx, A->nnz, a.G, a.np, A->m};
   int64_t fg = std::min<int64_t>(ceil_div(T, 256), 4 * sm_count());
-  MSREP_TRY(launch_dependent(fixup_split_rows<typename Pol::X, CooTileView>, fg, 256, st, v,
+  MSREP_TRY(launch_dependent(fixup_split_rows<typename Pol::X, CooTileView>, fg, 256, st, 0, v,
                              w.head, w.tail, a.y, alpha, beta));
   return MSREP_OK;
 }
@@ -770,11 +775,11 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   if (kF64) {
     if (w.perm)
-      MSREP_TRY(launch_dependent(csc_unpermute, sg, 256, st, a.hot,
+      MSREP_TRY(launch_dependent(csc_unpermute, sg, 256, st, 0, a.hot,
                                  static_cast<const double *>(a.yperm), a.pmask,
                                  static_cast<double *>(y), m, beta));
   } else {
-    MSREP_TRY(launch_dependent(finish_csc_f32, sg, 256, st, a.hot,
+    MSREP_TRY(launch_dependent(finish_csc_f32, sg, 256, st, 0, a.hot,
                                static_cast<const double *>(a.yperm), a.pmask,
                                static_cast<const double *>(w.yacc), static_cast<float *>(y), m,
                                alpha, beta));
