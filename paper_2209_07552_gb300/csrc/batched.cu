@@ -96,6 +96,7 @@ template <class X>
 __global__ void batched_fixup(const BatchItem *items, const int64_t *toff, int count,
                               void *const *ys, const double *head, const double *tail,
                               double alpha, double beta) {
+  grid_dependency_wait();
   const int64_t total = __ldg(toff + count);
   for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < total;
        g += int64_t(gridDim.x) * blockDim.x) {
@@ -207,8 +208,8 @@ msrep_status launch_batched(const BatchItem *items, const int64_t *toff, int cou
                                                        alpha, beta, finish, comp, err);
     MSREP_CUDA_TRY(cudaGetLastError());
     const int64_t fg = std::max<int64_t>(1, std::min<int64_t>(ceil_div(T, 256), 4 * sms));
-    fix<<<static_cast<int>(fg), 256, 0, st>>>(items, toff, count, ys, head, tail, alpha, beta);
-    MSREP_CUDA_TRY(cudaGetLastError());
+    MSREP_TRY(launch_dependent(fix, fg, 256, st, 0, items, toff, count, ys, head, tail, alpha,
+                               beta));
     return MSREP_OK;
   };
   switch (val_dtype) {

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 
@@ -136,6 +137,38 @@ inline int64_t coo_tiles_per_part(int64_t nnz, int32_t np, int32_t tile) {
   int64_t per = ceil_div(nnz, np);
   int64_t g = ceil_div(per, tile);
   return g < 1 ? 1 : g;
+}
+
+// ---------------------------------------------------------------------------
+// programmatic dependent launch
+// ---------------------------------------------------------------------------
+
+// Kernels launched with launch_dependent may start while the kernel before
+// them on the stream drains; they wait here (a no-op without that launch
+// attribute) before reading what it wrote.
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Launches a kernel that depends on the previous one on the stream as a
+// programmatic dependent launch: its blocks may be scheduled while that
+// kernel's last blocks drain, hiding the launch gap; the kernel itself waits
+// (grid_dependency_wait) before touching the results.
+template <class... KArgs, class... Args>
+inline msrep_status launch_dependent(void (*kernel)(KArgs...), int64_t grid, int block,
+                                     cudaStream_t st, size_t smem, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(std::max<int64_t>(grid, 1)));
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MSREP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+  return MSREP_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(kKThreads, 2) csr_spmm_direct(SpmmArgs<Pol, KP
                                                                 int64_t nnz) {
   __shared__ int32_t s_rp[kKWarps][32 * kKMaxIPT + 8];
   extern __shared__ __align__(16) unsigned char s_stage[];
+  grid_dependency_wait();
   const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char *stage = s_stage + threadIdx.x * SpmmStage<Pol, KP>::LANE;
   for (int b = blockIdx.x * kKWarps + wid; b < T; b += gridDim.x * kKWarps) {
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(kKThreads, 2) csr_spmm_direct(SpmmArgs<Pol, KP
 template <class X, int KP>
 __global__ void fixup_spmm(CsrTileView v, const double *head, const double *tail, X *y,
                            int64_t ldy, int k, double alpha, double beta) {
+  grid_dependency_wait();
   const int T = v.count();
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < T; b += gridDim.x * blockDim.x)
     fixup_tile_k<X, KP>(v, T, b, head, tail, y, ldy, k, alpha, beta);
@@ -155,13 +157,13 @@ static msrep_status run_spmm(const msrep_matrix *A, const msrep_partition *p, in
   MSREP_TRY(blocks_of(csr_spmm_direct<Pol, KP>, dyn, 2, &nb));
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.tmax, kKWarps),
                                                              int64_t(nb) * sm_count()));
-  csr_spmm_direct<Pol, KP><<<static_cast<int>(grid), kKThreads, dyn, st>>>(a, n_tiles, A->nnz);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_dependent(csr_spmm_direct<Pol, KP>, grid, kKThreads, st, dyn, a, n_tiles,
+                             A->nnz));
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   const int64_t fg = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count()));
-  fixup_spmm<X, KP><<<static_cast<int>(fg), 256, 0, st>>>(v, head, tail, a.y, ldy, k, alpha,
-                                                          beta);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_dependent(fixup_spmm<X, KP>, fg, 256, st, 0, v,
+                             static_cast<const double *>(head), static_cast<const double *>(tail),
+                             a.y, ldy, k, alpha, beta));
   return MSREP_OK;
 }
 
@@ -203,6 +205,7 @@ __global__ void __launch_bounds__(kKThreads, 2) batched_spmm(const BatchItem *it
   constexpr int KP = kBatchWidth;
   __shared__ int32_t s_rp[kKWarps][32 * kKMaxIPT + 8];
   extern __shared__ __align__(16) unsigned char s_stage[];
+  grid_dependency_wait();
   unsigned char *stage = s_stage + threadIdx.x * SpmmStage<Pol, KP>::LANE;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t total = __ldg(toff + count);
@@ -248,6 +251,7 @@ __global__ void __launch_bounds__(kKThreads, 2) batched_spmm(const BatchItem *it
 template <class X>
 __global__ void batched_fixup_k(const BatchItem *items, const int64_t *toff, int count,
                                 void *const *ys, const double *head, const double *tail) {
+  grid_dependency_wait();
   constexpr int KP = kBatchWidth;
   const int64_t total = __ldg(toff + count);
   for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < total;
@@ -297,13 +301,11 @@ msrep_status launch_batched_k(const BatchItem *items, const int64_t *toff, int c
   MSREP_TRY(blocks_of(batched_spmm<PolF32<float>>, dyn, 2, &nb));
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(total_tiles, kKWarps),
                                                              int64_t(nb) * sms));
-  batched_spmm<PolF32<float>><<<static_cast<int>(grid), kKThreads, dyn, st>>>(
-      items, toff, count, xt, ys, head, tail, comp);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_dependent(batched_spmm<PolF32<float>>, grid, kKThreads, st, dyn, items, toff,
+                             count, static_cast<const void *const *>(xt), ys, head, tail, comp));
   const int64_t fg = std::max<int64_t>(1, std::min<int64_t>(ceil_div(total_tiles, 256), 4 * sms));
-  batched_fixup_k<float><<<static_cast<int>(fg), 256, 0, st>>>(items, toff, count, ys, head,
-                                                               tail);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_dependent(batched_fixup_k<float>, fg, 256, st, 0, items, toff, count, ys,
+                             static_cast<const double *>(head), static_cast<const double *>(tail)));
   return MSREP_OK;
 }
 

@@ -85,13 +85,6 @@ struct StageGeom {
   static constexpr size_t BLOCK = kWarps * WARP;
 };
 
-// Kernels launched with launch_dependent may start while the kernel before
-// them on the stream drains; they wait here (a no-op without that launch
-// attribute) before reading what it wrote.
-__device__ __forceinline__ void grid_dependency_wait() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-}
-
 // loads the elements [e0, e1) of arr that the bulk copy could not cover
 template <class T>
 __device__ __forceinline__ void fill_tail(T *dst, const T *arr, const SegCopy &c, int64_t e0,
@@ -466,6 +459,7 @@ __global__ void fixup_split_rows(View v, const double *head, const double *tail,
 // the FP64 accumulator zeroed on the low-precision path.
 __global__ void csc_prepare(const int32_t *hot, double *yperm, int64_t perm_n, double *yrow,
                             int64_t m, double beta, int row_is_y) {
+  grid_dependency_wait();
   const int64_t i0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   const int64_t step = int64_t(gridDim.x) * blockDim.x;
   if (csc_skewed(hot, yperm)) {
@@ -613,27 +607,6 @@ static msrep_status kernel_occupancy(K kernel, size_t smem, int want_blocks, int
   return MSREP_OK;
 }
 
-// Launches a kernel that depends on the previous one on the stream as a
-// programmatic dependent launch: its blocks may be scheduled while that
-// kernel's last blocks drain, hiding the launch gap; the kernel itself waits
-// (grid_dependency_wait) before touching the results.
-template <class... KArgs, class... Args>
-static msrep_status launch_dependent(void (*kernel)(KArgs...), int64_t grid, int block,
-                                     cudaStream_t st, size_t smem, Args... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(static_cast<unsigned>(std::max<int64_t>(grid, 1)));
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  MSREP_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
-  return MSREP_OK;
-}
-
 // Launches the streaming kernel (dynamic shared-memory stages) unless the
 // caller asked for direct loads.  Grid: resident blocks x SMs, capped by the
 // number of tiles.
@@ -760,12 +733,13 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
     a.scale = alpha;
     a.scaled = alpha != 1.0;
     if (w.perm || beta != 1.0)
-      csc_prepare<<<sg, 256, 0, st>>>(a.hot, a.yperm, pn, a.yacc, m, beta, 1);
+      MSREP_TRY(launch_dependent(csc_prepare, sg, 256, st, 0, a.hot, a.yperm, pn, a.yacc, m, beta,
+                                 1));
   } else {
     a.yacc = w.yacc;
     a.scale = 1.0;
     a.scaled = false;
-    csc_prepare<<<sg, 256, 0, st>>>(a.hot, a.yperm, pn, w.yacc, m, 0.0, 0);
+    MSREP_TRY(launch_dependent(csc_prepare, sg, 256, st, 0, a.hot, a.yperm, pn, w.yacc, m, 0.0, 0));
   }
   MSREP_CUDA_TRY(cudaGetLastError());
   MSREP_TRY(launch_tiles(csc_stream<Pol, IPT>, csc_direct<Pol, IPT>,
