@@ -217,6 +217,17 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def workload_config(args, world):
+    """The workload both arms report (the reference arm runs the oracle's
+    plain SpMV over the same six (matrix, format) pairs)."""
+    return {"workload": "rmat20_16Mnnz+laplace2048", "formats": list(FORMATS),
+            "P": args.P, "tile": args.tile or 512, "alpha": 1.0, "beta": 0.0,
+            "streams": args.streams,
+            "l2": "inputs larger than L2 (each matrix 222-403 MB); no flush",
+            "parallelism": (f"{world} replicas, one per GPU, no data-path collective"
+                            if world > 1 else "single GPU")}
+
+
 def load_workload():
     return {"rmat": I.rmat_full(), "laplace": I.laplace_full()}
 
@@ -263,7 +274,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "rmat20_16Mnnz+laplace2048", "formats": list(FORMATS)},
+        "config": workload_config(args, 1),
         "cpu_baseline": {"value": val, "unit": "GFLOP/s", "cores": 1,
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": val, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
@@ -413,12 +424,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded R-MAT and 2D Laplacian)",
-        "config": {"workload": "rmat20_16Mnnz+laplace2048", "formats": list(FORMATS),
-                   "P": P, "tile": args.tile or 512, "alpha": 1.0, "beta": 0.0,
-                   "streams": args.streams,
-                   "l2": "inputs larger than L2 (each matrix 222-403 MB); no flush",
-                   "parallelism": (f"{world} replicas, one per GPU, no data-path collective"
-                        if world > 1 else "single GPU")},
+        "config": workload_config(args, world),
         "roofline": roof,
         "per_kernel": kern,
         "partition_ms": part_ms,
