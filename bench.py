@@ -646,7 +646,12 @@ def run_serving(M, args, dev):
     arrivals = I.poisson_arrivals(args.serve_rate, args.serve_seconds, seed)
     pick = g.integers(0, len(ids), arrivals.shape[0])
     ks = g.integers(1, 9, arrivals.shape[0])
-    pools = [[] for _ in mats]
+    # Page-locked y buffers are allocated up front: allocating page-locked
+    # memory in the submit loop takes milliseconds (and can wait on the
+    # device), which delayed submissions into bursts and showed up as p99.
+    pools = [[M.native.pinned_empty((8 * a.m,)) for _ in range(6 if a.m > (1 << 18) else 16)]
+             for a in mats]
+    misses = [0]
     lock = threading.Lock()
     q = queue.Queue()
 
@@ -660,10 +665,16 @@ def run_serving(M, args, dev):
             with lock:
                 pools[j].append(t.y)
 
-    th = threading.Thread(target=waiter, daemon=True)
-    th.start()
+    # several waiters, so a slow request holds back only its own buffer
+    ths = [threading.Thread(target=waiter, daemon=True) for _ in range(8)]
+    for th in ths:
+        th.start()
     warm = min(1.0, 0.2 * args.serve_seconds)
     reset_done = False
+    # the submit loop spins between arrivals; a short interpreter switch
+    # interval lets the waiters hand buffers back without 5 ms delays
+    switch = sys.getswitchinterval()
+    sys.setswitchinterval(1e-4)
     t0 = time.perf_counter()
     for i in range(arrivals.shape[0]):
         target = t0 + arrivals[i]
@@ -680,18 +691,23 @@ def run_serving(M, args, dev):
         with lock:
             y = pools[j].pop() if pools[j] else None
         if y is None:
+            misses[0] += 1
             y = M.native.pinned_empty((8 * mats[j].m,))
         t = S.submit(ids[j], X[j][:k], y)
         q.put((j, t))
     sent = time.perf_counter() - t0
-    q.put(None)
-    th.join()
+    for _ in ths:
+        q.put(None)
+    for th in ths:
+        th.join()
+    sys.setswitchinterval(switch)
     st = S.stats()
     S.close()
     st.update({"offered_rate": arrivals.shape[0] / args.serve_seconds,
                "achieved_submit_s": sent, "matrices": len(mats),
                "window_s": args.serve_seconds, "discarded_warmup_s": warm,
-               "budget_bytes": 60 << 30, "resident_bytes_after_register": resident})
+               "budget_bytes": 60 << 30, "resident_bytes_after_register": resident,
+               "y_buffer_allocations_in_loop": misses[0]})
     return st
 
 
