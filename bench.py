@@ -144,19 +144,24 @@ _UNIT = {"byte": 1.0, "kbyte": 1e3, "mbyte": 1e6, "gbyte": 1e9,
          "ns": 1e-9, "us": 1e-6, "ms": 1e-3}
 
 
+# the sources that make the single-matrix SpMV kernels and their tile plans
+STAMP_SOURCES = ("csrc/common.cuh", "csrc/tma.cuh", "csrc/spmv_core.cuh", "csrc/spmv.cu",
+                 "csrc/partition.cu")
+
+
 def source_stamp() -> str:
-    """Hash of the CUDA sources, the public header and the code-generation
-    flags of libmsrep.so (independent of where the repository lives)."""
+    """Hash of the sources of the single-matrix SpMV kernels (and their tile
+    plans), the public header and the code-generation flags of libmsrep.so,
+    independent of where the repository lives."""
     import hashlib
     from paper_2209_07552_gb300 import build as B
     h = hashlib.sha1(" ".join(B.ARCH + [f for f in B.NVCC_FLAGS if not f.startswith("-I")]).encode())
-    for d in (B.CSRC, B.INCLUDE):
-        for name in sorted(os.listdir(d)):
-            path = os.path.join(d, name)
-            if os.path.isfile(path) and name.endswith((".cu", ".cuh", ".cpp", ".h")):
-                h.update(name.encode())
-                with open(path, "rb") as f:
-                    h.update(f.read())
+    paths = [os.path.join(os.path.dirname(B.CSRC), p) for p in STAMP_SOURCES]
+    paths.append(os.path.join(B.INCLUDE, "msrep.h"))
+    for path in paths:
+        h.update(os.path.basename(path).encode())
+        with open(path, "rb") as f:
+            h.update(f.read())
     return h.hexdigest()
 
 

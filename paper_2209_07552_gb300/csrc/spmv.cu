@@ -33,9 +33,11 @@ int32_t effective_tile(int32_t tile);
 static __device__ int g_kernel_err = 0;
 
 int *kernel_err_ptr() {
+  static std::mutex mu;
   static int *cached[64] = {nullptr};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
   if (!cached[dev]) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_kernel_err) != cudaSuccess) return nullptr;
@@ -56,8 +58,9 @@ int *kernel_err_ptr() {
 // passes through L1, which is left to the x gathers.
 // Direct variant (default): no staging; each lane reads its groups with
 // 256-bit global loads that bypass L1.  On GB300 the SpMV is bound by the
-// FP64 pipe and by L2 sector requests for x, not by DRAM latency, and the
-// direct variant keeps twice as many warps resident and all of L1 for x.
+// x gathers (one L1 line lookup each, and an L2 sector request on a miss)
+// and the FP64 pipe, not by DRAM latency; the direct variant keeps more
+// warps resident and more of L1 for x.
 // ---------------------------------------------------------------------------
 
 // Minimum resident blocks per SM asked of the register allocator for the
