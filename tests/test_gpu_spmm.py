@@ -132,3 +132,28 @@ def test_rejects_bad_arguments():
     with pytest.raises(M.MsrepError):
         M.msrep_spmm(C, cpart, 1.0, X[:2], 0.0, Y[:2],
                      workspace=torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
+
+
+@pytest.mark.parametrize("k", [1, 3, 8])
+def test_empty_matrix_and_empty_rows(k):
+    """No nonzeros: Y = beta * Y for every vector; a matrix whose rows are
+    mostly empty: the oracle's product, exactly (integer data)."""
+    import torch
+
+    import oracle as O
+    import paper_2209_07552_gb300 as M
+    a = I.csr_from_triplets(37, 11, [], [], [])
+    A, part = _setup(a, "f64", 4)
+    Y0 = np.stack([I.y_vector(a.m, 700 + v) for v in range(k)])
+    Y = torch.from_numpy(Y0.copy()).cuda()
+    M.msrep_spmm(A, part, 1.0, torch.zeros((k, a.n), dtype=torch.float64, device="cuda"), 2.0, Y)
+    assert np.array_equal(Y.cpu().numpy(), 2.0 * Y0)
+    rows = [3, 3, 40, 41, 41, 41, 900]
+    cols = [0, 5, 2, 2, 3, 9, 1]
+    b, _ = I.integer_twin(I.csr_from_triplets(1000, 10, rows, cols, np.ones(len(rows))), seed=3)
+    B, bpart = _setup(b, "f64", 3, 256)
+    X = np.stack([I.integer_twin(b, seed=10 + v)[1] for v in range(k)])
+    Yb = torch.full((k, b.m), float("nan"), dtype=torch.float64, device="cuda")
+    M.msrep_spmm(B, bpart, 1.0, torch.from_numpy(X).cuda(), 0.0, Yb)
+    want = O.spmm_csr(b.m, b.row_ptr, b.col_idx, b.val, X.T.copy()).T
+    assert np.array_equal(Yb.cpu().numpy(), want)
