@@ -42,7 +42,7 @@ int sm_count();
 // Sets a kernel's preferred shared-memory carveout to the smallest share of
 // the SM's unified L1/shared memory that holds `blocks` resident blocks
 // (static + dyn_smem bytes each), leaving the rest to L1.  The x gathers of
-// the CSR kernels hit L1 (17-60%); with the driver's default carveout R-MAT
+// the CSR kernels hit L1 (17-60%); with CUDA's default carveout R-MAT
 // CSR took 108 us, with the smallest one 103 us.  No-op for kernels without
 // shared memory (they keep the default, all L1).  Current device.
 msrep_status set_min_carveout(const void *kernel, size_t dyn_smem, int blocks);

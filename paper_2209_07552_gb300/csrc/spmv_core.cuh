@@ -13,11 +13,11 @@
 //  * inside a tile the nonzeros are split evenly over the 32 lanes (the same
 //    floor(i*nnz/P) rule), and each lane sums its contiguous run with one
 //    fused multiply-add per nonzero.  On GB300 the FP64 pipe sustains about
-//    two lane operations per clock per SM, so the plain FP64 path is
-//    co-limited by FP64 issue and HBM; one DFMA per nonzero, equal nonzero
-//    counts per lane (no idle lanes in the DFMA warp instructions) and no
-//    FP64 work for row finishing when alpha = 1, beta = 0 keep it near the
-//    memory bound.
+//    two lane operations per clock per SM, so one DFMA per nonzero, equal
+//    nonzero counts per lane (no idle lanes in the DFMA warp instructions)
+//    and no FP64 work for row finishing when alpha = 1, beta = 0 keep the
+//    plain FP64 path from being FP64-bound; the x gathers (one L1 line
+//    lookup each) bound it instead.
 //  * rows split between lanes are merged by a warp segmented scan (skipped
 //    when every lane finished a row), rows split between tiles by the fix-up
 //    kernel in tile order, with beta applied once (Sec. 3.2.1, Sec. 4.3).
