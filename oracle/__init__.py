@@ -69,6 +69,14 @@ def _lib():
                 ctypes.c_int64, _i32p, ctypes.c_int32, _i32p, _i32p, _i32p,
                 _i32p, _u8p]
             lib.ref_partition_coo.restype = ctypes.c_int
+            lib.ref_partition_coo_unsorted.argtypes = [
+                ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
+                _i32p, _i32p, _u8p]
+            lib.ref_partition_coo_unsorted.restype = ctypes.c_int
+            lib.ref_pspmv_coo_scatter.argtypes = [
+                ctypes.c_int32, _i32p, _i32p, _f64p, ctypes.c_int32, _i32p,
+                _i32p, ctypes.c_double, _f64p, ctypes.c_double, _f64p]
+            lib.ref_pspmv_coo_scatter.restype = ctypes.c_int
             lib.ref_partition_local_coo.argtypes = [
                 _i32p, ctypes.c_int32, _i32p, _i32p, _i32p, _i32p]
             lib.ref_spmv_csr.argtypes = [
@@ -183,6 +191,39 @@ def partition_coo(row_idx, np_: int, with_local: bool = False):
     return out
 
 
+def partition_coo_by_col(col_idx, np_: int, with_local: bool = False):
+    """pCOO of a COO matrix sorted by (col, row), reading R9: Alg. 6 with
+    the column index as the major index (start/end column, split-column
+    flag; with ``with_local`` the local column index col - start_col)."""
+    return partition_coo(col_idx, np_, with_local)
+
+
+def partition_coo_unsorted(row_idx, m: int, np_: int, with_local: bool = False):
+    """pCOO of a COO matrix in no particular order, reading R9: the
+    nonzero ranges of Alg. 6; every non-empty partition spans rows
+    0..m-1, flags 0.  With ``with_local``, the local row index relative to
+    start_row = 0, i.e. the row index itself."""
+    row_idx = _c(row_idx, np.int32)
+    nnz = row_idx.shape[0]
+    out = {k: np.empty(np_, np.int32) for k in
+           ("start_idx", "end_idx", "start_major", "end_major")}
+    out["start_flag"] = np.empty(np_, np.uint8)
+    rc = _lib().ref_partition_coo_unsorted(
+        nnz, m, np_, _p(out["start_idx"], _i32p), _p(out["end_idx"], _i32p),
+        _p(out["start_major"], _i32p), _p(out["end_major"], _i32p),
+        _p(out["start_flag"], _u8p))
+    if rc != 0:
+        raise ValueError("invalid partition arguments")
+    if with_local:
+        lrow = np.empty(max(nnz, 1), np.int32)
+        _lib().ref_partition_local_coo(
+            _p(row_idx, _i32p), np_, _p(out["start_idx"], _i32p),
+            _p(out["end_idx"], _i32p), _p(out["start_major"], _i32p),
+            _p(lrow, _i32p))
+        out["local"] = lrow[:nnz]
+    return out
+
+
 # --------------------------------------------------------------------------
 # Plain SpMV (Sec. 2.2, Alg. 1 reading R1).
 # --------------------------------------------------------------------------
@@ -284,6 +325,26 @@ def pspmv_coo(m, row_idx, col_idx, val, part, x, alpha=1.0, beta=0.0, y=None):
     """Alg. 7: the COO analogue of Alg. 3 on row-sorted input."""
     return _pspmv(_lib().ref_pspmv_coo, m, row_idx, col_idx, val, part, x,
                   alpha, beta, y)
+
+
+def pspmv_coo_scatter(m, row_idx, col_idx, val, part, x, alpha=1.0, beta=0.0,
+                      y=None):
+    """Partitioned SpMV of a COO matrix sorted by column or in no order
+    (reading R9): a full m-vector of partials per partition, summed in
+    partition order."""
+    row_idx = _c(row_idx, np.int32)
+    col_idx = _c(col_idx, np.int32)
+    val = _c(val, np.float64)
+    x = _c(x, np.float64)
+    out = _yin(y, m)
+    np_ = part["start_idx"].shape[0]
+    s = _c(part["start_idx"], np.int32)
+    e = _c(part["end_idx"], np.int32)
+    rc = _lib().ref_pspmv_coo_scatter(
+        m, _p(row_idx, _i32p), _p(col_idx, _i32p), _p(val, _f64p), np_,
+        _p(s, _i32p), _p(e, _i32p), alpha, _p(x, _f64p), beta, _p(out, _f64p))
+    assert rc == 0
+    return out
 
 
 # --------------------------------------------------------------------------

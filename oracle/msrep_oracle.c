@@ -35,6 +35,13 @@
  *       (row, col): start_row = row_idx[start_idx], end_row =
  *       row_idx[end_idx], start_flag = start_idx > 0 &&
  *       row_idx[start_idx-1] == row_idx[start_idx].
+ *   R9  COO sorted by (col, row) (Sec. 3.2.3 names it, with cost
+ *       O(np log n)): Alg. 6 with the column index as the major index, so
+ *       start_major/end_major are columns and the flag marks a split
+ *       column.  COO in no order (Sec. 3.2.3: a partition may reach any
+ *       row): start_major = 0, end_major = m-1 for a non-empty partition,
+ *       start_flag = 0.  In both, each partition produces a full m-vector
+ *       of partials and the merge sums them in partition order (as R7).
  *
  * Build: plain C11, -ffp-contract=off so every product and sum rounds alone.
  */
@@ -148,6 +155,26 @@ int ref_partition_coo(int64_t nnz, const int32_t *row_idx, int32_t np,
     start_row[i] = row_idx[s];
     end_row[i] = row_idx[e];
     start_flag[i] = (s > 0 && row_idx[s - 1] == row_idx[s]) ? 1 : 0;
+  }
+  return 0;
+}
+
+/* pCOO of a COO matrix in no particular order, reading R9: the nonzero
+ * ranges of Alg. 6; the row range of every non-empty partition is the
+ * whole matrix. */
+int ref_partition_coo_unsorted(int64_t nnz, int32_t m, int32_t np,
+                               int32_t *start_idx, int32_t *end_idx,
+                               int32_t *start_row, int32_t *end_row,
+                               uint8_t *start_flag) {
+  if (np < 1 || nnz < 0 || m < 0) return 1;
+  for (int32_t i = 0; i < np; i++) {
+    int64_t s, e;
+    part_range(nnz, np, i, &s, &e);
+    start_idx[i] = (int32_t)s;
+    end_idx[i] = (int32_t)e;
+    start_row[i] = 0;
+    end_row[i] = e < s ? -1 : m - 1;
+    start_flag[i] = 0;
   }
   return 0;
 }
@@ -279,6 +306,31 @@ int ref_pspmv_csc(int32_t m, const int32_t *col_ptr, const int32_t *row_idx,
                                                    : end_idx[i];
       for (int64_t j = lo; j <= hi; j++) py[row_idx[j]] += val[j] * x[c];
     }
+    for (int32_t r = 0; r < m; r++) sum[r] += py[r];
+  }
+  for (int32_t r = 0; r < m; r++) y[r] = finish(alpha, sum[r], beta, y[r]);
+  free(py);
+  free(sum);
+  return 0;
+}
+
+/* Partitioned SpMV of a COO matrix sorted by column or in no order
+ * (reading R9): partition i adds val*x[col] for its nonzeros, in storage
+ * order, into its own full m-vector of partials py_i (the extra memory
+ * Sec. 3.2.3 mentions); then y = alpha * sum_i py_i + beta * y_in, the
+ * partials summed in partition order. */
+int ref_pspmv_coo_scatter(int32_t m, const int32_t *row_idx,
+                          const int32_t *col_idx, const double *val, int32_t np,
+                          const int32_t *start_idx, const int32_t *end_idx,
+                          double alpha, const double *x, double beta,
+                          double *y) {
+  double *sum = (double *)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
+  double *py = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  for (int32_t i = 0; i < np; i++) {
+    if (end_idx[i] < start_idx[i]) continue;
+    memset(py, 0, (size_t)(m > 0 ? m : 1) * sizeof(double));
+    for (int64_t j = start_idx[i]; j <= end_idx[i]; j++)
+      py[row_idx[j]] += val[j] * x[col_idx[j]];
     for (int32_t r = 0; r < m; r++) sum[r] += py[r];
   }
   for (int32_t r = 0; r < m; r++) y[r] = finish(alpha, sum[r], beta, y[r]);

@@ -27,7 +27,7 @@ import numpy as np
 SEED_BASE = 20220915
 
 # stream ids
-_S_COLS, _S_VALS, _S_X, _S_Y, _S_RMAT_BITS, _S_RMAT_VALS, _S_SIZES = range(7)
+_S_COLS, _S_VALS, _S_X, _S_Y, _S_RMAT_BITS, _S_RMAT_VALS, _S_SIZES, _S_ORDER = range(8)
 
 
 def rng(seed: int, stream: int) -> np.random.Generator:
@@ -66,7 +66,8 @@ class CSC:
 
 @dataclass
 class COO:
-    """COO matrix (Sec. 2.1.1) sorted by (row, col)."""
+    """COO matrix (Sec. 2.1.1): sorted by (row, col) unless made by
+    csr_to_coo_by_col or csr_to_coo_unsorted."""
     m: int
     n: int
     row_idx: np.ndarray
@@ -105,6 +106,22 @@ def csr_to_csc(a: CSR) -> CSC:
     counts = np.bincount(a.col_idx, minlength=a.n)
     return CSC(a.m, a.n, row_ptr_from_counts(counts),
                rows[order].astype(np.int32), a.val[order].copy())
+
+
+def csr_to_coo_by_col(a: CSR) -> COO:
+    """COO sorted by (col, row): the nonzeros in CSC order."""
+    c = csr_to_csc(a)
+    cols = np.repeat(np.arange(a.n, dtype=np.int32), np.diff(c.col_ptr.astype(np.int64)))
+    return COO(a.m, a.n, c.row_idx.copy(), cols, c.val.copy())
+
+
+def csr_to_coo_unsorted(a: CSR, seed: int = SEED_BASE + 1) -> COO:
+    """COO in no particular order: the nonzeros under a seeded random
+    permutation (Philox stream _S_ORDER of ``seed``)."""
+    q = csr_to_coo(a)
+    order = rng(seed, _S_ORDER).permutation(q.nnz)
+    return COO(a.m, a.n, q.row_idx[order].copy(), q.col_idx[order].copy(),
+               q.val[order].copy())
 
 
 def transpose_csr(a: CSR) -> CSR:

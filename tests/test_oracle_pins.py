@@ -382,6 +382,95 @@ def test_hub_row_spanning_every_partition_merges_exactly():
 
 
 # --------------------------------------------------------------------------
+# pCOO sorted by column and in no order (reading R9)
+# --------------------------------------------------------------------------
+
+def test_pcoo_by_col_is_pcsc():
+    """Column-sorted pCOO is Alg. 6 over the column index: its metadata
+    equals pCSC's (itself pinned as pCSR of the transpose), and the local
+    column index is col - start_col of the owning partition."""
+    for a in _adversarial() + [I.rmat(scale=11, nnz=20_000, seed=41)]:
+        c = I.csr_to_csc(a)
+        q = I.csr_to_coo_by_col(a)
+        nnz = a.nnz
+        for P in sorted({1, 3, 7, 148, max(1, nnz), nnz + 5}):
+            pq = O.partition_coo_by_col(q.col_idx, P, with_local=True)
+            pc = O.partition_csc(c.col_ptr, nnz, P)
+            for key in ("start_idx", "end_idx", "start_major", "end_major",
+                        "start_flag"):
+                assert np.array_equal(pq[key], pc[key]), (key, P)
+            if nnz:
+                owner = np.searchsorted(pc["start_idx"], np.arange(nnz), side="right") - 1
+                # the owner search lands on the last partition starting at or
+                # before k, which is the non-empty one holding k
+                assert np.array_equal(pq["local"], q.col_idx - pc["start_major"][owner])
+
+
+def test_pcoo_unsorted_ranges_and_whole_row_span():
+    a = I.rmat(scale=10, nnz=9_000, seed=43)
+    q = I.csr_to_coo_unsorted(a, seed=7)
+    s = I.csr_to_coo(a)
+    for P in (1, 5, 148, a.nnz, a.nnz + 3):
+        pu = O.partition_coo_unsorted(q.row_idx, a.m, P, with_local=True)
+        ps = O.partition_coo(s.row_idx, P)
+        assert np.array_equal(pu["start_idx"], ps["start_idx"])
+        assert np.array_equal(pu["end_idx"], ps["end_idx"])
+        ne = pu["end_idx"] >= pu["start_idx"]
+        assert np.all(pu["start_major"] == 0)
+        assert np.all(pu["end_major"][ne] == a.m - 1)
+        assert np.all(pu["end_major"][~ne] == -1)
+        assert not pu["start_flag"].any()
+        assert np.array_equal(pu["local"], q.row_idx)
+
+
+def test_unsorted_coo_is_a_permutation_of_the_sorted_one():
+    a = I.rmat(scale=9, nnz=3_000, seed=44)
+    q, s = I.csr_to_coo_unsorted(a, seed=9), I.csr_to_coo(a)
+    assert not np.array_equal(q.row_idx, s.row_idx)
+    key_q = np.lexsort((q.col_idx, q.row_idx))
+    assert np.array_equal(q.row_idx[key_q], s.row_idx)
+    assert np.array_equal(q.col_idx[key_q], s.col_idx)
+    assert np.array_equal(q.val[key_q], s.val)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_pspmv_coo_scatter_dense(seed):
+    """Partitioned SpMV of column-sorted and unsorted COO against numpy's
+    dense product, for P from 1 to beyond nnz, with alpha and beta."""
+    g = I.rng(seed, 19)
+    m, n = int(g.integers(1, 17)), int(g.integers(1, 17))
+    d, a = _tiny(seed + 100, m, n, float(g.uniform(0.05, 0.9)))
+    x = g.uniform(-1, 1, n)
+    yin = g.uniform(-1, 1, m)
+    want = 0.75 * (d @ x) - 1.5 * yin
+    for by_col, q in ((True, I.csr_to_coo_by_col(a)),
+                      (False, I.csr_to_coo_unsorted(a, seed=seed))):
+        for P in sorted({1, 2, 5, max(1, a.nnz), a.nnz + 2}):
+            p = (O.partition_coo_by_col(q.col_idx, P) if by_col
+                 else O.partition_coo_unsorted(q.row_idx, m, P))
+            y = O.pspmv_coo_scatter(m, q.row_idx, q.col_idx, q.val, p, x, 0.75, -1.5, yin)
+            assert np.allclose(y, want, rtol=0, atol=1e-13)
+            nan = np.full(m, np.nan)
+            y0 = O.pspmv_coo_scatter(m, q.row_idx, q.col_idx, q.val, p, x, 1.0, 0.0, nan)
+            assert np.allclose(y0, d @ x, rtol=0, atol=1e-13)
+
+
+def test_pspmv_coo_scatter_hub_row_exact():
+    """One row holds every nonzero, in shuffled order: every partition adds
+    to it, and the integer-valued sum is exact."""
+    n = 3000
+    a = I.csr_from_triplets(4, n, [2] * n, list(range(n)),
+                            I.rng(5, 5).integers(-3, 4, n).astype(float))
+    x = I.rng(5, 6).integers(-4, 5, n).astype(float)
+    exact = float(sum(int(v) * int(w) for v, w in zip(a.val, x)))
+    for q in (I.csr_to_coo_by_col(a), I.csr_to_coo_unsorted(a, seed=3)):
+        for P in (1, 7, 148, 3000, 4000):
+            p = O.partition_coo_unsorted(q.row_idx, 4, P)
+            y = O.pspmv_coo_scatter(4, q.row_idx, q.col_idx, q.val, p, x)
+            assert y.tolist() == [0.0, 0.0, exact, 0.0]
+
+
+# --------------------------------------------------------------------------
 # binary32 TwoSum and compensated summation
 # --------------------------------------------------------------------------
 
