@@ -292,6 +292,21 @@ def run_reference(args):
 # our arm
 # --------------------------------------------------------------------------
 
+def partition_overhead(part_ms, part_local_ms, kern):
+    """Partitioning as a share of partition + one SpMV (the paper's measure
+    of partitioning overhead, Sec. 5, with the matrix already on the
+    device, so nothing is distributed), without and with the local
+    pointers materialised."""
+    out = {}
+    for k, t in part_ms.items():
+        spmv_ms = kern[k]["call_us"] * 1e-3
+        tl = part_local_ms[k]
+        out[k] = {"ms": t, "ms_with_local": tl, "spmv_ms": spmv_ms,
+                  "pct": 100.0 * t / (t + spmv_ms),
+                  "pct_with_local": 100.0 * tl / (tl + spmv_ms)}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -306,7 +321,7 @@ def run_ours(args):
 
     mats = load_workload()
     pairs = []   # (name, fmt, A, part, x, y, ws, nnz, bytes)
-    part_ms = {}
+    part_ms, part_local_ms = {}, {}
     for name, a in mats.items():
         xh = I.vector(a.n, I.SEED_BASE + 1)
         x = torch.from_numpy(xh).to(dev)
@@ -325,6 +340,18 @@ def run_ours(args):
             e1.record()
             torch.cuda.synchronize()
             part_ms[f"{name}/{fmt}"] = e0.elapsed_time(e1) / reps
+            # the same with the local row/column pointers (pCOO: the local
+            # row-index array, one entry per nonzero) materialised
+            part_l = M.DevicePartition(A, P, tile=args.tile, local=True, device=dev)
+            M.msrep_partition(A, part_l)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                M.msrep_partition(A, part_l)
+            e1.record()
+            torch.cuda.synchronize()
+            part_local_ms[f"{name}/{fmt}"] = e0.elapsed_time(e1) / reps
+            del part_l
             y = torch.empty(a.m, dtype=torch.float64, device=dev)
             ws = M.alloc_workspace(A, part, device=dev)
             nb = algorithmic_bytes(fmt, a.m, a.n, a.nnz, 8, 8)
@@ -414,10 +441,12 @@ def run_ours(args):
     for k, v in kern.items():
         v["gbs"] = v["bytes"] / (v["kernel_us"] * 1e-6) / 1e9
         v["frac"] = v["gbs"] / peak
+    part_over = partition_overhead(part_ms, part_local_ms, kern)
 
     # end to end through the C ABI with host buffers: x up, SpMV, y down
     e2e = run_e2e(M, pairs, args, dev)
     p_sweep = run_p_sweep(M, pairs, args) if not args.skip_p_sweep else None
+    coo_orders = run_coo_orders(M, args, dev, kern, peak) if not args.skip_coo_orders else None
 
     # low-precision form on the R-MAT matrix (CSR)
     prec = run_precision(M, args, dev) if not args.skip_precision else None
@@ -433,6 +462,8 @@ def run_ours(args):
         "roofline": roof,
         "per_kernel": kern,
         "partition_ms": part_ms,
+        "partition_overhead": part_over,
+        "coo_orders": coo_orders,
         "e2e": e2e,
         # CSR and COO: main kernel + fix-up kernel; CSC: prepare (zero y or
         # the permuted accumulator) + main kernel + gather of y
@@ -794,6 +825,56 @@ def run_spmm_leg(M, A, part, a, xh, dev, spmv_call_us, k=8):
             "speedup_vs_k_spmv": k * spmv_call_us / us}
 
 
+def run_coo_orders(M, args, dev, kern, peak):
+    """pCOO of the workload's matrices sorted by column and in no order
+    (Sec. 3.2.3; their SpMV is a scatter): main-kernel and call time, GB/s
+    against COO's algorithmic bytes, and the result against the row-sorted
+    COO product of the same matrix (normwise)."""
+    import torch
+    out = {}
+    for name, a in (("rmat", I.rmat_full()), ("laplace", I.laplace_full())):
+        x = torch.from_numpy(I.vector(a.n, I.SEED_BASE + 1)).to(dev)
+        A0 = M.DeviceMatrix.from_host(a, "coo", "f64", device=dev)
+        p0 = M.DevicePartition(A0, args.P, device=dev)
+        M.msrep_partition(A0, p0)
+        y_ref = torch.empty(a.m, dtype=torch.float64, device=dev)
+        M.msrep_spmv(A0, p0, 1.0, x, 0.0, y_ref, workspace=M.alloc_workspace(A0, p0, device=dev))
+        del A0, p0
+        for fmt in ("coo_col", "coo_any"):
+            A = M.DeviceMatrix.from_host(a, fmt, "f64", device=dev)
+            part = M.DevicePartition(A, args.P, device=dev)
+            M.msrep_partition(A, part)
+            ws = M.alloc_workspace(A, part, device=dev)
+            y = torch.empty(a.m, dtype=torch.float64, device=dev)
+            for _ in range(3):
+                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+            reps = 50
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            M.native.msrep_profile_events(s0, s1)
+            tot = 0.0
+            for _ in range(reps):
+                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+                s1.synchronize()
+                tot += s0.elapsed_time(s1)
+            M.native.msrep_profile_events(None, None)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+            e1.record()
+            torch.cuda.synchronize()
+            nb = algorithmic_bytes("coo", a.m, a.n, a.nnz, 8, 8)
+            k_us, c_us = 1e3 * tot / reps, 1e3 * e0.elapsed_time(e1) / reps
+            d = torch.linalg.norm(y - y_ref) / torch.linalg.norm(y_ref)
+            out[f"{name}/{fmt}"] = {
+                "kernel_us": k_us, "call_us": c_us, "bytes": nb,
+                "gbs": nb / (k_us * 1e-6) / 1e9, "frac": nb / (k_us * 1e-6) / 1e9 / peak,
+                "row_sorted_coo_kernel_us": kern[f"{name}/coo"]["kernel_us"],
+                "normwise_vs_row_sorted": float(d)}
+            del A, part, ws
+    return out
+
+
 def run_profile_case(args):
     """A short fixed case for ncu captures: partition the R-MAT matrix once,
     then `--reps` calls of msrep_spmv in one format and value type."""
@@ -894,12 +975,14 @@ def main():
     ap.add_argument("--skip-precision", action="store_true")
     ap.add_argument("--skip-p-sweep", action="store_true",
                     help="skip the P = 148 .. 148*64 sweep of the main kernels")
+    ap.add_argument("--skip-coo-orders", action="store_true",
+                    help="skip the column-sorted / unsorted COO leg")
     ap.add_argument("--batched-count", type=int, default=512,
                     help="matrices in the batched-form measurement (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=4.0,
                     help="length of the served request stream (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
-    ap.add_argument("--profile", choices=FORMATS, default=None,
+    ap.add_argument("--profile", choices=FORMATS + ("coo_col", "coo_any"), default=None,
                     help="run only a short fixed case (for ncu captures)")
     ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")
     ap.add_argument("--profile-dtype", choices=["f64", "f32", "bf16"], default="f64")

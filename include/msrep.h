@@ -48,7 +48,17 @@ typedef enum {
   MSREP_ERR_WORKSPACE = 9    /* workspace or plan buffer too small         */
 } msrep_status;
 
-typedef enum { MSREP_CSR = 0, MSREP_CSC = 1, MSREP_COO = 2 } msrep_format;
+/* MSREP_COO is sorted by (row, col), the order Sec. 3.2.3 assumes.  The
+ * two other COO orders are the ones Sec. 3.2.3 names and sets aside:
+ * MSREP_COO_BY_COL sorted by (col, row), MSREP_COO_UNSORTED in no order
+ * (duplicate coordinates allowed; their products add up). */
+typedef enum {
+  MSREP_CSR = 0,
+  MSREP_CSC = 1,
+  MSREP_COO = 2,
+  MSREP_COO_BY_COL = 3,
+  MSREP_COO_UNSORTED = 4
+} msrep_format;
 
 /* Value / vector storage types.  MSREP_BF16 is bfloat16 (8-bit exponent,
  * 7-bit mantissa) stored as uint16. */
@@ -60,7 +70,8 @@ typedef enum { MSREP_F64 = 0, MSREP_F32 = 1, MSREP_BF16 = 2 } msrep_dtype;
  *   CSC (Sec. 2.1.3): ptr = col_ptr[n+1], idx = row_idx[nnz], idx2 = NULL;
  *                     row indices ascend within each column.
  *   COO (Sec. 2.1.1): ptr = NULL, idx = col_idx[nnz], idx2 = row_idx[nnz],
- *                     sorted by (row, col) as Sec. 3.2.3 assumes.
+ *                     sorted by (row, col) as Sec. 3.2.3 assumes; the same
+ *                     arrays for MSREP_COO_BY_COL and MSREP_COO_UNSORTED.
  * val has nnz entries of type val_dtype. */
 typedef struct {
   int32_t fmt;       /* msrep_format */
@@ -77,10 +88,13 @@ typedef struct {
  * Every array is caller-allocated device memory of the stated length.
  *   start_idx, end_idx  [np]  nonzero range of partition i, end inclusive:
  *                             floor(i*nnz/np) .. floor((i+1)*nnz/np)-1.
- *   start_major,        [np]  first / last row (CSR, COO) or column (CSC)
- *   end_major                 that owns a nonzero of the partition.
+ *   start_major,        [np]  first / last row (CSR, COO) or column (CSC,
+ *   end_major                 COO_BY_COL) that owns a nonzero of the
+ *                             partition; 0 and m-1 for COO_UNSORTED, whose
+ *                             partitions may reach any row.
  *   start_flag          [np]  1 if the partition's first row (column) also
- *                             has nonzeros in an earlier partition.
+ *                             has nonzeros in an earlier partition; 0 for
+ *                             COO_UNSORTED.
  *   local_off  (opt.) [np+1]  offsets of each partition's local pointers.
  *   local      (opt.)         CSR/CSC: local row_ptr/col_ptr of partition i
  *                             at local_off[i], end_major-start_major+2
@@ -88,9 +102,13 @@ typedef struct {
  *                             end_idx-start_idx+1); capacity
  *                             msrep_partition_local_bound().  COO: local row
  *                             index array, nnz entries, row_idx[k] -
- *                             start_major of k's partition.
- *   plan       (opt.)         opaque tile plan used by msrep_spmv for CSR
- *                             and CSC; plan_bytes >= msrep_plan_size().
+ *                             start_major of k's partition (COO_BY_COL: the
+ *                             local column index col_idx[k] - start_major;
+ *                             COO_UNSORTED: row_idx[k] itself).
+ *   plan       (opt.)         opaque plan used by msrep_spmv for CSR, CSC
+ *                             (tiles, hub rows), COO_BY_COL and
+ *                             COO_UNSORTED (hub rows); plan_bytes >=
+ *                             msrep_plan_size().
  *   tile                      nonzeros+rows per thread-block tile of the
  *                             plan, 0 = library default; must be a
  *                             supported size (msrep_tile_supported()).
@@ -121,14 +139,15 @@ const char *msrep_last_error(void);
 
 /* Host only, no GPU work.  Capacity that `local` needs for a CSR/CSC
  * partition with np parts: n_major + 2*np entries (Alg. 2 loop bound plus
- * the two closing entries per partition); nnz entries for COO. */
+ * the two closing entries per partition); nnz entries for the COO forms. */
 msrep_status msrep_partition_local_bound(const msrep_matrix *A, int32_t np,
                                          int64_t *entries);
 
 /* Host only.  1 if `tile` is a tile size msrep_spmv supports, else 0. */
 int msrep_tile_supported(int32_t tile);
 
-/* Host only.  Bytes of the tile plan for (A, np, tile); tile 0 = default. */
+/* Host only.  Bytes of the plan for (A, np, tile); tile 0 = default.  0 for
+ * row-sorted COO, which needs none. */
 msrep_status msrep_plan_size(const msrep_matrix *A, int32_t np, int32_t tile,
                              int64_t *bytes);
 
@@ -152,18 +171,28 @@ msrep_status msrep_partition_csr(const msrep_matrix *A, msrep_partition *part,
 msrep_status msrep_partition_csc(const msrep_matrix *A, msrep_partition *part,
                                  unsigned flags, void *stream);
 
-/* Row-sorted COO -> pCOO, Alg. 6 (Sec. 3.2.3).  Alg. 6 searches a row_ptr
- * that COO does not carry; here start_major = row_idx[start_idx], end_major
- * = row_idx[end_idx], start_flag = row_idx[start_idx-1] == row_idx[start_idx].
- * The result equals msrep_partition_csr on the CSR of the same matrix.
- * Validation also checks the (row, col) order. */
+/* COO -> pCOO, Alg. 6 (Sec. 3.2.3), for the three COO orders.
+ *   MSREP_COO (row-sorted): Alg. 6 searches a row_ptr that COO does not
+ *     carry; here start_major = row_idx[start_idx], end_major =
+ *     row_idx[end_idx], start_flag = row_idx[start_idx-1] ==
+ *     row_idx[start_idx].  The result equals msrep_partition_csr on the CSR
+ *     of the same matrix.
+ *   MSREP_COO_BY_COL: the same over col_idx (Sec. 3.2.3's column-sorted
+ *     case); equals msrep_partition_csc on the CSC of the same matrix.
+ *   MSREP_COO_UNSORTED: the nonzero ranges only; start_major = 0,
+ *     end_major = m-1 (Sec. 3.2.3: a partition of unsorted COO may reach
+ *     any row), start_flag = 0.
+ * For COO_BY_COL and COO_UNSORTED a plan (msrep_plan_size bytes) receives
+ * the hub rows, found as for msrep_partition_csc.  Validation checks the
+ * indices' range and, for the two sorted orders, the order. */
 msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *part,
                                  unsigned flags, void *stream);
 
 /* Host only.  Device workspace bytes msrep_spmv needs for (A, part): two
- * FP64 partials per tile, and for CSC an FP64 accumulator of 2^k >= m
- * entries (the permuted accumulator of matrices with hub rows, see
- * msrep_partition_csc; the low-precision path also accumulates there). */
+ * FP64 partials per tile, and for CSC, COO_BY_COL and COO_UNSORTED an FP64
+ * accumulator of 2^k >= m entries (the permuted accumulator of matrices
+ * with hub rows, see msrep_partition_csc; the low-precision path also
+ * accumulates there). */
 msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
                                        const msrep_partition *part,
                                        size_t *bytes);
@@ -177,7 +206,13 @@ msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
 
 /* y = alpha*A*x + beta*y over the partitions of `part` (Alg. 3 for CSR,
  * Alg. 5 for CSC, Alg. 7 for COO).  `part` must come from the matching
- * msrep_partition_* call on the same matrix; CSR and CSC also need its plan.
+ * msrep_partition_* call on the same matrix; CSR, CSC, COO_BY_COL and
+ * COO_UNSORTED also need its plan.  COO_BY_COL and COO_UNSORTED scatter
+ * like CSC: every partition may add to any row, so each product is an
+ * FP64 atomic add into y (or the accumulator), which is the sum of the
+ * partitions' full partial vectors; the result does not depend on where
+ * the partition boundaries fall, and the kernel spreads the nonzeros over
+ * its warps in equal runs.
  *
  * Types: val_dtype F64 with xy_dtype F64 (the plain path), or val_dtype F32
  * or BF16 with xy_dtype F32 (the low-precision form: FP32 products, FP32

@@ -6,6 +6,7 @@ CUDA behind the C ABI of include/msrep.h.  ``native`` is the Python binding
 of that ABI; ``inputs`` synthesises seeded test and benchmark matrices.
 """
 from .native import (MSREP_BF16, MSREP_COMP_ALL, MSREP_COMP_NONE, MSREP_COO,
+                     MSREP_COO_BY_COL, MSREP_COO_UNSORTED,
                      MSREP_STREAM_TMA, msrep_device_status,
                      MSREP_CSC, MSREP_CSR, MSREP_F32, MSREP_F64, MSREP_VALIDATE,
                      DeviceMatrix, DevicePartition, MsrepError, alloc_workspace,

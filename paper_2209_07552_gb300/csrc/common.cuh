@@ -131,6 +131,15 @@ inline PlanLayout plan_layout(int64_t n_major, int64_t nnz, int32_t np,
   return L;
 }
 
+// COO sorted by column or in no order: every partition may add to any row,
+// so its SpMV is a scatter, and its plan holds only the hub rows
+// (int32 hot[1+kMaxHot] at offset 0).
+inline bool coo_scatter_format(int32_t fmt) {
+  return fmt == MSREP_COO_BY_COL || fmt == MSREP_COO_UNSORTED;
+}
+inline bool coo_format(int32_t fmt) { return fmt == MSREP_COO || coo_scatter_format(fmt); }
+constexpr size_t kScatterPlanBytes = 256;
+
 // COO tiles: each partition is split into the same number G of sub-ranges
 // (Alg. 2's split applied inside the partition).
 inline int64_t coo_tiles_per_part(int64_t nnz, int32_t np, int32_t tile) {

@@ -56,8 +56,9 @@ int sm_count() {
 // [lo, hi] and the range shrinks about 33-fold (about five dependent loads
 // for a million rows instead of twenty for a binary search).  Every lane
 // returns the result.  Requires ptr[lo] <= k.
-__device__ __forceinline__ int32_t last_le_warp(const int32_t *__restrict__ ptr,
-                                                int32_t lo, int32_t hi, int64_t k) {
+template <typename T>
+__device__ __forceinline__ int32_t last_le_warp(const T *__restrict__ ptr, int32_t lo,
+                                                int32_t hi, int64_t k) {
   const int lane = threadIdx.x & 31;
   while (hi - lo >= 32) {
     const int64_t span = int64_t(hi) - lo;
@@ -164,6 +165,23 @@ __global__ void part_meta_coo(const int32_t *__restrict__ row_idx, int64_t nnz,
   start_flag[i] = (s > 0 && __ldg(row_idx + s - 1) == rs) ? 1 : 0;
 }
 
+// pCOO of a COO matrix in no particular order: Alg. 6's nonzero ranges; a
+// partition may reach any row (Sec. 3.2.3), so a non-empty one spans rows
+// 0..m-1, and no first row is known to be split.
+__global__ void part_meta_coo_unsorted(int64_t nnz, int32_t m, int32_t np, int32_t *start_idx,
+                                       int32_t *end_idx, int32_t *start_major,
+                                       int32_t *end_major, uint8_t *start_flag) {
+  const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+  if (i >= np) return;
+  const int64_t s = (i * nnz) / np;
+  const int64_t e = ((i + 1) * nnz) / np - 1;
+  start_idx[i] = static_cast<int32_t>(s);
+  end_idx[i] = static_cast<int32_t>(e);
+  start_major[i] = 0;
+  end_major[i] = e < s ? -1 : m - 1;
+  start_flag[i] = 0;
+}
+
 // ---------------------------------------------------------------------------
 // single-block exclusive scan (np is at most a few hundred thousand)
 // ---------------------------------------------------------------------------
@@ -214,39 +232,110 @@ __global__ void __launch_bounds__(1024)
 }
 
 // Local row_ptr / col_ptr (Alg. 2/4 inner loop, computed on the GPU as in
-// Sec. 4.1): one block per partition.
-__global__ void local_fill_compressed(const int32_t *__restrict__ ptr,
-                                      const int32_t *start_idx,
-                                      const int32_t *end_idx,
-                                      const int32_t *start_major,
-                                      const int32_t *end_major,
-                                      const int64_t *local_off,
-                                      int32_t *local) {
-  const int32_t i = blockIdx.x;
-  const int32_t sm = start_major[i], em = end_major[i];
-  const int32_t s = start_idx[i], e = end_idx[i];
-  int32_t *out = local + local_off[i];
-  const int32_t span = em - sm;  // -1 for an empty partition
-  for (int32_t j = threadIdx.x; j <= span + 1; j += blockDim.x) {
-    int32_t v;
-    if (j == 0)
-      v = 0;
-    else if (j == span + 1)
-      v = e - s + 1;
-    else
-      v = __ldg(ptr + sm + j) - s;
-    out[j] = v;
+// Sec. 4.1).  The outputs of all partitions form one array of local_off[np]
+// entries.  Each warp writes 256 consecutive entries, 8 per lane: a warp-wide
+// search over local_off brackets the partitions of the 256, a short binary
+// search gives each lane the partition of its first entry, and the lane walks
+// forward from there, so the work is spread evenly whatever P and the
+// partitions' row spans are.  Entry j of partition i: 0 (j = 0),
+// end - start + 1 (j = span + 1), else ptr[start_major + j] - start_idx.
+template <bool kVec>
+__global__ void __launch_bounds__(256)
+    local_fill_compressed(const int32_t *__restrict__ ptr, const int32_t *start_idx,
+                          const int32_t *end_idx, const int32_t *start_major,
+                          const int32_t *end_major, const int64_t *local_off, int32_t np,
+                          int32_t *local) {
+  const int64_t total = local_off[np];
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t w0 = (blockIdx.x * int64_t(blockDim.x >> 5) + (threadIdx.x >> 5)) * 256;
+       w0 < total; w0 += warps * 256) {
+    // partitions of the warp's first and last entries (warp-uniform)
+    const int32_t ia = last_le_warp(local_off, 0, np - 1, w0);
+    const int32_t ib = last_le_warp(local_off, ia, np - 1, w0 + 255 < total ? w0 + 255 : total - 1);
+    const int64_t t0 = w0 + 8 * lane;
+    if (t0 >= total) continue;
+    int32_t lo = ia, hi = ib;  // last i in [ia, ib] with local_off[i] <= t0
+    while (lo < hi) {
+      const int32_t mid = (lo + hi + 1) >> 1;
+      if (__ldg(local_off + mid) <= t0) lo = mid; else hi = mid - 1;
+    }
+    int32_t i = lo;
+    int64_t base = __ldg(local_off + i), next = __ldg(local_off + i + 1);
+    int32_t sm = __ldg(start_major + i), span = __ldg(end_major + i) - sm;
+    int32_t s = __ldg(start_idx + i), e = __ldg(end_idx + i);
+    int32_t v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t t = t0 + u;
+      while (t >= next && i + 1 < np) {
+        ++i;
+        base = next;
+        next = __ldg(local_off + i + 1);
+        sm = __ldg(start_major + i);
+        span = __ldg(end_major + i) - sm;
+        s = __ldg(start_idx + i);
+        e = __ldg(end_idx + i);
+      }
+      const int32_t j = static_cast<int32_t>(t - base);
+      v[u] = j == 0 ? 0 : (j == span + 1 ? e - s + 1 : __ldg(ptr + sm + j) - s);
+    }
+    if (kVec && t0 + 8 <= total) {
+      reinterpret_cast<int4 *>(local + t0)[0] = make_int4(v[0], v[1], v[2], v[3]);
+      reinterpret_cast<int4 *>(local + t0)[1] = make_int4(v[4], v[5], v[6], v[7]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (t0 + u < total) local[t0 + u] = v[u];
+    }
   }
 }
 
-// pCOO local row-index array: lrow[k] = row_idx[k] - start_row(partition).
-__global__ void local_fill_coo(const int32_t *__restrict__ row_idx,
-                               const int32_t *start_idx, const int32_t *end_idx,
-                               const int32_t *start_major, int32_t *local) {
-  const int32_t i = blockIdx.x;
-  const int32_t s = start_idx[i], e = end_idx[i], r0 = start_major[i];
-  for (int64_t k = s + threadIdx.x; k <= e; k += blockDim.x)
-    local[k] = __ldcs(row_idx + k) - r0;
+// pCOO local row-index array: lrow[k] = row_idx[k] - start_row(partition of
+// k).  Each thread converts 8 consecutive nonzeros.  Partition i starts at
+// floor(i nnz / np) (Alg. 6), so the partition owning k is
+// floor(((k + 1) np - 1) / nnz); the walk over start_idx confirms it and
+// moves on at a partition boundary inside the 8.
+template <bool kVec>
+__global__ void __launch_bounds__(256)
+    local_fill_coo(const int32_t *__restrict__ row_idx, int64_t nnz, int32_t np,
+                   const int32_t *start_idx, const int32_t *start_major, int32_t *local) {
+  const int64_t stride = int64_t(gridDim.x) * blockDim.x * 8;
+  for (int64_t k0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) * 8; k0 < nnz;
+       k0 += stride) {
+    int32_t i = static_cast<int32_t>(((k0 + 1) * np - 1) / nnz);
+    while (i > 0 && __ldg(start_idx + i) > k0) --i;
+    int64_t next = i + 1 < np ? __ldg(start_idx + i + 1) : nnz;
+    int32_t r0 = __ldg(start_major + i);
+    int32_t r[8];
+    const bool full = kVec && k0 + 8 <= nnz;
+    if (full) {
+      const int4 a = __ldcs(reinterpret_cast<const int4 *>(row_idx + k0));
+      const int4 b = __ldcs(reinterpret_cast<const int4 *>(row_idx + k0) + 1);
+      r[0] = a.x; r[1] = a.y; r[2] = a.z; r[3] = a.w;
+      r[4] = b.x; r[5] = b.y; r[6] = b.z; r[7] = b.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) r[u] = k0 + u < nnz ? __ldcs(row_idx + k0 + u) : 0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      while (k0 + u >= next && i + 1 < np) {
+        ++i;
+        next = i + 1 < np ? __ldg(start_idx + i + 1) : nnz;
+        r0 = __ldg(start_major + i);
+      }
+      r[u] -= r0;
+    }
+    if (full) {
+      __stcs(reinterpret_cast<int4 *>(local + k0), make_int4(r[0], r[1], r[2], r[3]));
+      __stcs(reinterpret_cast<int4 *>(local + k0) + 1, make_int4(r[4], r[5], r[6], r[7]));
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < nnz) local[k0 + u] = r[u];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -296,7 +385,8 @@ __global__ void plan_tiles(const int32_t *__restrict__ ptr, int32_t n_major,
 
 __device__ unsigned int g_validate_err;
 
-// Hub rows of a CSC matrix (at most kMaxHot): the row indices of
+// Hub rows of a CSC matrix, or of a COO matrix sorted by column or in no
+// order (at most kMaxHot): the row indices of
 // kHotSample evenly spaced nonzeros are counted in an open-addressing table
 // in shared memory (twice as many slots as samples, so probing ends), and
 // the most frequent rows with at least kHotMin samples kept, most frequent
@@ -396,16 +486,19 @@ __global__ void validate_compressed(const int32_t *__restrict__ ptr,
   }
 }
 
+// order: 0 = by (row, col), 1 = by (col, row), 2 = none
 __global__ void validate_coo(const int32_t *__restrict__ row, const int32_t *__restrict__ col,
-                             int64_t nnz, int32_t m, int32_t n) {
+                             int64_t nnz, int32_t m, int32_t n, int order) {
   int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   int64_t stride = int64_t(gridDim.x) * blockDim.x;
   for (int64_t k = t; k < nnz; k += stride) {
     int32_t r = row[k], c = col[k];
     if (r < 0 || r >= m || c < 0 || c >= n) atomicOr(&g_validate_err, 4u);
-    if (k + 1 < nnz) {
-      int32_t r2 = row[k + 1], c2 = col[k + 1];
-      if (r2 < r || (r2 == r && c2 <= c)) atomicOr(&g_validate_err, 8u);
+    if (order < 2 && k + 1 < nnz) {
+      const int32_t r2 = row[k + 1], c2 = col[k + 1];
+      const int32_t a = order == 0 ? r : c, b = order == 0 ? c : r;
+      const int32_t a2 = order == 0 ? r2 : c2, b2 = order == 0 ? c2 : r2;
+      if (a2 < a || (a2 == a && b2 <= b)) atomicOr(&g_validate_err, 8u);
     }
   }
 }
@@ -418,8 +511,9 @@ static msrep_status run_validation(const msrep_matrix *A, cudaStream_t st) {
   MSREP_CUDA_TRY(cudaMemcpyToSymbolAsync(g_validate_err, &zero, sizeof zero, 0,
                                          cudaMemcpyHostToDevice, st));
   const int blocks = 4 * sm_count();
-  if (A->fmt == MSREP_COO) {
-    validate_coo<<<blocks, 256, 0, st>>>(A->idx2, A->idx, A->nnz, A->m, A->n);
+  if (coo_format(A->fmt)) {
+    const int order = A->fmt == MSREP_COO ? 0 : A->fmt == MSREP_COO_BY_COL ? 1 : 2;
+    validate_coo<<<blocks, 256, 0, st>>>(A->idx2, A->idx, A->nnz, A->m, A->n, order);
   } else {
     const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
     const int32_t n_minor = A->fmt == MSREP_CSR ? A->n : A->m;
@@ -433,7 +527,7 @@ static msrep_status run_validation(const msrep_matrix *A, cudaStream_t st) {
   if (err)
     return fail(MSREP_ERR_BAD_MATRIX,
                 "matrix failed validation (code 0x%x: 1=ptr ends, 2=ptr not "
-                "monotone, 4=index out of range, 8=COO not sorted by (row, col))",
+                "monotone, 4=index out of range, 8=COO not in its order)",
                 err);
   return MSREP_OK;
 }
@@ -455,6 +549,8 @@ msrep_status check_matrix(const msrep_matrix *A) {
       if (!A->ptr) return fail(MSREP_ERR_INVALID_ARG, "ptr is NULL");
       break;
     case MSREP_COO:
+    case MSREP_COO_BY_COL:
+    case MSREP_COO_UNSORTED:
       if (!A->idx2 && A->nnz > 0)
         return fail(MSREP_ERR_INVALID_ARG, "COO row_idx (idx2) is NULL");
       break;
@@ -513,9 +609,18 @@ static msrep_status partition_compressed(const msrep_matrix *A,
                                        p->local_off);
     MSREP_CUDA_TRY(cudaGetLastError());
     if (p->local) {
-      local_fill_compressed<<<p->np, 128, 0, st>>>(
-          A->ptr, p->start_idx, p->end_idx, p->start_major, p->end_major,
-          p->local_off, p->local);
+      // at most m + 2 np entries (n + 2 np for CSC)
+      const int64_t most = int64_t(n_major) + 2 * int64_t(p->np);
+      const int grid = static_cast<int>(
+          std::max<int64_t>(1, std::min<int64_t>(ceil_div(most, 8 * 256), 8 * sm_count())));
+      if ((reinterpret_cast<uintptr_t>(p->local) & 15) == 0)
+        local_fill_compressed<true><<<grid, 256, 0, st>>>(
+            A->ptr, p->start_idx, p->end_idx, p->start_major, p->end_major, p->local_off,
+            p->np, p->local);
+      else
+        local_fill_compressed<false><<<grid, 256, 0, st>>>(
+            A->ptr, p->start_idx, p->end_idx, p->start_major, p->end_major, p->local_off,
+            p->np, p->local);
       MSREP_CUDA_TRY(cudaGetLastError());
     }
   }
@@ -554,7 +659,7 @@ msrep_status msrep_partition_local_bound(const msrep_matrix *A, int32_t np,
                                          int64_t *entries) {
   MSREP_TRY(check_matrix(A));
   if (np < 1 || !entries) return fail(MSREP_ERR_INVALID_ARG, "bad np or entries");
-  if (A->fmt == MSREP_COO)
+  if (coo_format(A->fmt))
     *entries = A->nnz;
   else
     *entries = int64_t(A->fmt == MSREP_CSR ? A->m : A->n) + 2 * int64_t(np);
@@ -569,6 +674,10 @@ msrep_status msrep_plan_size(const msrep_matrix *A, int32_t np, int32_t tile,
   if (!tile_supported(t)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", tile);
   if (A->fmt == MSREP_COO) {
     *bytes = 0;
+    return ok();
+  }
+  if (coo_scatter_format(A->fmt)) {
+    *bytes = static_cast<int64_t>(kScatterPlanBytes);
     return ok();
   }
   const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
@@ -589,19 +698,45 @@ msrep_status msrep_partition_csc(const msrep_matrix *A, msrep_partition *part,
 msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
                                  unsigned flags, void *stream) {
   MSREP_TRY(check_matrix(A));
-  if (A->fmt != MSREP_COO)
+  if (!coo_format(A->fmt))
     return fail(MSREP_ERR_INVALID_ARG, "matrix format %d is not COO", A->fmt);
   MSREP_TRY(check_partition(p));
+  const bool scatter = coo_scatter_format(A->fmt);
+  if (scatter && p->plan) {
+    if (p->plan_bytes < static_cast<int64_t>(kScatterPlanBytes))
+      return fail(MSREP_ERR_WORKSPACE, "plan buffer has %lld bytes, needs %zu",
+                  (long long)p->plan_bytes, kScatterPlanBytes);
+    if (reinterpret_cast<uintptr_t>(p->plan) & 15)
+      return fail(MSREP_ERR_INVALID_ARG, "plan must be 16-byte aligned");
+  }
   cudaStream_t st = as_stream(stream);
   if (flags & MSREP_VALIDATE) MSREP_TRY(run_validation(A, st));
+  // the major index: rows (sorted by row), columns (sorted by column)
+  const int32_t *major = A->fmt == MSREP_COO_BY_COL ? A->idx : A->idx2;
   const int threads = 256;
-  part_meta_coo<<<static_cast<int>(ceil_div(p->np, threads)), threads, 0, st>>>(
-      A->idx2, A->nnz, p->np, p->start_idx, p->end_idx, p->start_major,
-      p->end_major, p->start_flag);
+  const int blocks = static_cast<int>(ceil_div(p->np, threads));
+  if (A->fmt == MSREP_COO_UNSORTED)
+    part_meta_coo_unsorted<<<blocks, threads, 0, st>>>(A->nnz, A->m, p->np, p->start_idx,
+                                                       p->end_idx, p->start_major,
+                                                       p->end_major, p->start_flag);
+  else
+    part_meta_coo<<<blocks, threads, 0, st>>>(major, A->nnz, p->np, p->start_idx, p->end_idx,
+                                              p->start_major, p->end_major, p->start_flag);
   MSREP_CUDA_TRY(cudaGetLastError());
-  if (p->local) {
-    local_fill_coo<<<p->np, 256, 0, st>>>(A->idx2, p->start_idx, p->end_idx,
-                                          p->start_major, p->local);
+  if (p->local && A->nnz > 0) {
+    const int grid = static_cast<int>(
+        std::max<int64_t>(1, std::min<int64_t>(ceil_div(A->nnz, 8 * 256), 8 * sm_count())));
+    if (((reinterpret_cast<uintptr_t>(p->local) | reinterpret_cast<uintptr_t>(major)) & 15) == 0)
+      local_fill_coo<true><<<grid, 256, 0, st>>>(major, A->nnz, p->np, p->start_idx,
+                                                 p->start_major, p->local);
+    else
+      local_fill_coo<false><<<grid, 256, 0, st>>>(major, A->nnz, p->np, p->start_idx,
+                                                  p->start_major, p->local);
+    MSREP_CUDA_TRY(cudaGetLastError());
+  }
+  if (scatter && p->plan) {
+    MSREP_TRY(hot_rows_smem_opt_in());
+    hot_rows<<<1, 1024, kHotSmem, st>>>(A->idx2, A->nnz, static_cast<int32_t *>(p->plan));
     MSREP_CUDA_TRY(cudaGetLastError());
   }
   return ok();

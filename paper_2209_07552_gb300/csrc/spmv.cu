@@ -441,6 +441,72 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
 }
 
 // ---------------------------------------------------------------------------
+// COO sorted by column or in no order (Sec. 3.2.3): a scatter, like CSC
+// ---------------------------------------------------------------------------
+
+// Every partition of such a matrix may add to any row, so its partial
+// vector spans all of y (the full partial vectors Sec. 3.2.3 anticipates)
+// and the merge is their sum.  Here each product is one FP64 atomic add into
+// the row's entry of y (or of the accumulator): the atomic adds form the sum
+// of the partials in place, so the result does not depend on the partition
+// boundaries, and the nonzeros are spread over the grid in equal runs of 8
+// per lane.  Hub rows (from the plan) are summed per warp in shared memory
+// and the other rows go to the permuted accumulator, as for CSC.
+template <class Pol>
+struct ScatterArgs {
+  const int32_t *row_idx;
+  const int32_t *col_idx;
+  const typename Pol::V *val;
+  const typename Pol::X *x;
+  double *yacc;   // scatter target by row: y (FP64) or the FP64 accumulator
+  double *yperm;  // permuted accumulator (pmask + 1 entries), or null
+  uint32_t pmask;
+  double scale;   // alpha on the FP64 path, 1 when a finishing pass follows
+  bool scaled;
+  const int32_t *hot;  // hub rows, or null
+  int64_t nnz;
+};
+
+template <class Pol>
+__global__ void __launch_bounds__(kThreads, 4) coo_scatter(ScatterArgs<Pol> a) {
+  grid_dependency_wait();
+  using LV = typename LoadT<typename Pol::V>::type;
+  __shared__ double s_hot[kWarps][kMaxHot];
+  const bool skew = a.hot != nullptr && csc_skewed(a.hot, a.yperm);
+  HotRows hot;
+  if (skew) hot.load(a.hot, s_hot);
+  const int64_t groups = (a.nnz + 7) >> 3;
+  const int64_t step = int64_t(gridDim.x) * blockDim.x;
+  auto run = [&](auto with_hot) {
+    constexpr bool kSkew = decltype(with_hot)::value;
+    for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < groups; g += step) {
+      const int64_t g8 = g << 3;
+      int32_t r[8], c[8];
+      LV v[8];
+      load_group(a.row_idx, g8, a.nnz, r);
+      load_group(a.col_idx, g8, a.nnz, c);
+      load_group(a.val, g8, a.nnz, v);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (g8 + u >= a.nnz) break;
+        const double xv = double(load_x(a.x, c[u]));
+        const double prod = __dmul_rn(double(v[u]), a.scaled ? __dmul_rn(xv, a.scale) : xv);
+        if (!kSkew)
+          atomicAdd(a.yacc + r[u], prod);
+        else if (!hot.take(r[u], prod))
+          atomicAdd(a.yperm + perm_slot(r[u], a.pmask), prod);
+      }
+    }
+  };
+  if (skew) {
+    run(std::true_type{});
+    hot.flush(a.yperm, a.pmask, s_hot);
+  } else {
+    run(std::false_type{});
+  }
+}
+
+// ---------------------------------------------------------------------------
 // fix-up: rows split between tiles, merged in tile (= partition) order
 // ---------------------------------------------------------------------------
 
@@ -534,7 +600,7 @@ struct Workspace {
 // (perm_extent(m) entries, also used in row order by the low-precision
 // path) when perm_ok, else the low-precision path's row-ordered FP64 sums.
 static int64_t csc_acc_len(const msrep_matrix *A, bool perm_ok) {
-  if (A->fmt != MSREP_CSC) return 0;
+  if (A->fmt != MSREP_CSC && !coo_scatter_format(A->fmt)) return 0;
   if (perm_ok) return perm_extent(A->m);
   return A->val_dtype == MSREP_F64 ? 0 : A->m;
 }
@@ -557,6 +623,7 @@ static size_t ws_layout(int64_t tiles, int64_t m_acc, Workspace *w, void *base) 
 }
 
 static int64_t tiles_for(const msrep_matrix *A, const msrep_partition *p, int32_t tile) {
+  if (coo_scatter_format(A->fmt)) return 0;
   if (A->fmt == MSREP_COO) return p->np * coo_tiles_per_part(A->nnz, p->np, tile);
   const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
   return plan_layout(n_major, A->nnz, p->np, tile).tmax;
@@ -764,11 +831,66 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   return MSREP_OK;
 }
 
+// COO sorted by column or in no order: prepare the target as for CSC, one
+// scatter over all nonzeros, then the gather of y from the permuted
+// accumulator (FP64) or the finishing pass (low precision).
+template <class Pol>
+static msrep_status run_coo_scatter(const msrep_matrix *A, const msrep_partition *p,
+                                    double alpha, const void *x, double beta, void *y,
+                                    const Workspace &w, cudaStream_t st) {
+  constexpr bool kF64 = sizeof(typename Pol::X) == 8;
+  ScatterArgs<Pol> a;
+  a.row_idx = A->idx2;
+  a.col_idx = A->idx;
+  a.val = static_cast<const typename Pol::V *>(A->val);
+  a.x = static_cast<const typename Pol::X *>(x);
+  a.hot = static_cast<const int32_t *>(p->plan);
+  a.nnz = A->nnz;
+  const int64_t m = A->m;
+  const int sg = 4 * sm_count();
+  const int64_t pn = w.perm ? perm_extent(m) : 0;
+  a.yperm = w.perm ? w.yacc : nullptr;
+  a.pmask = w.perm ? static_cast<uint32_t>(pn - 1) : 0u;
+  if (kF64) {
+    a.yacc = static_cast<double *>(y);
+    a.scale = alpha;
+    a.scaled = alpha != 1.0;
+    if (w.perm || beta != 1.0)
+      MSREP_TRY(launch_dependent(csc_prepare, sg, 256, st, 0, a.hot, a.yperm, pn, a.yacc, m, beta,
+                                 1));
+  } else {
+    a.yacc = w.yacc;
+    a.scale = 1.0;
+    a.scaled = false;
+    MSREP_TRY(launch_dependent(csc_prepare, sg, 256, st, 0, a.hot, a.yperm, pn, w.yacc, m, 0.0, 0));
+  }
+  int nb = 1;
+  MSREP_TRY(kernel_occupancy(coo_scatter<Pol>, 0, 0, &nb));
+  const int64_t grid = std::max<int64_t>(
+      1, std::min<int64_t>(ceil_div(ceil_div(A->nnz, 8), kThreads), int64_t(nb) * sm_count()));
+  prof_begin(st);
+  MSREP_TRY(launch_dependent(coo_scatter<Pol>, grid, kThreads, st, 0, a));
+  prof_end(st);
+  if (kF64) {
+    if (w.perm)
+      MSREP_TRY(launch_dependent(csc_unpermute, sg, 256, st, 0, a.hot,
+                                 static_cast<const double *>(a.yperm), a.pmask,
+                                 static_cast<double *>(y), m, beta));
+  } else {
+    MSREP_TRY(launch_dependent(finish_csc_f32, sg, 256, st, 0, a.hot,
+                               static_cast<const double *>(a.yperm), a.pmask,
+                               static_cast<const double *>(w.yacc), static_cast<float *>(y), m,
+                               alpha, beta));
+  }
+  return MSREP_OK;
+}
+
 template <class Pol>
 static msrep_status dispatch_tile(const msrep_matrix *A, const msrep_partition *p,
                                   double alpha, const void *x, double beta,
                                   void *y, unsigned flags, const Workspace &w,
                                   cudaStream_t st) {
+  if (coo_scatter_format(A->fmt)) return run_coo_scatter<Pol>(A, p, alpha, x, beta, y, w, st);
   const int32_t tile = effective_tile(p->tile);
 #define MSREP_FMT_CASE(IPT)                                                   \
   switch (A->fmt) {                                                           \
@@ -872,7 +994,12 @@ msrep_status spmv_run(const msrep_matrix *A, const msrep_partition *part, double
                 A->val_dtype, xy_dtype);
   cudaStream_t st = as_stream(stream);
   if (A->m == 0) return ok();
-  if (A->fmt != MSREP_COO) {
+  if (coo_scatter_format(A->fmt)) {
+    if (!part->plan || part->plan_bytes < static_cast<int64_t>(kScatterPlanBytes))
+      return fail(MSREP_ERR_WORKSPACE,
+                  "column-sorted or unsorted COO SpMV needs the partition's plan (%zu bytes)",
+                  kScatterPlanBytes);
+  } else if (A->fmt != MSREP_COO) {
     const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
     const int64_t need = static_cast<int64_t>(plan_layout(n_major, A->nnz, part->np, tile).bytes);
     if (!part->plan || part->plan_bytes < need)
@@ -904,7 +1031,7 @@ msrep_status spmv_run(const msrep_matrix *A, const msrep_partition *part, double
   const int64_t tiles = tiles_for(A, part, tile);
   Workspace w;
   ws_layout(tiles, csc_acc_len(A, perm_ok), &w, workspace);
-  w.perm = perm_ok && A->fmt == MSREP_CSC;
+  w.perm = perm_ok && (A->fmt == MSREP_CSC || coo_scatter_format(A->fmt));
   msrep_status s;
   switch (A->val_dtype) {
     case MSREP_F64:

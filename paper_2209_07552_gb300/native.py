@@ -20,7 +20,8 @@ LIB_PATH = os.environ.get("MSREP_LIB_PATH") or os.path.join(_HERE, "libmsrep.so"
 _LOCK = threading.Lock()
 _LIB = None
 
-MSREP_CSR, MSREP_CSC, MSREP_COO = 0, 1, 2
+MSREP_CSR, MSREP_CSC, MSREP_COO, MSREP_COO_BY_COL, MSREP_COO_UNSORTED = 0, 1, 2, 3, 4
+COO_FORMATS = (MSREP_COO, MSREP_COO_BY_COL, MSREP_COO_UNSORTED)
 MSREP_F64, MSREP_F32, MSREP_BF16 = 0, 1, 2
 MSREP_VALIDATE = 0x1
 MSREP_COMP_ALL = 0x10
@@ -214,12 +215,15 @@ class DeviceMatrix:
 
     @property
     def format_name(self):
-        return {MSREP_CSR: "csr", MSREP_CSC: "csc", MSREP_COO: "coo"}[self.fmt]
+        return {MSREP_CSR: "csr", MSREP_CSC: "csc", MSREP_COO: "coo",
+                MSREP_COO_BY_COL: "coo_col", MSREP_COO_UNSORTED: "coo_any"}[self.fmt]
 
     @classmethod
     def from_host(cls, a, fmt: str = "csr", val_dtype: str = "f64",
-                  device="cuda"):
-        """Upload an inputs.CSR (converted to `fmt`) to the device."""
+                  device="cuda", order_seed=None):
+        """Upload an inputs.CSR (converted to `fmt`) to the device.  `fmt`:
+        "csr", "csc", "coo" (sorted by row), "coo_col" (sorted by column) or
+        "coo_any" (the nonzeros in a seeded random order, `order_seed`)."""
         import torch
 
         from . import inputs as I
@@ -233,9 +237,16 @@ class DeviceMatrix:
             c = I.csr_to_csc(a)
             return cls(MSREP_CSC, a.m, a.n, a.nnz, t32(c.col_ptr), t32(c.row_idx),
                        None, _val_tensor(c.val, val_dtype, device), val_dtype)
-        if fmt == "coo":
-            q = I.csr_to_coo(a)
-            return cls(MSREP_COO, a.m, a.n, a.nnz, None, t32(q.col_idx),
+        if fmt in ("coo", "coo_col", "coo_any"):
+            if fmt == "coo":
+                q, code = I.csr_to_coo(a), MSREP_COO
+            elif fmt == "coo_col":
+                q, code = I.csr_to_coo_by_col(a), MSREP_COO_BY_COL
+            else:
+                q = (I.csr_to_coo_unsorted(a) if order_seed is None
+                     else I.csr_to_coo_unsorted(a, order_seed))
+                code = MSREP_COO_UNSORTED
+            return cls(code, a.m, a.n, a.nnz, None, t32(q.col_idx),
                        t32(q.row_idx), _val_tensor(q.val, val_dtype, device),
                        val_dtype)
         raise ValueError(fmt)
@@ -263,7 +274,7 @@ class DevicePartition:
         self.start_flag = torch.empty(self.np, dtype=torch.uint8, device=device)
         self.local_off = self.local = None
         if local:
-            if A.fmt != MSREP_COO:
+            if A.fmt not in COO_FORMATS:
                 self.local_off = torch.empty(self.np + 1, dtype=torch.int64,
                                              device=device)
             self.local = torch.empty(max(1, msrep_partition_local_bound(A, self.np)),
@@ -336,7 +347,8 @@ def msrep_partition(A: DeviceMatrix, part: DevicePartition, flags: int = 0,
                     stream=None):
     """Dispatch to msrep_partition_{csr,csc,coo} by the matrix format."""
     {MSREP_CSR: msrep_partition_csr, MSREP_CSC: msrep_partition_csc,
-     MSREP_COO: msrep_partition_coo}[A.fmt](A, part, flags, stream)
+     MSREP_COO: msrep_partition_coo, MSREP_COO_BY_COL: msrep_partition_coo,
+     MSREP_COO_UNSORTED: msrep_partition_coo}[A.fmt](A, part, flags, stream)
 
 
 def msrep_spmv_workspace_size(A: DeviceMatrix, part: DevicePartition) -> int:

@@ -6,6 +6,8 @@ import oracle as O
 from paper_2209_07552_gb300 import inputs as I
 
 FORMATS = ("csr", "csc", "coo")
+# COO sorted by column and in no order (the scatter forms of pCOO)
+SCATTER_COO = ("coo_col", "coo_any")
 
 
 def normwise(y, yref):
@@ -23,8 +25,18 @@ def oracle_spmv(a: I.CSR, fmt: str, x, alpha=1.0, beta=0.0, y=None):
     if fmt == "csc":
         c = I.csr_to_csc(a)
         return O.spmv_csc(a.m, a.n, c.col_ptr, c.row_idx, c.val, x, alpha, beta, y)
-    q = I.csr_to_coo(a)
+    q = coo_of(a, fmt)
     return O.spmv_coo(a.m, q.row_idx, q.col_idx, q.val, x, alpha, beta, y)
+
+
+def coo_of(a: I.CSR, fmt: str) -> I.COO:
+    """The COO arrays the binding uploads for "coo", "coo_col" and
+    "coo_any" (default order seed)."""
+    if fmt == "coo_col":
+        return I.csr_to_coo_by_col(a)
+    if fmt == "coo_any":
+        return I.csr_to_coo_unsorted(a)
+    return I.csr_to_coo(a)
 
 
 def oracle_partition(a: I.CSR, fmt: str, P: int, with_local=False):
@@ -33,7 +45,11 @@ def oracle_partition(a: I.CSR, fmt: str, P: int, with_local=False):
     if fmt == "csc":
         c = I.csr_to_csc(a)
         return O.partition_csc(c.col_ptr, c.nnz, P, with_local)
-    q = I.csr_to_coo(a)
+    q = coo_of(a, fmt)
+    if fmt == "coo_col":
+        return O.partition_coo_by_col(q.col_idx, P, with_local)
+    if fmt == "coo_any":
+        return O.partition_coo_unsorted(q.row_idx, a.m, P, with_local)
     return O.partition_coo(q.row_idx, P, with_local)
 
 

@@ -39,3 +39,12 @@ def test_traffic_record_round_trip(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "source_stamp", lambda: "stamp-b")
     assert bench.recorded_traffic("rmat/csc") is None
     assert json.loads((tmp_path / "traffic.json").read_text())["kernels"]["rmat/csc"]["command"] == "ncu ..."
+
+
+def test_partition_overhead_share():
+    # partition 1 ms, SpMV 3 ms -> 25 %; with local pointers 3 ms -> 50 %
+    kern = {"rmat/coo": {"call_us": 3000.0}}
+    out = bench.partition_overhead({"rmat/coo": 1.0}, {"rmat/coo": 3.0}, kern)["rmat/coo"]
+    assert abs(out["pct"] - 25.0) < 1e-12
+    assert abs(out["pct_with_local"] - 50.0) < 1e-12
+    assert out["spmv_ms"] == 3.0

@@ -104,3 +104,37 @@ def test_partition_rejects_bad_arguments():
     part = M.DevicePartition(A, 4)
     with pytest.raises(M.MsrepError):
         M.msrep_partition_csc(A, part)  # wrong format for the call
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_partition_local_unaligned_output(fmt):
+    """Local pointers into a buffer that is not 16-byte aligned (the scalar
+    store path) equal the oracle's, as do those into an aligned one."""
+    import ctypes
+
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    a = I.rmat(scale=12, nnz=60_000, seed=11)
+    A = M.DeviceMatrix.from_host(a, fmt, "f64")
+    for P in (3, 148, 4099):
+        want = oracle_partition(a, fmt, P, with_local=True)
+        part = M.DevicePartition(A, P, local=True)
+        buf = torch.full((part.local.numel() + 1,), -7, dtype=torch.int32, device="cuda")
+        part.local = buf[1:]
+        part.c.local = ctypes.c_void_p(part.local.data_ptr())
+        M.msrep_partition(A, part)
+        got = part.to_host()
+        _assert_same(got, want)
+        assert int(buf[0].item()) == -7  # nothing written before the array
+
+
+@pytest.mark.parametrize("fmt", FORMATS)
+def test_partition_local_many_strides(fmt):
+    """Local arrays longer than one pass of the fill kernels' grid
+    (8 x 152 blocks x 256 threads x 8 entries = 2.49M)."""
+    a = I.laplace5(1600)   # 12.8M nonzeros, 2.56M rows
+    for P in (1, 2368):
+        got = _gpu_partition(a, fmt, P)
+        want = oracle_partition(a, fmt, P, with_local=True)
+        _assert_same(got, want)

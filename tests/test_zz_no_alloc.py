@@ -54,9 +54,11 @@ def test_noalloc_rejects_problems_larger_than_its_scratch():
     assert "scratch" in str(e.value)
 
 
+@pytest.mark.parametrize("fmt", ["csc", "coo_col", "coo_any"])
 @pytest.mark.parametrize("scale", [14, 18])
-def test_noalloc_csc_with_and_without_the_permuted_accumulator(scale):
-    """CSC on a power-law matrix (hub rows found): at 2^14 rows the permuted
+def test_noalloc_csc_with_and_without_the_permuted_accumulator(scale, fmt):
+    """CSC, and COO sorted by column or in no order, which scatter the same
+    way, on a power-law matrix (hub rows found): at 2^14 rows the permuted
     accumulator fits in the scratch array, at 2^18 rows (2 MiB) it does not
     and the call scatters into y directly.  Integer-valued data make every
     sum exact, so both entry points must match the oracle bit for bit, with
@@ -69,7 +71,7 @@ def test_noalloc_csc_with_and_without_the_permuted_accumulator(scale):
     a, x = I.integer_twin(a0, seed=64)
     y0 = np.round(I.y_vector(a.m, 65) * 4)
     want = oracle_spmv(a, "csc", x, 1.0, 2.0, y0)
-    A = M.DeviceMatrix.from_host(a, "csc", "f64")
+    A = M.DeviceMatrix.from_host(a, fmt, "f64")
     part = M.DevicePartition(A, 148)
     M.msrep_partition(A, part)
     ws = M.alloc_workspace(A, part)
