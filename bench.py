@@ -398,21 +398,15 @@ def run_ours(args):
         kern = {}
         reps = max(20, min(args.steps, 200))
         for (name, fmt, A, part, x, y, ws, nnz, nb) in pairs:
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            M.native.msrep_profile_events(s0, s1)
-            tot = 0.0
-            for _ in range(reps):
-                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
-                s1.synchronize()
-                tot += s0.elapsed_time(s1)
-            M.native.msrep_profile_events(None, None)
+            k_us = main_kernel_us(
+                M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws), reps)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(reps):
                 M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
             e1.record()
             torch.cuda.synchronize()
-            kern[f"{name}/{fmt}"] = {"kernel_us": 1e3 * tot / reps,
+            kern[f"{name}/{fmt}"] = {"kernel_us": k_us,
                                      "call_us": 1e3 * e0.elapsed_time(e1) / reps,
                                      "bytes": nb, "nnz": nnz}
             fl = access_floor_us(M, A, x, reps)
@@ -502,18 +496,32 @@ def run_p_sweep(M, pairs, args, Ps=(148, 148 * 4, 148 * 16, 148 * 64), reps=20):
             ws = M.alloc_workspace(A, part, device=x.device)
             for _ in range(3):
                 M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            M.native.msrep_profile_events(s0, s1)
-            tot = 0.0
-            for _ in range(reps):
-                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
-                s1.synchronize()
-                tot += s0.elapsed_time(s1)
-            M.native.msrep_profile_events(None, None)
-            row[str(P)] = 1e3 * tot / reps
+            row[str(P)] = main_kernel_us(
+                M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws), reps)
             del part, ws
         out[f"{name}/{fmt}"] = row
     return {"kernel_us": out, "P": list(Ps)}
+
+
+def main_kernel_us(M, call, reps, skip=3):
+    """Mean CUDA-event time (us) of the main SpMV kernel over `reps`
+    back-to-back calls of `call`.  Each call gets its own pair of profiling
+    events, recorded on the launch stream just before and just after its
+    main kernel.  The calls are not synchronised one by one: the host stays
+    ahead of the device, so no host submission latency falls inside an
+    event pair.  The first `skip` calls, which the idle device may reach
+    before the host has queued their kernels, are dropped."""
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(reps + skip)]
+    torch.cuda.synchronize()
+    for s0, s1 in evs:
+        M.native.msrep_profile_events(s0, s1)
+        call()
+    M.native.msrep_profile_events(None, None)
+    torch.cuda.synchronize()
+    ts = [s0.elapsed_time(s1) for s0, s1 in evs[skip:]]
+    return 1e3 * sum(ts) / len(ts)
 
 
 def access_floor_us(M, A, x, reps):
@@ -768,16 +776,10 @@ def run_precision(M, args, dev):
         ws = M.alloc_workspace(A, part, device=dev)
         for _ in range(3):
             M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         reps = 20
-        M.native.msrep_profile_events(s0, s1)
-        kt = 0.0
-        for _ in range(reps):
-            M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
-            s1.synchronize()
-            kt += s0.elapsed_time(s1)
-        M.native.msrep_profile_events(None, None)
+        kus = main_kernel_us(M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws),
+                             reps)
         e0.record()
         for _ in range(reps):
             M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
@@ -786,7 +788,6 @@ def run_precision(M, args, dev):
         call_us = 1e3 * e0.elapsed_time(e1) / reps
         sv = {"f64": 8, "f32": 4, "bf16": 2}[dt]
         nb = algorithmic_bytes("csr", a.m, a.n, a.nnz, sv, 8 if dt == "f64" else 4)
-        kus = 1e3 * kt / reps
         rec = {"call_us": call_us, "kernel_us": kus, "gbs": nb / (kus * 1e-6) / 1e9,
                "frac": nb / (kus * 1e-6) / 1e9 / peak,
                "gflops": 2.0 * a.nnz / (call_us * 1e-6) / 1e9}
@@ -849,14 +850,8 @@ def run_coo_orders(M, args, dev, kern, peak):
             for _ in range(3):
                 M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
             reps = 50
-            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            M.native.msrep_profile_events(s0, s1)
-            tot = 0.0
-            for _ in range(reps):
-                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
-                s1.synchronize()
-                tot += s0.elapsed_time(s1)
-            M.native.msrep_profile_events(None, None)
+            k_us = main_kernel_us(
+                M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws), reps)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(reps):
@@ -864,7 +859,7 @@ def run_coo_orders(M, args, dev, kern, peak):
             e1.record()
             torch.cuda.synchronize()
             nb = algorithmic_bytes("coo", a.m, a.n, a.nnz, 8, 8)
-            k_us, c_us = 1e3 * tot / reps, 1e3 * e0.elapsed_time(e1) / reps
+            c_us = 1e3 * e0.elapsed_time(e1) / reps
             d = torch.linalg.norm(y - y_ref) / torch.linalg.norm(y_ref)
             out[f"{name}/{fmt}"] = {
                 "kernel_us": k_us, "call_us": c_us, "bytes": nb,
@@ -945,15 +940,8 @@ def run_sweep(args):
                     ws = M.alloc_workspace(A, part, device=dev)
                     for _ in range(3):
                         M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
-                    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                    M.native.msrep_profile_events(s0, s1)
-                    tot = 0.0
-                    for _ in range(10):
-                        M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
-                        s1.synchronize()
-                        tot += s0.elapsed_time(s1)
-                    M.native.msrep_profile_events(None, None)
-                    us = 100.0 * tot
+                    us = main_kernel_us(M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y,
+                                                                 flags=flags, workspace=ws), 10)
                     print(json.dumps({"matrix": name, "fmt": fmt, "tile": tile, "P": P,
                                       "direct": direct, "kernel_us": us, "gbs": nb / us / 1e3,
                                       "frac": nb / us / 1e3 / peak}), flush=True)

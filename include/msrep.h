@@ -241,25 +241,28 @@ msrep_status msrep_spmv(const msrep_matrix *A, const msrep_partition *part,
 /* vector; the served form's requests carry up to eight).                 */
 /* ---------------------------------------------------------------------- */
 
+/* Vectors msrep_spmm multiplies in one pass over A (more take several). */
 #define MSREP_SPMM_MAX_K 8
 
 /* Host only.  Workspace bytes of msrep_spmm for (A, part, k): two FP64
  * partials per tile and vector, and the interleaved copy of X (n rows of
- * k rounded up to 1, 2, 4 or 8 values).  CSR only. */
+ * min(k, 8) rounded up to 1, 2, 4 or 8 values).  CSR only. */
 msrep_status msrep_spmm_workspace_size(const msrep_matrix *A, const msrep_partition *part,
                                        int32_t k, size_t *bytes);
 
-/* Y = alpha*A*X + beta*Y for k <= 8 vectors at once, A in CSR over the
+/* Y = alpha*A*X + beta*Y for k >= 1 vectors, A in CSR over the
  * tiles of `part` (from msrep_partition_csr, with its plan).  X holds the k
  * x vectors one after another (x_v = X + v*ldx, n values each, ldx >= n);
  * Y the k y vectors (y_v = Y + v*ldy, ldy >= m); device memory, types as
- * for msrep_spmv.  The library first copies X into the workspace with its
- * k values of each row side by side, so that each nonzero gathers one
- * segment for all k vectors and A is read once.  Every column of Y is
- * computed exactly as msrep_spmv computes y for that x (same order of
- * operations, bit-identical results).  `flags`: MSREP_COMP_ALL /
- * MSREP_COMP_NONE as for msrep_spmv.  Asynchronous on `stream`.
- * Errors: INVALID_ARG (format not CSR, k outside 1..8, ldx < n, ldy < m,
+ * for msrep_spmv.  The vectors are taken in passes of up to
+ * MSREP_SPMM_MAX_K (8): each pass first copies its vectors into the
+ * workspace with their values of each row side by side, so that each
+ * nonzero gathers one segment for all of them and A is read once per pass
+ * (ceil(k / 8) times in all).  Every column of Y is computed exactly as
+ * msrep_spmv computes y for that x (same order of operations,
+ * bit-identical results).  `flags`: MSREP_COMP_ALL / MSREP_COMP_NONE as
+ * for msrep_spmv.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (format not CSR, k < 1, ldx < n, ldy < m,
  * types, alignment as for msrep_spmv), WORKSPACE (no plan, NULL
  * workspace), CUDA. */
 msrep_status msrep_spmm(const msrep_matrix *A, const msrep_partition *part, int32_t k,

@@ -318,14 +318,16 @@ extern "C" {
 msrep_status msrep_spmm_workspace_size(const msrep_matrix *A, const msrep_partition *part,
                                        int32_t k, size_t *bytes) {
   MSREP_TRY(check_matrix(A));
-  if (!part || part->np < 1 || !bytes || k < 1 || k > MSREP_SPMM_MAX_K)
+  if (!part || part->np < 1 || !bytes || k < 1)
     return fail(MSREP_ERR_INVALID_ARG, "bad partition, k or bytes pointer");
   if (A->fmt != MSREP_CSR) return fail(MSREP_ERR_INVALID_ARG, "msrep_spmm takes CSR");
   const int32_t tile = effective_tile(part->tile);
   if (!tile_supported(tile)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", part->tile);
   const int64_t tiles = plan_layout(A->m, A->nnz, part->np, tile).tmax;
   const size_t xs = A->val_dtype == MSREP_F64 ? sizeof(double) : sizeof(float);
-  *bytes = spmm_ws_layout(tiles, spmm_width(k), A->n, xs, nullptr, nullptr, nullptr, nullptr);
+  // one pass of at most MSREP_SPMM_MAX_K vectors at a time
+  *bytes = spmm_ws_layout(tiles, spmm_width(std::min(k, MSREP_SPMM_MAX_K)), A->n, xs, nullptr,
+                          nullptr, nullptr, nullptr);
   return ok();
 }
 
@@ -337,8 +339,7 @@ msrep_status msrep_spmm(const msrep_matrix *A, const msrep_partition *part, int3
   if (A->fmt != MSREP_CSR) return fail(MSREP_ERR_INVALID_ARG, "msrep_spmm takes CSR");
   if (!part || part->np < 1 || !part->start_idx)
     return fail(MSREP_ERR_INVALID_ARG, "bad partition");
-  if (k < 1 || k > MSREP_SPMM_MAX_K)
-    return fail(MSREP_ERR_INVALID_ARG, "k = %d outside 1..%d", k, MSREP_SPMM_MAX_K);
+  if (k < 1) return fail(MSREP_ERR_INVALID_ARG, "k = %d < 1", k);
   if (ldx < A->n || ldy < A->m) return fail(MSREP_ERR_INVALID_ARG, "ldx < n or ldy < m");
   const int32_t tile = effective_tile(part->tile);
   if (!tile_supported(tile)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", part->tile);
@@ -363,18 +364,27 @@ msrep_status msrep_spmm(const msrep_matrix *A, const msrep_partition *part, int3
     return fail(MSREP_ERR_INVALID_ARG, "workspace must be 16-byte aligned");
   if (A->m == 0) return ok();
   cudaStream_t st = as_stream(stream);
-  switch (A->val_dtype) {
-    case MSREP_F64:
-      MSREP_TRY(dispatch_k<PolF64>(A, part, k, alpha, x, ldx, beta, y, ldy, flags, workspace, st));
-      break;
-    case MSREP_F32:
-      MSREP_TRY(dispatch_k<PolF32<float>>(A, part, k, alpha, x, ldx, beta, y, ldy, flags,
-                                          workspace, st));
-      break;
-    default:
-      MSREP_TRY(dispatch_k<PolF32<bf16_t>>(A, part, k, alpha, x, ldx, beta, y, ldy, flags,
-                                           workspace, st));
-      break;
+  // passes of at most MSREP_SPMM_MAX_K vectors, in stream order on the same
+  // workspace; each pass reads A once
+  const size_t es = f64 ? sizeof(double) : sizeof(float);
+  for (int32_t j = 0; j < k; j += MSREP_SPMM_MAX_K) {
+    const int32_t kc = std::min(MSREP_SPMM_MAX_K, k - j);
+    const void *xj = static_cast<const char *>(x) + size_t(j) * size_t(ldx) * es;
+    void *yj = static_cast<char *>(y) + size_t(j) * size_t(ldy) * es;
+    switch (A->val_dtype) {
+      case MSREP_F64:
+        MSREP_TRY(dispatch_k<PolF64>(A, part, kc, alpha, xj, ldx, beta, yj, ldy, flags,
+                                     workspace, st));
+        break;
+      case MSREP_F32:
+        MSREP_TRY(dispatch_k<PolF32<float>>(A, part, kc, alpha, xj, ldx, beta, yj, ldy, flags,
+                                            workspace, st));
+        break;
+      default:
+        MSREP_TRY(dispatch_k<PolF32<bf16_t>>(A, part, kc, alpha, xj, ldx, beta, yj, ldy, flags,
+                                             workspace, st));
+        break;
+    }
   }
   return ok();
 }

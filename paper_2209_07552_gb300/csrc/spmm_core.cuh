@@ -299,8 +299,7 @@ __device__ __forceinline__ void fixup_tile_k(const View &v, int T, int b, const 
     double s = tail[int64_t(b - 1) * KP + j];
     for (int t = 0; t < run; ++t) s += head[int64_t(b + t) * KP + j];
     X *yp = y + j * ldy + r;
-    const double yo = beta == 0.0 ? 0.0 : double(*yp);
-    *yp = static_cast<X>(beta == 0.0 ? alpha * s : alpha * s + beta * yo);
+    *yp = static_cast<X>(finish_merged(s, alpha, beta, beta == 0.0 ? 0.0 : double(*yp)));
   }
 }
 

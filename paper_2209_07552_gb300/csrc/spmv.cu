@@ -561,9 +561,7 @@ __global__ void finish_csc_f32(const int32_t *hot, const double *yperm, uint32_t
   for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < m;
        r += int64_t(gridDim.x) * blockDim.x) {
     const double acc = skew ? yperm[perm_slot(static_cast<int32_t>(r), pmask)] : yacc[r];
-    double v = alpha * acc;
-    if (beta != 0.0) v += beta * double(y[r]);
-    y[r] = float(v);
+    y[r] = float(finish_merged(acc, alpha, beta, beta == 0.0 ? 0.0 : double(y[r])));
   }
 }
 

@@ -692,6 +692,15 @@ __device__ __forceinline__ void csc_stage_x(const CscArgs<Pol> &a, int32_t c0, i
 // fix-up of rows split between tiles, merged in tile (= partition) order
 // ---------------------------------------------------------------------------
 
+// alpha * s + beta * y_in for a row merged in FP64 (split rows), with the
+// rounding spelled out so that every kernel that merges rows (one vector or
+// k of them) rounds alike: one product when beta = 0, else
+// fma(alpha, s, beta * y_in).
+__device__ __forceinline__ double finish_merged(double s, double alpha, double beta,
+                                                double yo) {
+  return beta == 0.0 ? __dmul_rn(alpha, s) : __fma_rn(alpha, s, __dmul_rn(beta, yo));
+}
+
 struct CsrTileView {
   const int32_t *tile_row, *tile_k, *row_ptr, *n_tiles;
   __device__ int count() const { return *n_tiles; }
@@ -772,8 +781,7 @@ __device__ __forceinline__ int fixup_chunk(const View &v, int T, int j0, int32_t
 template <class X>
 __device__ __forceinline__ void fixup_write(X *y, int32_t r, double s, double alpha,
                                             double beta) {
-  const double yo = beta == 0.0 ? 0.0 : double(y[r]);
-  y[r] = static_cast<X>(beta == 0.0 ? alpha * s : alpha * s + beta * yo);
+  y[r] = static_cast<X>(finish_merged(s, alpha, beta, beta == 0.0 ? 0.0 : double(y[r])));
 }
 
 // One thread, tile b.

@@ -396,8 +396,9 @@ def msrep_spmm_workspace_size(A: DeviceMatrix, part: DevicePartition, k: int) ->
 
 def msrep_spmm(A: DeviceMatrix, part: DevicePartition, alpha: float, X, beta: float, Y,
                flags: int = 0, workspace=None, stream=None):
-    """Y = alpha*A*X + beta*Y for k <= 8 vectors: X is a (k, n) and Y a (k, m)
-    device tensor (row v = vector v, rows contiguous).  A must be CSR."""
+    """Y = alpha*A*X + beta*Y for k vectors (passes of up to 8): X is a
+    (k, n) and Y a (k, m) device tensor (row v = vector v, rows contiguous).
+    A must be CSR."""
     import torch
     k = X.shape[0]
     if workspace is None:

@@ -63,10 +63,11 @@ def test_spmm_workspace_size_host_checks(so):
     P = N.DevicePartition.__new__(N.DevicePartition)
     P.c = N.c_msrep_partition()
     P.c.np = 4
-    sizes = [N.msrep_spmm_workspace_size(A, P, k) for k in (1, 2, 3, 4, 8)]
-    # the interleaved copy of X grows with k rounded up to 1, 2, 4, 8
-    assert sizes[0] < sizes[1] < sizes[2] == sizes[3] < sizes[4]
-    for bad in (0, 9):
+    sizes = [N.msrep_spmm_workspace_size(A, P, k) for k in (1, 2, 3, 4, 8, 9, 40)]
+    # the interleaved copy of X grows with k rounded up to 1, 2, 4, 8; more
+    # than 8 vectors go in passes of 8 through the same workspace
+    assert sizes[0] < sizes[1] < sizes[2] == sizes[3] < sizes[4] == sizes[5] == sizes[6]
+    for bad in (0, -3):
         with pytest.raises(N.MsrepError) as e:
             N.msrep_spmm_workspace_size(A, P, bad)
         assert e.value.status == 1

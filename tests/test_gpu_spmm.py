@@ -34,7 +34,7 @@ def _setup(a, dtype, P, tile=0):
     return A, part
 
 
-@pytest.mark.parametrize("k", [1, 2, 3, 5, 8])
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 8, 9, 21])
 def test_fp64_matches_oracle(k):
     import torch
 
@@ -66,12 +66,37 @@ def test_columns_equal_spmv_bit_for_bit(dtype):
     k = 6
     X = torch.from_numpy(np.stack([I.vector(a.n, 300 + v) for v in range(k)])).to("cuda", xt)
     Y0 = torch.from_numpy(np.stack([I.y_vector(a.m, 400 + v) for v in range(k)])).to("cuda", xt)
-    Y = Y0.clone()
-    M.msrep_spmm(A, part, 2.0, X, 0.5, Y)
     ws = M.alloc_workspace(A, part)
+    # alpha = 2, beta = 0.5 scale exactly; 1.5 and -0.3 round, so the merged
+    # rows' finishing must round alike in both kernels too
+    for alpha, beta in ((2.0, 0.5), (1.5, -0.3), (0.7, 0.0)):
+        Y = Y0.clone()
+        M.msrep_spmm(A, part, alpha, X, beta, Y)
+        for v in range(k):
+            y = Y0[v].clone()
+            M.msrep_spmv(A, part, alpha, X[v], beta, y, workspace=ws)
+            assert torch.equal(Y[v], y), (alpha, beta, v)
+
+
+@pytest.mark.parametrize("k", [9, 16, 21])
+def test_more_than_eight_vectors_in_passes(k):
+    """k > 8 vectors run in passes of up to 8 through one workspace: every
+    column still equals msrep_spmv of its x bit for bit."""
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    a = I.rmat(scale=12, nnz=50_000, seed=25)
+    A, part = _setup(a, "f64", 148)
+    X = torch.from_numpy(np.stack([I.vector(a.n, 700 + v) for v in range(k)])).cuda()
+    Y0 = torch.from_numpy(np.stack([I.y_vector(a.m, 800 + v) for v in range(k)])).cuda()
+    Y = Y0.clone()
+    ws = torch.empty(M.msrep_spmm_workspace_size(A, part, k), dtype=torch.uint8, device="cuda")
+    assert ws.numel() == M.msrep_spmm_workspace_size(A, part, 8)
+    M.msrep_spmm(A, part, 1.5, X, -0.25, Y, workspace=ws)
+    wsv = M.alloc_workspace(A, part)
     for v in range(k):
         y = Y0[v].clone()
-        M.msrep_spmv(A, part, 2.0, X[v], 0.5, y, workspace=ws)
+        M.msrep_spmv(A, part, 1.5, X[v], -0.25, y, workspace=wsv)
         assert torch.equal(Y[v], y), v
 
 
@@ -115,6 +140,8 @@ def test_low_precision_error_vs_fp64_oracle():
 
 
 def test_rejects_bad_arguments():
+    import ctypes
+
     import torch
 
     import paper_2209_07552_gb300 as M
@@ -122,9 +149,16 @@ def test_rejects_bad_arguments():
     A, part = _setup(a, "f64", 4)
     X = torch.zeros((9, a.n), dtype=torch.float64, device="cuda")
     Y = torch.zeros((9, a.m), dtype=torch.float64, device="cuda")
-    with pytest.raises(M.MsrepError) as e:
-        M.msrep_spmm(A, part, 1.0, X, 0.0, Y, workspace=torch.empty(1 << 20, dtype=torch.uint8,
-                                                                     device="cuda"))
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    lib = M.native.lib()
+    for ldx, ldy in ((a.n, a.m - 1), (a.n - 1, a.m)):   # ldy < m, ldx < n
+        rc = lib.msrep_spmm(ctypes.byref(A.c), ctypes.byref(part.c), 2, 1.0,
+                            ctypes.c_void_p(X.data_ptr()), ldx, 0.0,
+                            ctypes.c_void_p(Y.data_ptr()), ldy, M.MSREP_F64, 0,
+                            ctypes.c_void_p(ws.data_ptr()), None)
+        assert rc == 1
+    with pytest.raises(M.MsrepError) as e:     # k = 0
+        M.msrep_spmm(A, part, 1.0, X[:0], 0.0, Y[:0], workspace=ws)
     assert e.value.status == 1
     C = M.DeviceMatrix.from_host(a, "csc", "f64")
     cpart = M.DevicePartition(C, 4)
