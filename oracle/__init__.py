@@ -61,6 +61,10 @@ def _lib():
                 ctypes.c_int32, ctypes.c_int64, _i32p, ctypes.c_int32,
                 _i32p, _i32p, _i32p, _i32p, _u8p]
             lib.ref_partition_compressed.restype = ctypes.c_int
+            lib.ref_partition_merge_path.argtypes = [
+                ctypes.c_int32, ctypes.c_int64, _i32p, ctypes.c_int32,
+                _i32p, _i32p, _i32p, _i32p, _u8p, _i32p]
+            lib.ref_partition_merge_path.restype = ctypes.c_int
             lib.ref_local_offsets.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p]
             lib.ref_local_offsets.restype = ctypes.c_int64
             lib.ref_partition_local_compressed.argtypes = [
@@ -124,16 +128,25 @@ def _c(a, dtype) -> np.ndarray:
 # Partitioning: Alg. 2 (pCSR), Alg. 4 (pCSC), Alg. 6 (pCOO).
 # --------------------------------------------------------------------------
 
-def _partition_compressed(ptr, nnz: int, np_: int, with_local: bool):
+def _partition_compressed(ptr, nnz: int, np_: int, with_local: bool,
+                          merge_path: bool = False):
     ptr = _c(ptr, np.int32)
     n_major = ptr.shape[0] - 1
     out = {k: np.empty(np_, np.int32) for k in
            ("start_idx", "end_idx", "start_major", "end_major")}
     out["start_flag"] = np.empty(np_, np.uint8)
-    rc = _lib().ref_partition_compressed(
-        n_major, nnz, _p(ptr, _i32p), np_, _p(out["start_idx"], _i32p),
-        _p(out["end_idx"], _i32p), _p(out["start_major"], _i32p),
-        _p(out["end_major"], _i32p), _p(out["start_flag"], _u8p))
+    if merge_path:
+        out["cut_row"] = np.empty(np_ + 1, np.int32)
+        rc = _lib().ref_partition_merge_path(
+            n_major, nnz, _p(ptr, _i32p), np_, _p(out["start_idx"], _i32p),
+            _p(out["end_idx"], _i32p), _p(out["start_major"], _i32p),
+            _p(out["end_major"], _i32p), _p(out["start_flag"], _u8p),
+            _p(out["cut_row"], _i32p))
+    else:
+        rc = _lib().ref_partition_compressed(
+            n_major, nnz, _p(ptr, _i32p), np_, _p(out["start_idx"], _i32p),
+            _p(out["end_idx"], _i32p), _p(out["start_major"], _i32p),
+            _p(out["end_major"], _i32p), _p(out["start_flag"], _u8p))
     if rc != 0:
         raise ValueError("invalid partition arguments")
     if with_local:
@@ -163,6 +176,14 @@ def partition_csr(row_ptr, nnz: int, np_: int, with_local: bool = False):
 def partition_csc(col_ptr, nnz: int, np_: int, with_local: bool = False):
     """CSC -> pCSC metadata, Alg. 4 (Sec. 3.2.2): Alg. 2 over col_ptr."""
     return _partition_compressed(col_ptr, nnz, np_, with_local)
+
+
+def partition_merge_path(ptr, nnz: int, np_: int, with_local: bool = False):
+    """Row+nonzero merge-path partitioning of CSR (row_ptr) or CSC (col_ptr),
+    reading R10: cuts at equal steps of the merged sequence of row ends and
+    nonzeros, metadata as Alg. 2 for each cut's nonzero range.  Also returns
+    ``cut_row``, the row coordinate of each of the np+1 cuts."""
+    return _partition_compressed(ptr, nnz, np_, with_local, merge_path=True)
 
 
 def partition_coo(row_idx, np_: int, with_local: bool = False):

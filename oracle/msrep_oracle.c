@@ -35,6 +35,15 @@
  *       (row, col): start_row = row_idx[start_idx], end_row =
  *       row_idx[end_idx], start_flag = start_idx > 0 &&
  *       row_idx[start_idx-1] == row_idx[start_idx].
+ *   R10 Row+nonzero merge-path partitioning (the split of Merrill and
+ *       Garland's merge-based CSR SpMV, which the paper cites among the
+ *       single-GPU kernels it builds on): the m row ends and the nnz
+ *       nonzeros form one merged sequence, the row end of row r placed after
+ *       the row's nonzeros (an empty row's end before the next nonzero).
+ *       Cut i is at item floor(i*(m+nnz)/np); partition i takes the nonzeros
+ *       between cuts i and i+1, and its metadata follow Alg. 2 (R3, R4) for
+ *       that nonzero range.  Optional variant: Alg. 2's pure nonzero split
+ *       stays the default.
  *   R9  COO sorted by (col, row) (Sec. 3.2.3 names it, with cost
  *       O(np log n)): Alg. 6 with the column index as the major index, so
  *       start_major/end_major are columns and the flag marks a split
@@ -98,6 +107,55 @@ int ref_partition_compressed(int32_t n_major, int64_t nnz, const int32_t *ptr,
      * row's first nonzero (Sec. 3.2.1). */
     start_flag[i] = (s > (int64_t)ptr[sr]) ? 1 : 0;
   }
+  return 0;
+}
+
+/* Merge-path partitioning, reading R10.  The cuts are found by walking the
+ * merged sequence one item at a time from the start: at (r row ends,
+ * k nonzeros) the next item is row r's end when all of row r's nonzeros
+ * are behind (ptr[r+1] <= k), else nonzero k.  cut_row (np+1 entries, or
+ * NULL) receives the row coordinate of every cut. */
+int ref_partition_merge_path(int32_t n_major, int64_t nnz, const int32_t *ptr,
+                             int32_t np, int32_t *start_idx, int32_t *end_idx,
+                             int32_t *start_major, int32_t *end_major,
+                             uint8_t *start_flag, int32_t *cut_row) {
+  if (np < 1 || n_major < 0 || nnz < 0) return 1;
+  const int64_t total = (int64_t)n_major + nnz;
+  int64_t *cut_k = (int64_t *)malloc(sizeof(int64_t) * ((size_t)np + 1));
+  if (!cut_k) return 2;
+  int32_t r = 0;
+  int64_t k = 0, d = 0;
+  for (int32_t i = 0; i <= np; i++) {
+    const int64_t di = ((int64_t)i * total) / np;
+    while (d < di) {
+      if (r < n_major && (int64_t)ptr[r + 1] <= k)
+        r++;
+      else
+        k++;
+      d++;
+    }
+    cut_k[i] = k;
+    if (cut_row) cut_row[i] = r;
+  }
+  int32_t hint = 0;
+  for (int32_t i = 0; i < np; i++) {
+    const int64_t s = cut_k[i], e = cut_k[i + 1] - 1;
+    start_idx[i] = (int32_t)s;
+    end_idx[i] = (int32_t)e;
+    if (e < s) { /* reading R4 */
+      start_major[i] = 0;
+      end_major[i] = -1;
+      start_flag[i] = 0;
+      continue;
+    }
+    int32_t sr = owner_scan(ptr, n_major, s, hint);
+    int32_t er = owner_scan(ptr, n_major, e, sr);
+    hint = sr;
+    start_major[i] = sr;
+    end_major[i] = er;
+    start_flag[i] = (s > (int64_t)ptr[sr]) ? 1 : 0;
+  }
+  free(cut_k);
   return 0;
 }
 

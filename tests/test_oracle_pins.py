@@ -382,6 +382,79 @@ def test_hub_row_spanning_every_partition_merges_exactly():
 
 
 # --------------------------------------------------------------------------
+# Row+nonzero merge-path partitioning (reading R10)
+# --------------------------------------------------------------------------
+
+def _brute_merge_cuts(ptr, nnz, P):
+    """Cut (row, nonzero) coordinates by a library search: the row
+    coordinate of item d is the last r with ptr[r] + r <= d."""
+    ptr = np.asarray(ptr, np.int64)
+    m = ptr.shape[0] - 1
+    d = (np.arange(P + 1, dtype=np.int64) * (m + nnz)) // P
+    r = np.searchsorted(ptr + np.arange(m + 1), d, side="right") - 1
+    return r, d - r
+
+
+def _brute_meta(ptr, s, e):
+    ptr = np.asarray(ptr, np.int64)
+    m = ptr.shape[0] - 1
+    if e < s:
+        return 0, -1, 0
+    sr = int(np.searchsorted(ptr[:m], s, side="right") - 1)
+    er = int(np.searchsorted(ptr[:m], e, side="right") - 1)
+    return sr, er, int(s > ptr[sr])
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_merge_path_partition_brute_force(k):
+    a = _adversarial()[k]
+    nnz = a.nnz
+    for P in sorted({1, 2, 3, 4, 7, 16, a.m + nnz, a.m + nnz + 3}):
+        got = O.partition_merge_path(a.row_ptr, nnz, P, with_local=True)
+        r, kk = _brute_merge_cuts(a.row_ptr, nnz, P)
+        assert got["cut_row"].tolist() == r.tolist(), P
+        assert got["start_idx"].tolist() == kk[:-1].tolist()
+        assert got["end_idx"].tolist() == (kk[1:] - 1).tolist()
+        for i in range(P):
+            want = _brute_meta(a.row_ptr, int(kk[i]), int(kk[i + 1]) - 1)
+            assert (got["start_major"][i], got["end_major"][i], got["start_flag"][i]) == want
+        # every partition holds floor or ceil of (m + nnz) / P merged items
+        items = np.diff(r + kk)
+        assert set(items.tolist()) <= {(a.m + nnz) // P, -(-(a.m + nnz) // P)}
+
+
+def test_merge_path_closed_forms():
+    """Uniform rows (10 nonzeros + 1 row end each): the merge-path split at
+    P = 4 equals the nonzero split, cutting at rows 500/1000/1500.  One full
+    row after 999 empty ones, P = 2: the first cut comes after the 999 empty
+    rows' ends and the full row's first nonzero."""
+    a = I.uniform_rows()
+    p = O.partition_merge_path(a.row_ptr, a.nnz, 4)
+    q = O.partition_csr(a.row_ptr, a.nnz, 4)
+    for key in ("start_idx", "end_idx", "start_major", "end_major", "start_flag"):
+        assert np.array_equal(p[key], q[key])
+    assert p["cut_row"].tolist() == [0, 500, 1000, 1500, 2000]
+    b = I.csr_from_triplets(1000, 1000, [999] * 1000, list(range(1000)), np.ones(1000))
+    p = O.partition_merge_path(b.row_ptr, b.nnz, 2)
+    assert p["cut_row"].tolist() == [0, 999, 1000]
+    assert p["start_idx"].tolist() == [0, 1] and p["end_idx"].tolist() == [0, 999]
+    assert p["start_flag"].tolist() == [0, 1]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_merge_path_partitioned_spmv_dense(seed):
+    g = I.rng(seed, 29)
+    m, n = int(g.integers(1, 17)), int(g.integers(1, 17))
+    d, a = _tiny(seed + 200, m, n, float(g.uniform(0.05, 0.9)))
+    x = g.uniform(-1, 1, n)
+    yin = g.uniform(-1, 1, m)
+    for P in sorted({1, 2, 3, 5, m + a.nnz, m + a.nnz + 4}):
+        p = O.partition_merge_path(a.row_ptr, a.nnz, P)
+        y = O.pspmv_csr(m, a.row_ptr, a.col_idx, a.val, p, x, 0.5, 2.0, yin)
+        assert np.allclose(y, 0.5 * (d @ x) + 2.0 * yin, rtol=0, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
 # pCOO sorted by column and in no order (reading R9)
 # --------------------------------------------------------------------------
 
