@@ -485,20 +485,24 @@ def run_ours(args):
 
 def run_p_sweep(M, pairs, args, Ps=(148, 148 * 4, 148 * 16, 148 * 64), reps=20):
     """Main-kernel time of every (matrix, format) pair at P = 148 .. 148*64
-    partitions (the sweep of the partition count), FP64, default tile."""
-    import torch
+    partitions (the sweep of the partition count), FP64, default tile; for
+    CSR and CSC also with row+nonzero merge-path cuts ("<P>_merge_path")."""
     out = {}
     for (name, fmt, A, _, x, y, _, _, _) in pairs:
         row = {}
+        variants = [(0, "")]
+        if fmt in ("csr", "csc"):
+            variants.append((M.MSREP_PART_MERGE_PATH, "_merge_path"))
         for P in Ps:
-            part = M.DevicePartition(A, P, tile=args.tile, device=x.device)
-            M.msrep_partition(A, part)
-            ws = M.alloc_workspace(A, part, device=x.device)
-            for _ in range(3):
-                M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
-            row[str(P)] = main_kernel_us(
-                M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws), reps)
-            del part, ws
+            for pflags, tag in variants:
+                part = M.DevicePartition(A, P, tile=args.tile, device=x.device)
+                M.msrep_partition(A, part, pflags)
+                ws = M.alloc_workspace(A, part, device=x.device)
+                for _ in range(3):
+                    M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+                row[f"{P}{tag}"] = main_kernel_us(
+                    M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws), reps)
+                del part, ws
         out[f"{name}/{fmt}"] = row
     return {"kernel_us": out, "P": list(Ps)}
 

@@ -130,6 +130,9 @@ typedef struct {
 
 /* flags for msrep_partition_* */
 #define MSREP_VALIDATE 0x1u /* check structure on the device first; syncs */
+#define MSREP_PART_MERGE_PATH 0x2u /* CSR/CSC: row+nonzero merge-path cuts
+                                      instead of Alg. 2's nonzero cuts (see
+                                      msrep_partition_csr) */
 
 /* Library version string. */
 const char *msrep_version(void);
@@ -155,6 +158,13 @@ msrep_status msrep_plan_size(const msrep_matrix *A, int32_t np, int32_t tile,
  * local row pointers / tile plan when those pointers are non-NULL.  All
  * results are integers and exactly reproducible.  The binary search of
  * Alg. 2 owns nonzero k by row(k) = max{r < m : row_ptr[r] <= k}.
+ * With MSREP_PART_MERGE_PATH the cuts follow the merged sequence of the m
+ * row ends and the nnz nonzeros (the split of merge-based CSR SpMV, which
+ * the paper cites among the single-GPU kernels it builds on; a row's end
+ * comes after its nonzeros): cut i is at item floor(i*(m+nnz)/np), so every
+ * partition holds the same number of rows plus nonzeros, and partition i
+ * takes the nonzeros between cuts i and i+1 (possibly none, when it covers
+ * only empty rows), with the metadata above for that range.
  * Errors: INVALID_ARG (np < 1, NULL array, wrong format), WORKSPACE (plan
  * too small), BAD_MATRIX (with MSREP_VALIDATE: row_ptr not monotone,
  * row_ptr[0] != 0, row_ptr[m] != nnz, column out of range). */
@@ -184,7 +194,8 @@ msrep_status msrep_partition_csc(const msrep_matrix *A, msrep_partition *part,
  *     any row), start_flag = 0.
  * For COO_BY_COL and COO_UNSORTED a plan (msrep_plan_size bytes) receives
  * the hub rows, found as for msrep_partition_csc.  Validation checks the
- * indices' range and, for the two sorted orders, the order. */
+ * indices' range and, for the two sorted orders, the order.
+ * MSREP_PART_MERGE_PATH is INVALID_ARG here. */
 msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *part,
                                  unsigned flags, void *stream);
 

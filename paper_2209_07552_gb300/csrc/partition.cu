@@ -76,6 +76,28 @@ __device__ __forceinline__ int32_t last_le_warp(const T *__restrict__ ptr, int32
   return lo + __popc(__ballot_sync(0xffffffffu, le)) - 1;
 }
 
+// last_le_warp on the merge path: largest r in [lo, hi] with
+// ptr[r] + r <= d, the row coordinate of item d of the merged sequence of
+// row ends and nonzeros.  ptr[r] + r is strictly increasing.  Requires
+// ptr[lo] + lo <= d; every lane returns the result.
+__device__ __forceinline__ int32_t path_row_warp(const int32_t *__restrict__ ptr, int32_t lo,
+                                                 int32_t hi, int64_t d) {
+  const int lane = threadIdx.x & 31;
+  while (hi - lo >= 32) {
+    const int64_t span = int64_t(hi) - lo;
+    const int32_t q = lo + static_cast<int32_t>((int64_t(lane) + 1) * span / 33);
+    const bool le = static_cast<int64_t>(__ldg(ptr + q)) + q <= d;
+    const int t = __popc(__ballot_sync(0xffffffffu, le));
+    const int32_t qlo = __shfl_sync(0xffffffffu, q, t > 0 ? t - 1 : 0);
+    const int32_t qhi = __shfl_sync(0xffffffffu, q, t < 32 ? t : 31);
+    if (t > 0) lo = qlo;
+    if (t < 32) hi = qhi - 1;
+  }
+  const bool le =
+      lo + lane <= hi && static_cast<int64_t>(__ldg(ptr + lo + lane)) + lo + lane <= d;
+  return lo + __popc(__ballot_sync(0xffffffffu, le)) - 1;
+}
+
 // Merge-path coordinate of diagonal d: largest r in [lo, hi] with
 // ptr[r] + r <= d (rows 0..r-1 have ended; ties consume the row end first).
 __device__ __forceinline__ int32_t path_row(const int32_t *__restrict__ ptr,
@@ -95,32 +117,53 @@ __device__ __forceinline__ int32_t path_row(const int32_t *__restrict__ ptr,
 // ---------------------------------------------------------------------------
 
 // One warp per partition i (and one for the closing cut i = np).
+// merge_path = 0: Alg. 2's nonzero split, cut i at nonzero floor(i nnz/np).
+// merge_path = 1: cut i at item floor(i (n_major + nnz) / np) of the merged
+// sequence of row ends and nonzeros; partition i then holds the nonzeros
+// between cuts i and i+1, with Alg. 2's metadata for that range.
 __global__ void part_meta_compressed(const int32_t *__restrict__ ptr,
                                      int32_t n_major, int64_t nnz, int32_t np,
                                      int32_t *start_idx, int32_t *end_idx,
                                      int32_t *start_major, int32_t *end_major,
                                      uint8_t *start_flag, int64_t *plan_D,
-                                     int32_t *plan_R) {
+                                     int32_t *plan_R, int merge_path) {
   const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const bool lead = (threadIdx.x & 31) == 0;
   if (i > np) return;  // warp-uniform
-  int64_t s = (i * nnz) / np;
-  if (plan_D) {
-    // level-1 cut of the tile plan: (R(s_i), s_i) with R over [0, n_major]
-    int32_t R;
-    if (i == 0)
-      R = 0;
-    else if (i == np)
-      R = n_major;
-    else
-      R = last_le_warp(ptr, 0, n_major, s);
-    if (lead) {
+  int64_t s, e;
+  if (merge_path) {
+    const int64_t total = int64_t(n_major) + nnz;
+    const int64_t d = (i * total) / np;
+    const int32_t R = path_row_warp(ptr, static_cast<int32_t>(d > nnz ? d - nnz : 0),
+                                    static_cast<int32_t>(d < n_major ? d : n_major), d);
+    s = d - R;
+    if (plan_D && lead) {
       plan_R[i] = R;
-      plan_D[i] = (i == 0) ? 0 : s + R;
+      plan_D[i] = d;
     }
+    if (i == np) return;
+    const int64_t d1 = ((i + 1) * total) / np;
+    const int32_t R1 = path_row_warp(ptr, R, static_cast<int32_t>(d1 < n_major ? d1 : n_major), d1);
+    e = d1 - R1 - 1;
+  } else {
+    s = (i * nnz) / np;
+    if (plan_D) {
+      // level-1 cut of the tile plan: (R(s_i), s_i) with R over [0, n_major]
+      int32_t R;
+      if (i == 0)
+        R = 0;
+      else if (i == np)
+        R = n_major;
+      else
+        R = last_le_warp(ptr, 0, n_major, s);
+      if (lead) {
+        plan_R[i] = R;
+        plan_D[i] = (i == 0) ? 0 : s + R;
+      }
+    }
+    if (i == np) return;
+    e = ((i + 1) * nnz) / np - 1;
   }
-  if (i == np) return;
-  int64_t e = ((i + 1) * nnz) / np - 1;
   if (e < s) {
     if (lead) {
       start_idx[i] = static_cast<int32_t>(s);
@@ -602,7 +645,8 @@ static msrep_status partition_compressed(const msrep_matrix *A,
   const int blocks = static_cast<int>(ceil_div(int64_t(p->np + 1) * 32, threads));
   part_meta_compressed<<<blocks, threads, 0, st>>>(
       A->ptr, n_major, A->nnz, p->np, p->start_idx, p->end_idx,
-      p->start_major, p->end_major, p->start_flag, D, R);
+      p->start_major, p->end_major, p->start_flag, D, R,
+      (flags & MSREP_PART_MERGE_PATH) ? 1 : 0);
   MSREP_CUDA_TRY(cudaGetLastError());
   if (p->local_off) {
     local_off_scan<<<1, 1024, 0, st>>>(p->start_major, p->end_major, p->np,
@@ -701,6 +745,8 @@ msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
   if (!coo_format(A->fmt))
     return fail(MSREP_ERR_INVALID_ARG, "matrix format %d is not COO", A->fmt);
   MSREP_TRY(check_partition(p));
+  if (flags & MSREP_PART_MERGE_PATH)
+    return fail(MSREP_ERR_INVALID_ARG, "merge-path partitioning takes CSR or CSC");
   const bool scatter = coo_scatter_format(A->fmt);
   if (scatter && p->plan) {
     if (p->plan_bytes < static_cast<int64_t>(kScatterPlanBytes))

@@ -24,6 +24,7 @@ MSREP_CSR, MSREP_CSC, MSREP_COO, MSREP_COO_BY_COL, MSREP_COO_UNSORTED = 0, 1, 2,
 COO_FORMATS = (MSREP_COO, MSREP_COO_BY_COL, MSREP_COO_UNSORTED)
 MSREP_F64, MSREP_F32, MSREP_BF16 = 0, 1, 2
 MSREP_VALIDATE = 0x1
+MSREP_PART_MERGE_PATH = 0x2
 MSREP_COMP_ALL = 0x10
 MSREP_COMP_NONE = 0x20
 MSREP_STREAM_TMA = 0x40

@@ -54,14 +54,14 @@ def oracle_partition(a: I.CSR, fmt: str, P: int, with_local=False):
 
 
 def gpu_spmv(a: I.CSR, fmt: str, P: int, x, alpha=1.0, beta=0.0, y0=None,
-             tile=0, val_dtype="f64", flags=0, repeat=1):
+             tile=0, val_dtype="f64", flags=0, repeat=1, part_flags=0):
     """Partition and run msrep_spmv on the GPU; returns y as numpy."""
     import torch
 
     import paper_2209_07552_gb300 as M
     A = M.DeviceMatrix.from_host(a, fmt, val_dtype)
     part = M.DevicePartition(A, P, tile=tile)
-    M.msrep_partition(A, part)
+    M.msrep_partition(A, part, part_flags)
     xt = torch.float64 if val_dtype == "f64" else torch.float32
     xd = torch.from_numpy(np.asarray(x)).to("cuda", xt)
     if y0 is None:
