@@ -514,6 +514,103 @@ static msrep_status hot_rows_smem_opt_in() {
   return MSREP_OK;
 }
 
+// Frequent-row search (only for a matrix with hub rows), step 1: the hub
+// rows take their slots of the frequent-row table first; then the rows of
+// kWarmSample evenly spaced nonzeros are counted in an open-addressing table
+// of kWarmTab slots (twice the samples, so probing ends).  The tables hold
+// row + 1 (0 = empty), so that they start all zero.
+__global__ void warm_count(const int32_t *__restrict__ row_idx, int64_t nnz, const int32_t *hot,
+                           int32_t *warm, int32_t *key, int32_t *cnt) {
+  const int nh = hot[0];
+  if (nh == 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0)
+    for (int q = 0; q < nh && q < kMaxHot; ++q) {
+      const int32_t r = hot[1 + q];
+      if (r >= 0) atomicCAS(warm + warm_slot(r), 0, r + 1);
+    }
+  const int S = static_cast<int>(nnz < kWarmSample ? nnz : kWarmSample);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x) {
+    const int32_t r = __ldg(row_idx + (2 * int64_t(i) + 1) * nnz / (2 * int64_t(S)));
+    uint32_t h = (static_cast<uint32_t>(r) * kPermMul) >> (32 - kWarmTabBits);
+    for (int probe = 0; probe < kWarmTab; ++probe) {
+      const int32_t old = atomicCAS(key + h, 0, r + 1);
+      if (old == 0 || old == r + 1) {
+        atomicAdd(cnt + h, 1);
+        break;
+      }
+      h = (h + 1) & (kWarmTab - 1);
+    }
+  }
+}
+
+// Step 2: histogram of the sample counts >= kWarmMin (counts above 255 as
+// 255) into hist[256].  Rows seen fewer times never qualify; they are most
+// rows and would all land in one bin.
+__global__ void warm_hist(const int32_t *hot, const int32_t *cnt, int32_t *hist) {
+  __shared__ int h[256];
+  if (hot[0] == 0) return;
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kWarmTab; i += gridDim.x * blockDim.x) {
+    const int c = cnt[i];
+    if (c >= kWarmMin) atomicAdd(h + min(c, 255), 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (h[i]) atomicAdd(hist + i, h[i]);
+}
+
+// Step 3: every counted row whose count reaches T claims its slot if it is
+// still free, T the smallest count >= kWarmMin that at most kWarm rows
+// reach.
+__global__ void warm_select(const int32_t *hot, const int32_t *key, const int32_t *cnt,
+                            const int32_t *hist, int32_t *warm) {
+  __shared__ int thresh;
+  if (hot[0] == 0) return;
+  if (threadIdx.x == 0) {
+    int cum = 0, T = 256;
+    for (int c = 255; c >= kWarmMin; --c) {
+      if (cum + hist[c] > kWarm) break;
+      cum += hist[c];
+      T = c;
+    }
+    thresh = T;
+  }
+  __syncthreads();
+  const int T = thresh;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kWarmTab; i += gridDim.x * blockDim.x) {
+    if (cnt[i] < T) continue;
+    const int32_t k = key[i];
+    if (k > 0) atomicCAS(warm + warm_slot(k - 1), 0, k);
+  }
+}
+
+// Hub rows, then the frequent-row table, of a scatter (CSC, or COO sorted by
+// column or in no order): hot, warm and the search scratch (key, cnt) are
+// in the plan.
+static msrep_status find_frequent_rows(const int32_t *row_idx, int64_t nnz, int32_t *hot,
+                                       int32_t *warm, int32_t *key, int32_t *cnt,
+                                       cudaStream_t st) {
+  MSREP_TRY(hot_rows_smem_opt_in());
+  hot_rows<<<1, 1024, kHotSmem, st>>>(row_idx, nnz, hot);
+  MSREP_CUDA_TRY(cudaGetLastError());
+  // table, scratch and histogram lie back to back, all starting at zero
+  int32_t *hist = cnt + kWarmTab;
+  MSREP_CUDA_TRY(cudaMemsetAsync(warm, 0, reinterpret_cast<char *>(hist + 256) -
+                                              reinterpret_cast<char *>(warm), st));
+  const int S = static_cast<int>(nnz < kWarmSample ? nnz : kWarmSample);
+  warm_count<<<static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(S, 256),
+                                                                       4 * sm_count()))),
+               256, 0, st>>>(row_idx, nnz, hot, warm, key, cnt);
+  MSREP_CUDA_TRY(cudaGetLastError());
+  warm_hist<<<kWarmTab / 256, 256, 0, st>>>(hot, cnt, hist);
+  MSREP_CUDA_TRY(cudaGetLastError());
+  warm_select<<<kWarmTab / 256, 256, 0, st>>>(hot, key, cnt, hist, warm);
+  MSREP_CUDA_TRY(cudaGetLastError());
+  return MSREP_OK;
+}
+
+
 __global__ void validate_compressed(const int32_t *__restrict__ ptr,
                                     int32_t n_major, int64_t nnz,
                                     const int32_t *__restrict__ idx,
@@ -632,7 +729,7 @@ static msrep_status partition_compressed(const msrep_matrix *A,
   if (flags & MSREP_VALIDATE) MSREP_TRY(run_validation(A, st));
   const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
   const int32_t tile = effective_tile(p->tile);
-  PlanLayout L = plan_layout(n_major, A->nnz, p->np, tile);
+  PlanLayout L = plan_layout(n_major, A->nnz, p->np, tile, A->fmt == MSREP_CSC);
   if (p->plan && p->plan_bytes < static_cast<int64_t>(L.bytes))
     return fail(MSREP_ERR_WORKSPACE, "plan buffer has %lld bytes, needs %zu",
                 (long long)p->plan_bytes, L.bytes);
@@ -678,10 +775,10 @@ static msrep_status partition_compressed(const msrep_matrix *A,
                                       toff, trow, tk);
     MSREP_CUDA_TRY(cudaGetLastError());
     if (A->fmt == MSREP_CSC) {
-      MSREP_TRY(hot_rows_smem_opt_in());
-      hot_rows<<<1, 1024, kHotSmem, st>>>(A->idx, A->nnz,
-                                          reinterpret_cast<int32_t *>(plan + L.off_hot));
-      MSREP_CUDA_TRY(cudaGetLastError());
+      int32_t *wtab = reinterpret_cast<int32_t *>(plan + L.off_wtab);
+      MSREP_TRY(find_frequent_rows(A->idx, A->nnz, reinterpret_cast<int32_t *>(plan + L.off_hot),
+                                   reinterpret_cast<int32_t *>(plan + L.off_warm), wtab,
+                                   wtab + kWarmTab, st));
     }
   }
   return ok();
@@ -725,7 +822,7 @@ msrep_status msrep_plan_size(const msrep_matrix *A, int32_t np, int32_t tile,
     return ok();
   }
   const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
-  *bytes = static_cast<int64_t>(plan_layout(n_major, A->nnz, np, t).bytes);
+  *bytes = static_cast<int64_t>(plan_layout(n_major, A->nnz, np, t, A->fmt == MSREP_CSC).bytes);
   return ok();
 }
 
@@ -781,9 +878,11 @@ msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
     MSREP_CUDA_TRY(cudaGetLastError());
   }
   if (scatter && p->plan) {
-    MSREP_TRY(hot_rows_smem_opt_in());
-    hot_rows<<<1, 1024, kHotSmem, st>>>(A->idx2, A->nnz, static_cast<int32_t *>(p->plan));
-    MSREP_CUDA_TRY(cudaGetLastError());
+    char *plan = static_cast<char *>(p->plan);
+    int32_t *wtab = reinterpret_cast<int32_t *>(plan + kScatterTabOff);
+    MSREP_TRY(find_frequent_rows(A->idx2, A->nnz, reinterpret_cast<int32_t *>(plan),
+                                 reinterpret_cast<int32_t *>(plan + kScatterWarmOff), wtab,
+                                 wtab + kWarmTab, st));
   }
   return ok();
 }

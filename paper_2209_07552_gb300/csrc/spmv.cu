@@ -312,38 +312,44 @@ __global__ void __launch_bounds__(kThreads) coo_stream(CooArgs<Pol> a) {
 }
 
 template <class Pol, int IPT>
-// Four resident blocks (64 registers a thread) match the shared-memory
-// budget of the x and column-pointer stages.
+// Four resident blocks (64 registers a thread); the column-pointer stages
+// and the frequent-row table fit four blocks' shared memory.
 __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
   grid_dependency_wait();
-  // dynamic shared memory: per warp, x values then column pointers
+  // dynamic shared memory: per warp, the tile's column pointers
   extern __shared__ __align__(16) unsigned char dsm[];
   constexpr int CAP = 32 * IPT + 8;
   const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double *s_x = reinterpret_cast<double *>(dsm) + wid * CAP;
-  int32_t *s_cp = reinterpret_cast<int32_t *>(reinterpret_cast<double *>(dsm) + kWarps * CAP) +
-                  wid * CAP;
-  __shared__ double s_hot[kWarps][kMaxHot];
-  HotRows hot;
-  hot.load(a.hot, s_hot);
+  int32_t *s_cp = reinterpret_cast<int32_t *>(dsm) + wid * CAP;
+  __shared__ int32_t s_wtag[kWarm];
+  __shared__ double s_wacc[kWarm];
+  const bool skew = csc_skewed(a.hot, a.yperm);
+  WarmRows warm;
+  if (skew) warm.load(a.warm, s_wtag, s_wacc);
   auto tiles = [&](auto with_hot) {
     for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
       const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
       const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
       const int32_t cend = min(c1 + 1, a.n + 1);
       for (int32_t c = c0 + lane; c < cend; c += 32) s_cp[c - c0] = __ldg(a.col_ptr + c);
-      csc_stage_x(a, c0, c1, s_x);
       __syncwarp();
+      // scale * x of tile column c, read when a lane reaches the column
+      const auto xat = [&a, c0](int c) {
+        const int32_t g = c0 + c;
+        if (g >= a.n) return 0.0;
+        const double xv = double(load_x(a.x, g));
+        return a.scaled ? __dmul_rn(xv, a.scale) : xv;
+      };
       csc_tile_compute<Pol, decltype(with_hot)::value>(
-          a, c0, k0, c1, k1, s_cp, s_x, Seg<int32_t>{a.row_idx, 0},
-          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{}, hot);
+          a, c0, k0, c1, k1, s_cp, xat, Seg<int32_t>{a.row_idx, 0},
+          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{}, warm);
       __syncwarp();
     }
   };
-  if (csc_skewed(a.hot, a.yperm)) {
+  if (skew) {
     tiles(std::true_type{});
-    hot.flush(a.yperm, a.pmask, s_hot);
+    warm.flush(a.yperm, a.pmask);
   } else {
     tiles(std::false_type{});
   }
@@ -419,12 +425,13 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
     fill_tail(val_s(s), a.val, v, v.base, g_end);
     csc_stage_x(a, c.x, c.z, xs);
     __syncwarp();
+    const auto xat = [xs](int j) { return xs[j]; };
     if (skew)
-      csc_tile_compute<Pol, true>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xs,
+      csc_tile_compute<Pol, true>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xat,
                                   Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base},
                                   nnz, SharedSrc{}, hot);
     else
-      csc_tile_compute<Pol, false>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xs,
+      csc_tile_compute<Pol, false>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xat,
                                    Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base},
                                    nnz, SharedSrc{}, hot);
     __syncwarp();
@@ -463,7 +470,8 @@ struct ScatterArgs {
   uint32_t pmask;
   double scale;   // alpha on the FP64 path, 1 when a finishing pass follows
   bool scaled;
-  const int32_t *hot;  // hub rows, or null
+  const int32_t *hot;   // hub rows, or null
+  const int32_t *warm;  // frequent-row table (kWarm entries)
   int64_t nnz;
 };
 
@@ -471,10 +479,11 @@ template <class Pol>
 __global__ void __launch_bounds__(kThreads, 4) coo_scatter(ScatterArgs<Pol> a) {
   grid_dependency_wait();
   using LV = typename LoadT<typename Pol::V>::type;
-  __shared__ double s_hot[kWarps][kMaxHot];
+  __shared__ int32_t s_wtag[kWarm];
+  __shared__ double s_wacc[kWarm];
   const bool skew = a.hot != nullptr && csc_skewed(a.hot, a.yperm);
-  HotRows hot;
-  if (skew) hot.load(a.hot, s_hot);
+  WarmRows hot;
+  if (skew) hot.load(a.warm, s_wtag, s_wacc);
   const int64_t groups = (a.nnz + 7) >> 3;
   const int64_t step = int64_t(gridDim.x) * blockDim.x;
   auto run = [&](auto with_hot) {
@@ -500,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 4) coo_scatter(ScatterArgs<Pol> a) {
   };
   if (skew) {
     run(std::true_type{});
-    hot.flush(a.yperm, a.pmask, s_hot);
+    hot.flush(a.yperm, a.pmask);
   } else {
     run(std::false_type{});
   }
@@ -774,7 +783,7 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
                             double alpha, const void *x, double beta, void *y,
                             unsigned flags, const Workspace &w, cudaStream_t st) {
   const int32_t tile = effective_tile(p->tile);
-  PlanLayout L = plan_layout(A->n, A->nnz, p->np, tile);
+  PlanLayout L = plan_layout(A->n, A->nnz, p->np, tile, true);
   const char *plan = static_cast<const char *>(p->plan);
   constexpr bool kF64 = sizeof(typename Pol::X) == 8;
   CscArgs<Pol> a;
@@ -789,6 +798,7 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   a.err = kernel_err_ptr();
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   a.hot = reinterpret_cast<const int32_t *>(plan + L.off_hot);
+  a.warm = reinterpret_cast<const int32_t *>(plan + L.off_warm);
   const int64_t m = A->m;
   const int sg = 4 * sm_count();
   const int64_t pn = w.perm ? perm_extent(m) : 0;
@@ -813,7 +823,7 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   MSREP_TRY(launch_tiles(csc_stream<Pol, IPT>, csc_direct<Pol, IPT>,
                          StageGeom<typename Pol::V, IPT, 2>::BLOCK +
                              sizeof(double) * kWarps * (32 * IPT + 8),
-                         (sizeof(double) + sizeof(int32_t)) * kWarps * (32 * IPT + 8), 0,
+                         sizeof(int32_t) * kWarps * (32 * IPT + 8), 0,
                          (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
   if (kF64) {
     if (w.perm)
@@ -843,6 +853,7 @@ static msrep_status run_coo_scatter(const msrep_matrix *A, const msrep_partition
   a.val = static_cast<const typename Pol::V *>(A->val);
   a.x = static_cast<const typename Pol::X *>(x);
   a.hot = static_cast<const int32_t *>(p->plan);
+  a.warm = reinterpret_cast<const int32_t *>(static_cast<const char *>(p->plan) + kScatterWarmOff);
   a.nnz = A->nnz;
   const int64_t m = A->m;
   const int sg = 4 * sm_count();
@@ -999,7 +1010,8 @@ msrep_status spmv_run(const msrep_matrix *A, const msrep_partition *part, double
                   kScatterPlanBytes);
   } else if (A->fmt != MSREP_COO) {
     const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
-    const int64_t need = static_cast<int64_t>(plan_layout(n_major, A->nnz, part->np, tile).bytes);
+    const int64_t need = static_cast<int64_t>(
+        plan_layout(n_major, A->nnz, part->np, tile, A->fmt == MSREP_CSC).bytes);
     if (!part->plan || part->plan_bytes < need)
       return fail(MSREP_ERR_WORKSPACE, "CSR/CSC SpMV needs the partition's tile plan (%lld bytes)",
                   (long long)need);

@@ -572,7 +572,8 @@ struct CscArgs {
   double scale;  // alpha on the FP64 path, 1 when a finishing pass follows
   bool scaled;   // scale != 1
   const int32_t *tile_row, *tile_k;
-  const int32_t *hot;  // hub rows: count, then kMaxHot rows (-1 = none)
+  const int32_t *hot;   // hub rows: count, then kMaxHot rows (-1 = none)
+  const int32_t *warm;  // frequent-row table, kWarm entries (row + 1, 0 = empty)
   int32_t n;
   int *err;
 };
@@ -626,14 +627,50 @@ struct HotRows {
   }
 };
 
-// cp[j] = col_ptr[c0 + j], j = 0..c1-c0, and xs[j] = scale * x[c0 + j] for
-// the columns that hold nonzeros of the tile, both in shared memory.
-template <class Pol, bool kSkew, class Src>
+// Sums of the frequent rows of a skewed scatter (see kWarm): one
+// direct-mapped table per thread block in shared memory, its row tags
+// copied from the plan.  Each warp adds its products for the tabled rows to
+// the block's slots with shared-memory atomics; the block adds every
+// non-zero slot to the permuted accumulator once, at its end.  The hub rows
+// hold slots of their own, so this also does what HotRows does.
+struct WarmRows {
+  int32_t *tag;  // kWarm row tags, row + 1 (0 = empty), shared memory
+  double *acc;   // kWarm sums, shared memory
+  // every thread of the block
+  __device__ __forceinline__ void load(const int32_t *warm, int32_t *s_tag, double *s_acc) {
+    tag = s_tag;
+    acc = s_acc;
+    for (int i = threadIdx.x; i < kWarm; i += blockDim.x) {
+      s_tag[i] = __ldg(warm + i);
+      s_acc[i] = 0.0;
+    }
+    __syncthreads();
+  }
+  __device__ __forceinline__ bool take(int32_t row, double v) {
+    const uint32_t s = warm_slot(row);
+    if (tag[s] != row + 1) return false;
+    atomicAdd(acc + s, v);
+    return true;
+  }
+  // every thread of the block, after its last tile
+  __device__ __forceinline__ void flush(double *yperm, uint32_t pmask) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < kWarm; i += blockDim.x) {
+      const int32_t row = tag[i] - 1;
+      if (row >= 0 && acc[i] != 0.0) atomicAdd(yperm + perm_slot(row, pmask), acc[i]);
+    }
+  }
+};
+
+// cp[j] = col_ptr[c0 + j], j = 0..c1-c0, in shared memory; xat(j) = scale *
+// x[c0 + j] for the columns that hold nonzeros of the tile.  Hot is HotRows
+// or WarmRows.
+template <class Pol, bool kSkew, class Src, class Hot, class XAt>
 __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t c0, int32_t k0,
                                                  int32_t c1, int32_t k1, const int32_t *cp,
-                                                 const double *xs, Seg<int32_t> row,
+                                                 XAt xat, Seg<int32_t> row,
                                                  Seg<typename Pol::V> val, int64_t nnz, Src src,
-                                                 HotRows &hot) {
+                                                 Hot &hot) {
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
   const int ncols = c1 - c0;
@@ -642,10 +679,10 @@ __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t 
   const int64_t ka = lr.ka, kb = lr.kb;
   int c = upper_bound_smem(s_end, ncols, static_cast<int32_t>(ka));
   int32_t cend = c < ncols ? s_end[c] : INT32_MAX;
-  // x of the current column, reloaded from shared memory only when the
-  // column changes (xs has an entry for every column index c <= ncols that
-  // holds nonzeros of the tile)
-  double xc = xs[c];
+  // x of the current column, reloaded only when the column changes (xat has
+  // a value for every column index c <= ncols that holds nonzeros of the
+  // tile)
+  double xc = xat(c);
   for (int64_t gg = lr.glo; gg < lr.ghi; ++gg) {
     const int64_t g8 = gg << 3;
     int32_t rw[8];
@@ -661,7 +698,7 @@ __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t 
           ++c;
           cend = c < ncols ? s_end[c] : INT32_MAX;
         } while (cend <= e);
-        xc = xs[c];
+        xc = xat(c);
       }
       const double prod = __dmul_rn(double(v[u]), in ? xc : 0.0);
       if (in) {
