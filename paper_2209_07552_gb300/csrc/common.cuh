@@ -72,7 +72,8 @@ inline bool tile_supported(int t) {
 //   int32  tile_row[Tmax+1], tile_k[Tmax+1]  tile start coordinates; the
 //                         entry after the last tile is (n_major, nnz).
 //   int32  hot[1+kMaxHot] CSC only: count, then the hub rows (-1 = none)
-//   int32  warm[kWarm]    CSC only: the frequent-row table (row + 1; 0 = empty)
+//   uint64 warm[kWarm]    CSC only: the frequent-row table,
+//                         (priority << 32) | ~row per slot, 0 = empty
 //   int32  wkey[kWarmTab], wcnt[kWarmTab], whist[256]  CSC only:
 //                         partition-time scratch of the frequent-row search
 struct PlanLayout {
@@ -113,10 +114,11 @@ __host__ __device__ __forceinline__ uint32_t perm_slot(int32_t r, uint32_t mask)
 // warm_slot(r) (the top bits of r * kPermMul, so rows that differ only in
 // their high bits spread out); a slot holds one row.  They are chosen at
 // partition time from kWarmSample evenly spaced nonzeros, counted in a
-// kWarmTab-slot hash table: the hub rows first, then every row whose sample
-// count reaches the largest threshold (>= kWarmMin) that at most kWarm rows
-// reach.  On the R-MAT workload this removes about a fifth of the atomic
-// adds of its scatter.
+// kWarmTab-slot hash table: the hub rows and every row whose sample count
+// reaches the largest threshold (>= kWarmMin) that at most kWarm rows reach
+// claim their slots, and a slot keeps the most frequent claimant (hub rows
+// first, the smaller row on ties).  On the R-MAT workload this removes about
+// a fifth of the atomic adds of its scatter.
 constexpr int kWarmBits = 11;
 constexpr int kWarm = 1 << kWarmBits;
 constexpr int kWarmSample = 1 << 16;
@@ -156,7 +158,7 @@ inline PlanLayout plan_layout(int64_t n_major, int64_t nnz, int32_t np,
   L.off_warm = o;
   L.off_wtab = o;
   if (warm) {
-    o = align256(o + sizeof(int32_t) * kWarm);
+    o = align256(o + sizeof(uint64_t) * kWarm);
     L.off_wtab = o;
     o = align256(o + sizeof(int32_t) * (2 * kWarmTab + 256));
   }
@@ -167,14 +169,14 @@ inline PlanLayout plan_layout(int64_t n_major, int64_t nnz, int32_t np,
 // COO sorted by column or in no order: every partition may add to any row,
 // so its SpMV is a scatter, and its plan holds only what that scatter
 // needs: the hub rows (int32 hot[1+kMaxHot] at offset 0), the frequent-row
-// table (int32 warm[kWarm] at kScatterWarmOff) and the scratch of its
+// table (uint64 warm[kWarm] at kScatterWarmOff) and the scratch of its
 // search (at kScatterTabOff).
 inline bool coo_scatter_format(int32_t fmt) {
   return fmt == MSREP_COO_BY_COL || fmt == MSREP_COO_UNSORTED;
 }
 inline bool coo_format(int32_t fmt) { return fmt == MSREP_COO || coo_scatter_format(fmt); }
 constexpr size_t kScatterWarmOff = 256;
-constexpr size_t kScatterTabOff = kScatterWarmOff + sizeof(int32_t) * kWarm;
+constexpr size_t kScatterTabOff = kScatterWarmOff + sizeof(uint64_t) * kWarm;
 constexpr size_t kScatterPlanBytes = kScatterTabOff + sizeof(int32_t) * (2 * kWarmTab + 256);
 
 // COO tiles: each partition is split into the same number G of sub-ranges

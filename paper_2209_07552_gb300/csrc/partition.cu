@@ -514,19 +514,27 @@ static msrep_status hot_rows_smem_opt_in() {
   return MSREP_OK;
 }
 
+// A frequent-row table slot during the search: (priority << 32) | ~row,
+// 0 = empty.  atomicMax keeps the row of highest priority (sample count;
+// hub rows highest), the smaller row on ties, whatever the order of the
+// claims, so the table is the same on every run.
+__device__ __forceinline__ unsigned long long warm_entry(uint32_t prio, int32_t row) {
+  return (static_cast<unsigned long long>(prio) << 32) | ~static_cast<uint32_t>(row);
+}
+
 // Frequent-row search (only for a matrix with hub rows), step 1: the hub
-// rows take their slots of the frequent-row table first; then the rows of
-// kWarmSample evenly spaced nonzeros are counted in an open-addressing table
-// of kWarmTab slots (twice the samples, so probing ends).  The tables hold
-// row + 1 (0 = empty), so that they start all zero.
+// rows claim their slots of the frequent-row table at top priority; the
+// rows of kWarmSample evenly spaced nonzeros are counted in an
+// open-addressing table of kWarmTab slots (twice the samples, so probing
+// ends), which holds row + 1 (0 = empty).  Everything starts all zero.
 __global__ void warm_count(const int32_t *__restrict__ row_idx, int64_t nnz, const int32_t *hot,
-                           int32_t *warm, int32_t *key, int32_t *cnt) {
+                           unsigned long long *warm, int32_t *key, int32_t *cnt) {
   const int nh = hot[0];
   if (nh == 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0)
     for (int q = 0; q < nh && q < kMaxHot; ++q) {
       const int32_t r = hot[1 + q];
-      if (r >= 0) atomicCAS(warm + warm_slot(r), 0, r + 1);
+      if (r >= 0) atomicMax(warm + warm_slot(r), warm_entry(0xffffffffu, r));
     }
   const int S = static_cast<int>(nnz < kWarmSample ? nnz : kWarmSample);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < S; i += gridDim.x * blockDim.x) {
@@ -560,11 +568,11 @@ __global__ void warm_hist(const int32_t *hot, const int32_t *cnt, int32_t *hist)
     if (h[i]) atomicAdd(hist + i, h[i]);
 }
 
-// Step 3: every counted row whose count reaches T claims its slot if it is
-// still free, T the smallest count >= kWarmMin that at most kWarm rows
-// reach.
+// Step 3: every counted row whose count reaches T claims its slot with its
+// count as priority, T the smallest count >= kWarmMin that at most kWarm
+// rows reach.
 __global__ void warm_select(const int32_t *hot, const int32_t *key, const int32_t *cnt,
-                            const int32_t *hist, int32_t *warm) {
+                            const int32_t *hist, unsigned long long *warm) {
   __shared__ int thresh;
   if (hot[0] == 0) return;
   if (threadIdx.x == 0) {
@@ -579,9 +587,10 @@ __global__ void warm_select(const int32_t *hot, const int32_t *key, const int32_
   __syncthreads();
   const int T = thresh;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kWarmTab; i += gridDim.x * blockDim.x) {
-    if (cnt[i] < T) continue;
+    const int c = cnt[i];
+    if (c < T) continue;
     const int32_t k = key[i];
-    if (k > 0) atomicCAS(warm + warm_slot(k - 1), 0, k);
+    if (k > 0) atomicMax(warm + warm_slot(k - 1), warm_entry(static_cast<uint32_t>(c), k - 1));
   }
 }
 
@@ -589,7 +598,7 @@ __global__ void warm_select(const int32_t *hot, const int32_t *key, const int32_
 // column or in no order): hot, warm and the search scratch (key, cnt) are
 // in the plan.
 static msrep_status find_frequent_rows(const int32_t *row_idx, int64_t nnz, int32_t *hot,
-                                       int32_t *warm, int32_t *key, int32_t *cnt,
+                                       unsigned long long *warm, int32_t *key, int32_t *cnt,
                                        cudaStream_t st) {
   MSREP_TRY(hot_rows_smem_opt_in());
   hot_rows<<<1, 1024, kHotSmem, st>>>(row_idx, nnz, hot);
@@ -777,7 +786,7 @@ static msrep_status partition_compressed(const msrep_matrix *A,
     if (A->fmt == MSREP_CSC) {
       int32_t *wtab = reinterpret_cast<int32_t *>(plan + L.off_wtab);
       MSREP_TRY(find_frequent_rows(A->idx, A->nnz, reinterpret_cast<int32_t *>(plan + L.off_hot),
-                                   reinterpret_cast<int32_t *>(plan + L.off_warm), wtab,
+                                   reinterpret_cast<unsigned long long *>(plan + L.off_warm), wtab,
                                    wtab + kWarmTab, st));
     }
   }
@@ -881,7 +890,7 @@ msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
     char *plan = static_cast<char *>(p->plan);
     int32_t *wtab = reinterpret_cast<int32_t *>(plan + kScatterTabOff);
     MSREP_TRY(find_frequent_rows(A->idx2, A->nnz, reinterpret_cast<int32_t *>(plan),
-                                 reinterpret_cast<int32_t *>(plan + kScatterWarmOff), wtab,
+                                 reinterpret_cast<unsigned long long *>(plan + kScatterWarmOff), wtab,
                                  wtab + kWarmTab, st));
   }
   return ok();

@@ -471,7 +471,7 @@ struct ScatterArgs {
   double scale;   // alpha on the FP64 path, 1 when a finishing pass follows
   bool scaled;
   const int32_t *hot;   // hub rows, or null
-  const int32_t *warm;  // frequent-row table (kWarm entries)
+  const unsigned long long *warm;  // frequent-row table (kWarm entries)
   int64_t nnz;
 };
 
@@ -798,7 +798,7 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   a.err = kernel_err_ptr();
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   a.hot = reinterpret_cast<const int32_t *>(plan + L.off_hot);
-  a.warm = reinterpret_cast<const int32_t *>(plan + L.off_warm);
+  a.warm = reinterpret_cast<const unsigned long long *>(plan + L.off_warm);
   const int64_t m = A->m;
   const int sg = 4 * sm_count();
   const int64_t pn = w.perm ? perm_extent(m) : 0;
@@ -853,7 +853,8 @@ static msrep_status run_coo_scatter(const msrep_matrix *A, const msrep_partition
   a.val = static_cast<const typename Pol::V *>(A->val);
   a.x = static_cast<const typename Pol::X *>(x);
   a.hot = static_cast<const int32_t *>(p->plan);
-  a.warm = reinterpret_cast<const int32_t *>(static_cast<const char *>(p->plan) + kScatterWarmOff);
+  a.warm = reinterpret_cast<const unsigned long long *>(static_cast<const char *>(p->plan) +
+                                                        kScatterWarmOff);
   a.nnz = A->nnz;
   const int64_t m = A->m;
   const int sg = 4 * sm_count();

@@ -573,7 +573,7 @@ struct CscArgs {
   bool scaled;   // scale != 1
   const int32_t *tile_row, *tile_k;
   const int32_t *hot;   // hub rows: count, then kMaxHot rows (-1 = none)
-  const int32_t *warm;  // frequent-row table, kWarm entries (row + 1, 0 = empty)
+  const unsigned long long *warm;  // frequent-row table, kWarm entries
   int32_t n;
   int *err;
 };
@@ -636,12 +636,15 @@ struct HotRows {
 struct WarmRows {
   int32_t *tag;  // kWarm row tags, row + 1 (0 = empty), shared memory
   double *acc;   // kWarm sums, shared memory
-  // every thread of the block
-  __device__ __forceinline__ void load(const int32_t *warm, int32_t *s_tag, double *s_acc) {
+  // every thread of the block; warm: the plan's table, (priority << 32) |
+  // ~row per slot, 0 = empty
+  __device__ __forceinline__ void load(const unsigned long long *warm, int32_t *s_tag,
+                                       double *s_acc) {
     tag = s_tag;
     acc = s_acc;
     for (int i = threadIdx.x; i < kWarm; i += blockDim.x) {
-      s_tag[i] = __ldg(warm + i);
+      const unsigned long long e = __ldg(warm + i);
+      s_tag[i] = e ? static_cast<int32_t>(~static_cast<uint32_t>(e)) + 1 : 0;
       s_acc[i] = 0.0;
     }
     __syncthreads();
