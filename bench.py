@@ -149,10 +149,20 @@ STAMP_SOURCES = ("csrc/common.cuh", "csrc/tma.cuh", "csrc/spmv_core.cuh", "csrc/
                  "csrc/partition.cu")
 
 
+def code_of(text: str) -> str:
+    """C/C++/CUDA source without its comments and blank lines (the sources
+    hashed by source_stamp hold no comment markers inside string literals),
+    so that a change to comments alone leaves the stamp as it is."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def source_stamp() -> str:
-    """Hash of the sources of the single-matrix SpMV kernels (and their tile
-    plans), the public header and the code-generation flags of libmsrep.so,
-    independent of where the repository lives."""
+    """Hash of the code (comments stripped) of the single-matrix SpMV kernels
+    and their tile plans, the public header and the code-generation flags of
+    libmsrep.so, independent of where the repository lives."""
     import hashlib
     from paper_2209_07552_gb300 import build as B
     h = hashlib.sha1(" ".join(B.ARCH + [f for f in B.NVCC_FLAGS if not f.startswith("-I")]).encode())
@@ -160,8 +170,8 @@ def source_stamp() -> str:
     paths.append(os.path.join(B.INCLUDE, "msrep.h"))
     for path in paths:
         h.update(os.path.basename(path).encode())
-        with open(path, "rb") as f:
-            h.update(f.read())
+        with open(path, encoding="utf-8") as f:
+            h.update(code_of(f.read()).encode())
     return h.hexdigest()
 
 

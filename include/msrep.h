@@ -106,9 +106,9 @@ typedef struct {
  *                             local column index col_idx[k] - start_major;
  *                             COO_UNSORTED: row_idx[k] itself).
  *   plan       (opt.)         opaque plan used by msrep_spmv for CSR, CSC
- *                             (tiles, hub rows), COO_BY_COL and
- *                             COO_UNSORTED (hub rows); plan_bytes >=
- *                             msrep_plan_size().
+ *                             (tiles, hub and frequent rows), COO_BY_COL
+ *                             and COO_UNSORTED (hub and frequent rows);
+ *                             plan_bytes >= msrep_plan_size().
  *   tile                      nonzeros+rows per thread-block tile of the
  *                             plan, 0 = library default; must be a
  *                             supported size (msrep_tile_supported()).
@@ -173,11 +173,15 @@ msrep_status msrep_partition_csr(const msrep_matrix *A, msrep_partition *part,
 
 /* CSC -> pCSC, Alg. 4 (Sec. 3.2.2): Alg. 2 over col_ptr.  With a plan, it
  * also records up to four hub rows (rows holding about 0.1% or more of the
- * nonzeros, found from 4096 evenly spaced samples of row_idx): msrep_spmv
- * sums their products privately per thread block instead of with one
- * atomic add per nonzero on the same y entry.  The result is the same up
- * to the order of FP64 additions, which CSC's atomic scatter leaves open
- * anyway. */
+ * nonzeros, found from 4096 evenly spaced samples of row_idx) and, when
+ * there are hub rows, a table of up to 2048 frequent rows (counted from
+ * 65536 evenly spaced samples; a row claims a slot of a direct-mapped
+ * table, and the most frequent claimant keeps it).  msrep_spmv sums the
+ * products of those rows per thread block in shared memory and adds each
+ * sum once, instead of one atomic add per nonzero.  The result is the same
+ * up to the order of FP64 additions, which CSC's atomic scatter leaves
+ * open anyway.  The plan (msrep_plan_size) also holds the 1 MB scratch of
+ * that search. */
 msrep_status msrep_partition_csc(const msrep_matrix *A, msrep_partition *part,
                                  unsigned flags, void *stream);
 
@@ -193,7 +197,8 @@ msrep_status msrep_partition_csc(const msrep_matrix *A, msrep_partition *part,
  *     end_major = m-1 (Sec. 3.2.3: a partition of unsorted COO may reach
  *     any row), start_flag = 0.
  * For COO_BY_COL and COO_UNSORTED a plan (msrep_plan_size bytes) receives
- * the hub rows, found as for msrep_partition_csc.  Validation checks the
+ * the hub rows and the frequent-row table, found as for
+ * msrep_partition_csc.  Validation checks the
  * indices' range and, for the two sorted orders, the order.
  * MSREP_PART_MERGE_PATH is INVALID_ARG here. */
 msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *part,

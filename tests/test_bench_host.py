@@ -48,3 +48,11 @@ def test_partition_overhead_share():
     assert abs(out["pct"] - 25.0) < 1e-12
     assert abs(out["pct_with_local"] - 50.0) < 1e-12
     assert out["spmv_ms"] == 3.0
+
+
+def test_stamp_ignores_comments_only():
+    a = "int f(int x) {  // doubles x\n  return 2 * x; /* no overflow check */\n}\n"
+    b = "/* a comment block\n   over lines */\nint f(int x) {\n  return 2 * x;\n}\n"
+    c = "int f(int x) {\n  return 3 * x;\n}\n"
+    assert bench.code_of(a) == bench.code_of(b)
+    assert bench.code_of(a) != bench.code_of(c)
