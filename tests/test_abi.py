@@ -74,3 +74,28 @@ def test_spmm_workspace_size_host_checks(so):
     A.c.fmt = N.MSREP_CSC
     with pytest.raises(N.MsrepError):
         N.msrep_spmm_workspace_size(A, P, 2)
+
+
+def test_plan_sizes_per_format(so):
+    """CSC plans also hold the frequent-row table and its 1 MB search
+    scratch; row-sorted COO needs no plan; column-sorted and unsorted COO
+    need a fixed-size one (hub rows, frequent-row table, scratch)."""
+    from paper_2209_07552_gb300 import native as N
+    N.lib(so._name)
+    A = N.DeviceMatrix.__new__(N.DeviceMatrix)
+    A.c = N.c_msrep_matrix(N.MSREP_CSR, N.MSREP_F64, 1000, 1000, 5000, 1, 1, None, 1)
+    csr = N.msrep_plan_size(A, 10, 0)
+    A.c.fmt = N.MSREP_CSC
+    csc = N.msrep_plan_size(A, 10, 0)
+    assert csc - csr >= (1 << 20)
+    A.c.fmt = N.MSREP_COO
+    A.c.ptr = None
+    A.c.idx2 = 1
+    assert N.msrep_plan_size(A, 10, 0) == 0
+    sizes = set()
+    for fmt in (N.MSREP_COO_BY_COL, N.MSREP_COO_UNSORTED):
+        A.c.fmt = fmt
+        for np_, nnz in ((10, 5000), (4096, 1 << 24)):
+            A.c.nnz = nnz
+            sizes.add(N.msrep_plan_size(A, np_, 0))
+    assert len(sizes) == 1 and sizes.pop() >= (1 << 20)
