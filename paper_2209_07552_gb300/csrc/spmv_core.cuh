@@ -579,12 +579,14 @@ struct CscArgs {
 };
 
 // A skewed CSC matrix (hub rows found and a permuted accumulator given)
-// takes the hub-row sums and the permuted scatter.
+// takes the frequent-row sums (WarmRows; the bulk-copy streaming kernel
+// keeps the hub-row sums of HotRows) and the permuted scatter.
 __device__ __forceinline__ bool csc_skewed(const int32_t *hot, const double *yperm) {
   return yperm != nullptr && __ldg(hot) > 0;
 }
 
-// Private sums of the hub rows of a CSC matrix.  Every nonzero of a hub row
+// Private sums of the hub rows of a CSC matrix (the bulk-copy streaming
+// kernel; the direct kernels use WarmRows, below).  Every nonzero of a hub row
 // is an atomic add to the same y entry, and same-address atomics serialise
 // in L2 (about 40,000 of them on one row of the R-MAT workload cost some
 // 100 us).  A warp adds its products for the hub rows to its own slots in
