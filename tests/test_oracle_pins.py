@@ -59,6 +59,36 @@ def test_hand_example_pcsc_pcoo():
     assert q["local"].tolist() == e["local_row_idx"]
 
 
+def test_hand_example_merge_path_and_other_coo_orders():
+    g = _hand()
+    p = O.partition_merge_path(g["csr"]["row_ptr"], 9, g["np"], with_local=True)
+    e = g["pcsr_merge_path"]
+    assert p["cut_row"].tolist() == e["cut_row"]
+    assert p["start_idx"].tolist() == e["start_idx"]
+    assert p["end_idx"].tolist() == e["end_idx"]
+    assert p["start_major"].tolist() == e["start_row"]
+    assert p["end_major"].tolist() == e["end_row"]
+    assert p["start_flag"].tolist() == e["start_flag"]
+    assert p["local"].tolist() == [v for part in e["local_row_ptr"] for v in part]
+    x, yin, a, b = g["x"], g["y_in"], g["alpha"], g["beta"]
+    assert O.pspmv_csr(6, g["csr"]["row_ptr"], g["csr"]["col_idx"], g["csr"]["val"], p,
+                       x, a, b, yin).tolist() == g["y"]
+    e = g["pcoo_by_col"]
+    q = O.partition_coo_by_col(e["col_idx"], g["np"], with_local=True)
+    assert q["start_major"].tolist() == e["start_col"]
+    assert q["end_major"].tolist() == e["end_col"]
+    assert q["start_flag"].tolist() == e["start_flag"]
+    assert q["local"].tolist() == e["local_col_idx"]
+    assert O.pspmv_coo_scatter(6, e["row_idx"], e["col_idx"], g["csc"]["val"], q, x, a, b,
+                               yin).tolist() == g["y"]
+    e = g["pcoo_unsorted"]
+    u = O.partition_coo_unsorted(g["coo"]["row_idx"], 6, g["np"])
+    for key, name in (("start_idx", "start_idx"), ("end_idx", "end_idx"),
+                      ("start_major", "start_row"), ("end_major", "end_row"),
+                      ("start_flag", "start_flag")):
+        assert u[key].tolist() == e[name]
+
+
 def test_hand_example_spmv_all_formats():
     g = _hand()
     x, yin = g["x"], g["y_in"]
