@@ -99,3 +99,37 @@ def test_plan_sizes_per_format(so):
             A.c.nnz = nnz
             sizes.add(N.msrep_plan_size(A, np_, 0))
     assert len(sizes) == 1 and sizes.pop() >= (1 << 20)
+
+
+def test_partition_argument_errors_before_any_device_work(so):
+    """Errors the partitioners report from their arguments alone, before
+    touching the device: the merge-path flag on COO, and plans smaller than
+    msrep_plan_size (CSC: it holds the frequent-row table; COO sorted by
+    column: its fixed-size plan).  The pointers are never dereferenced."""
+    import ctypes
+
+    from paper_2209_07552_gb300 import native as N
+    N.lib(so._name)
+    fake = ctypes.c_void_p(256)
+
+    def part(plan_bytes):
+        p = N.c_msrep_partition()
+        p.np = 4
+        p.start_idx = p.end_idx = p.start_major = p.end_major = p.start_flag = fake
+        p.plan = fake if plan_bytes else None
+        p.plan_bytes = plan_bytes
+        return p
+
+    A = N.c_msrep_matrix(N.MSREP_COO, N.MSREP_F64, 100, 100, 500, None, 256, 256, 256)
+    rc = N.lib().msrep_partition_coo(ctypes.byref(A), ctypes.byref(part(0)),
+                                     N.MSREP_PART_MERGE_PATH, None)
+    assert rc == 1
+    A.fmt = N.MSREP_COO_BY_COL
+    rc = N.lib().msrep_partition_coo(ctypes.byref(A), ctypes.byref(part(1024)), 0, None)
+    assert rc == 9                                       # plan too small
+    C = N.c_msrep_matrix(N.MSREP_CSC, N.MSREP_F64, 100, 100, 500, 256, 256, None, 256)
+    M = N.DeviceMatrix.__new__(N.DeviceMatrix)
+    M.c = C
+    need = N.msrep_plan_size(M, 4, 0)
+    rc = N.lib().msrep_partition_csc(ctypes.byref(C), ctypes.byref(part(need - 256)), 0, None)
+    assert rc == 9
