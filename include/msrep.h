@@ -445,16 +445,23 @@ msrep_status msrep_serve_destroy(msrep_server *s);
  * a cudaMalloc is not acceptable.  Instead of a caller workspace it uses
  * one scratch array compiled into the library (MSREP_NOALLOC_SCRATCH_BYTES,
  * a static device array), so this call allocates nothing.
- *  - The first call on a device looks up the array's device address with
- *    cudaGetSymbolAddress (with that device current) and caches it; make
- *    that first call before any stream capture.
- *  - Problems whose workspace exceeds the array are rejected with
- *    MSREP_ERR_WORKSPACE and nothing is queued; for CSR and COO that is
- *    about 65,000 tiles (e.g. m + nnz up to about 32 million at the default
- *    tile of 512); CSC with FP32/BF16 values also needs m doubles.  A CSC
- *    SpMV whose permuted accumulator does not fit scatters into y directly
- *    (same result up to the order of additions, slower on matrices with hub
- *    rows). 
+ *  - Every call made outside a stream capture looks up the array's device
+ *    address with cudaGetSymbolAddress (for the current device), so a
+ *    context destroyed and recreated in between (cudaDeviceReset) is
+ *    handled.  A call inside a capture reuses the address of the device's
+ *    last uncaptured call: make one call on each device before capturing.
+ *  - The scratch must hold what msrep_spmv_workspace_size reports, minus
+ *    the permuted accumulator when that does not fit (below); problems that
+ *    need more are rejected with MSREP_ERR_WORKSPACE and nothing is queued.
+ *    Two FP64 partials per tile: CSR about (m + nnz)/tile + np tiles, CSC
+ *    (n + nnz)/tile + np, row-sorted COO np * ceil(ceil(nnz/np)/tile), so
+ *    about 65,000 tiles in all (e.g. m + nnz up to about 32 million for CSR
+ *    at the default tile of 512); CSC, COO_BY_COL and COO_UNSORTED with
+ *    FP32/BF16 values also need m doubles for their FP64 accumulator.
+ *  - A CSC or scatter-COO SpMV whose permuted accumulator (2^k >= m
+ *    doubles) does not fit scatters into y (or into the row-ordered
+ *    accumulator) directly: the same result up to the order of the FP64
+ *    additions, slower on matrices with hub rows.
  *  - Every call shares the one array and leaves its contents behind: two
  *    calls whose work overlaps on the GPU (different streams, or several
  *    host threads) race on it and give wrong results; serialise them.
@@ -470,6 +477,19 @@ msrep_status msrep_spmv_noalloc(const msrep_matrix *A, const msrep_partition *pa
  * expires (which means the copy engine stalled or an argument was wrong).
  * *status = 0 and MSREP_OK when no kernel failed, else MSREP_ERR_TIMEOUT. */
 msrep_status msrep_device_status(void *stream, int *status);
+
+/* Self-test of the bounded device wait (no counterpart in the paper; the
+ * failure-detection check of the streaming kernels' waits).  Launches one
+ * kernel whose thread initialises an mbarrier expecting two arrivals,
+ * arrives once and issues no copy, so the barrier can never complete; its
+ * bounded wait gives up after max_cycles SM clock cycles (1 ..
+ * 2,000,000,000, the limit the streaming kernels use), writes 1 to
+ * *gave_up (a device int32; 0 if the wait had completed) and records the
+ * timeout in the device error word, exactly as a stalled bulk copy would,
+ * so that the next msrep_device_status reports MSREP_ERR_TIMEOUT.  Nothing
+ * faults or hangs: the kernel returns either way.  Asynchronous on
+ * `stream`.  Errors: INVALID_ARG, CUDA. */
+msrep_status msrep_wait_selftest(int64_t max_cycles, int32_t *gave_up, void *stream);
 
 /* Measurement aid (no counterpart in the paper): the access-pattern floor
  * of an SpMV.  One kernel that streams idx (and, mode 1, idx2) and val once

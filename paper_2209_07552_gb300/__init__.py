@@ -7,7 +7,7 @@ of that ABI; ``inputs`` synthesises seeded test and benchmark matrices.
 """
 from .native import (MSREP_BF16, MSREP_COMP_ALL, MSREP_COMP_NONE, MSREP_COO,
                      MSREP_COO_BY_COL, MSREP_COO_UNSORTED,
-                     MSREP_STREAM_TMA, msrep_device_status,
+                     MSREP_STREAM_TMA, msrep_device_status, msrep_wait_selftest,
                      MSREP_CSC, MSREP_CSR, MSREP_F32, MSREP_F64, MSREP_VALIDATE,
                      MSREP_PART_MERGE_PATH,
                      DeviceMatrix, DevicePartition, MsrepError, alloc_workspace,

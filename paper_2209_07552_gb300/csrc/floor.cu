@@ -10,6 +10,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace msrep {
 
@@ -62,9 +63,40 @@ __global__ void __launch_bounds__(256) access_floor(const int32_t *__restrict__ 
   if (MODE <= 1 && (acc == 1.2345e-300 || other == 0x7fffabcd)) sink[0] = acc;
 }
 
+// Self-test of the bounded device wait (msrep_wait_selftest): one thread
+// initialises an mbarrier that expects two arrivals, arrives once and issues
+// no copy, so the barrier's phase can never complete; the bounded wait must
+// give up after `max_cycles`, record kErrWaitTimeout in the device error
+// word and return.  Nothing else is in flight, so the kernel ends either way.
+__global__ void wait_selftest(int *err, long long max_cycles, int *gave_up) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 2);
+  fence_mbar_init();
+  asm volatile(
+      "{\n\t.reg .b64 st;\n\t"
+      "mbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(&bar))
+      : "memory");
+  *gave_up = mbar_wait(&bar, 0, err, max_cycles) ? 0 : 1;
+}
+
+int *kernel_err_ptr();
+
 }  // namespace msrep
 
 using namespace msrep;
+
+extern "C" msrep_status msrep_wait_selftest(int64_t max_cycles, int32_t *gave_up,
+                                            void *stream) {
+  if (max_cycles < 1 || max_cycles > kWaitCycles || !gave_up)
+    return fail(MSREP_ERR_INVALID_ARG, "max_cycles must be in 1..%lld and gave_up non-NULL",
+                (long long)kWaitCycles);
+  int *err = kernel_err_ptr();
+  if (!err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
+  wait_selftest<<<1, 32, 0, as_stream(stream)>>>(err, max_cycles, gave_up);
+  MSREP_CUDA_TRY(cudaGetLastError());
+  return ok();
+}
 
 extern "C" msrep_status msrep_access_floor(int32_t mode, const int32_t *idx, const int32_t *idx2,
                                            const double *val, double *vec, int64_t nnz,

@@ -58,12 +58,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
 }
 
 // Bounded wait for phase `parity` of `bar`.  Returns false (and records the
-// failure in *err) if the phase did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
+// failure in *err) if the phase did not complete within kWaitPolls polls or
+// `max_cycles` SM clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
+                                          long long max_cycles = kWaitCycles) {
   const long long t0 = clock64();
   for (uint32_t i = 0; i < kWaitPolls; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (clock64() - t0 > kWaitCycles) break;
+    if (clock64() - t0 > max_cycles) break;
   }
   atomicOr(err, kErrWaitTimeout);
   return false;

@@ -118,6 +118,7 @@ SIGNATURES = {
     "msrep_spmv_noalloc": (ctypes.c_int, [_M, _P, ctypes.c_double, _vp, ctypes.c_double,
                                           _vp, ctypes.c_int32, ctypes.c_uint, _vp]),
     "msrep_device_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "msrep_wait_selftest": (ctypes.c_int, [ctypes.c_int64, _vp, _vp]),
     "msrep_tune_default": (ctypes.c_int, [ctypes.POINTER(c_msrep_tune_table)]),
     "msrep_batch_plan_size": (ctypes.c_int, [ctypes.c_int32, _M,
                                              ctypes.POINTER(c_msrep_tune_table),
@@ -442,6 +443,12 @@ def msrep_device_status(stream=None) -> int:
     st = ctypes.c_int()
     _check(lib().msrep_device_status(_stream(stream), ctypes.byref(st)))
     return st.value
+
+
+def msrep_wait_selftest(max_cycles: int, gave_up, stream=None):
+    """Queue the bounded-wait self-test kernel; gave_up: a device int32
+    tensor of one element (1 after the wait gave up)."""
+    _check(lib().msrep_wait_selftest(int(max_cycles), _ptr(gave_up), _stream(stream)))
 
 
 # --------------------------------------------------------------------------

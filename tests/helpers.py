@@ -76,3 +76,19 @@ def gpu_spmv(a: I.CSR, fmt: str, P: int, x, alpha=1.0, beta=0.0, y0=None,
         outs.append(yy.cpu().numpy().astype(np.float64))
     torch.cuda.synchronize()
     return outs[0] if repeat == 1 else outs
+
+
+U32 = 2.0 ** -24
+
+
+def f32_row_bound(a_stored: I.CSR, x, yref):
+    """Element-wise error bound of a binary32 SpMV row against the FP64
+    product of the stored values and x: recursive summation of L_r products
+    (Higham, "Accuracy and Stability of Numerical Algorithms", Sec. 3.1)
+    gives |y_r - yref_r| <= (L_r + 2) u (|A| |x|)_r + u |yref_r|, u = 2^-24;
+    compensated rows are well inside it."""
+    absa = I.CSR(a_stored.m, a_stored.n, a_stored.row_ptr, a_stored.col_idx,
+                 np.abs(a_stored.val))
+    ax = O.spmv_csr(absa.m, absa.row_ptr, absa.col_idx, absa.val, np.abs(x))
+    L = np.diff(a_stored.row_ptr.astype(np.int64)).astype(np.float64)
+    return (L + 2) * U32 * ax + U32 * np.abs(yref)

@@ -9,7 +9,8 @@ import threading
 import numpy as np
 import pytest
 
-from helpers import normwise, oracle_spmv
+import oracle as O
+from helpers import f32_row_bound, normwise, oracle_spmv
 from paper_2209_07552_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -40,17 +41,27 @@ def _solo(M, a, X):
     return np.stack(ys)
 
 
+def _stored(a):
+    return I.CSR(a.m, a.n, a.row_ptr, a.col_idx, a.val.astype(np.float32).astype(np.float64))
+
+
 def test_serve_results_alone_and_in_the_mix():
+    """Every one of the 8 columns a request can carry: alone (one request
+    of 8 vectors, the batched k-vector kernel) it equals msrep_spmv of that
+    column bit for bit and the FP64 oracle on the stored values within the
+    binary32 bound; in the mix (requests of 1..8 vectors for all matrices,
+    from several threads, so launches hold both batched kernels) each of its
+    k columns equals the alone result bit for bit."""
     import paper_2209_07552_gb300 as M
     mats = _mats()
     with M.Server(budget_bytes=4 << 30, arena_bytes=16 << 20, contexts=3) as S:
         ids = [S.register(a) for a in mats]
         rng = I.rng(9, 9)
         X = [rng.uniform(-1, 1, (8, a.n)).astype(np.float32) for a in mats]
-        # alone: one request at a time
+        # alone: one request at a time, all eight vectors
         alone = []
         for mid, x in zip(ids, X):
-            alone.append(S.wait(S.submit(mid, x[:3])).copy())
+            alone.append(S.wait(S.submit(mid, x)).copy())
         # in the mix: many requests of every matrix from several threads
         tickets, lock = [], threading.Lock()
 
@@ -68,17 +79,58 @@ def test_serve_results_alone_and_in_the_mix():
             t.start()
         for t in th:
             t.join()
+        ks = set()
         for j, k, t in tickets:
             y = S.wait(t, 60_000_000)
-            assert np.array_equal(y[: min(k, 3)], alone[j][: min(k, 3)])
+            assert y.shape[0] == k
+            assert np.array_equal(y, alone[j][:k]), (j, k)
+            ks.add(k)
+        assert ks == set(range(1, 9))
         st = S.stats()
         assert st["completed"] >= len(tickets) + len(ids)
         assert st["launches"] >= 1 and st["p99_us"] >= st["p50_us"] > 0
     for a, x, y in zip(mats, X, alone):
-        assert np.array_equal(y, _solo(M, a, x[:3]))
-        st = I.CSR(a.m, a.n, a.row_ptr, a.col_idx, a.val.astype(np.float64))
-        for v in range(3):
-            assert normwise(y[v], oracle_spmv(st, "csr", x[v].astype(np.float64))) <= 1e-6
+        assert y.shape == (8, a.m)
+        assert np.array_equal(y, _solo(M, a, x))
+        st = _stored(a)
+        want = O.spmm_csr(a.m, a.row_ptr, a.col_idx, st.val, x.astype(np.float64).T)
+        for v in range(8):
+            assert normwise(y[v], want[:, v]) <= 1e-6, v
+            assert np.all(np.abs(y[v] - want[:, v]) <= f32_row_bound(st, x[v], want[:, v])), v
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5, 8])
+def test_serve_k_vector_kernel_columns(k):
+    """The server's batched k-vector kernel (and its interleaving of X) on
+    uneven matrices in one launch: requests of k vectors for every matrix
+    are queued while the server is held busy, so they share launches.
+    Every column is checked element-wise against the oracle's k-vector
+    product on the stored values (binary32 bound) and bit for bit against
+    msrep_spmv of that column."""
+    import paper_2209_07552_gb300 as M
+    mats = _mats(seed=7)
+    with M.Server(budget_bytes=4 << 30, arena_bytes=32 << 20, contexts=1) as S:
+        ids = [S.register(a) for a in mats]
+        g = I.rng(31, k)
+        X = [g.uniform(-1, 1, (k, a.n)).astype(np.float32) for a in mats]
+        # a large request first keeps the single context busy while the
+        # others queue, so they are packed into one launch
+        big = I.rmat(scale=16, nnz=1_500_000, seed=33)
+        bid = S.register(big)
+        hold = S.submit(bid, np.ones((8, big.n), np.float32))
+        tickets = [S.submit(mid, x) for mid, x in zip(ids, X)]
+        S.wait(hold)
+        ys = [S.wait(t) for t in tickets]
+        st = S.stats()
+        assert st["launches"] <= 2 + len(ids)
+    for a, x, y in zip(mats, X, ys):
+        assert y.shape == (k, a.m)
+        s = _stored(a)
+        want = O.spmm_csr(a.m, a.row_ptr, a.col_idx, s.val, x.astype(np.float64).T)
+        solo = _solo(M, a, x)
+        for v in range(k):
+            assert np.all(np.abs(y[v] - want[:, v]) <= f32_row_bound(s, x[v], want[:, v])), v
+            assert np.array_equal(y[v], solo[v]), v
 
 
 def test_serve_budget_admission_and_unregister():

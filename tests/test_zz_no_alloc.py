@@ -84,3 +84,35 @@ def test_noalloc_csc_with_and_without_the_permuted_accumulator(scale, fmt):
         torch.cuda.synchronize()
         assert np.array_equal(y_ref.cpu().numpy(), want), call
         assert np.array_equal(y.cpu().numpy(), want), call
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+@pytest.mark.parametrize("fmt", ["csc", "coo_col"])
+def test_noalloc_low_precision_scatter_row_ordered_accumulator(fmt, dt):
+    """Low-precision CSC and column-sorted COO at 100,000 rows: the permuted
+    accumulator (2^17 doubles, 1 MiB) does not fit in the scratch array but
+    m doubles do, so the call accumulates in FP64 in row order in the
+    scratch and rounds to FP32 once.  Checked against msrep_spmv and against
+    the FP64 oracle on the original values (1e-5 FP32, 1e-2 BF16 values),
+    on two calls in a row."""
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    from helpers import oracle_spmv
+    tol = {"f32": 1e-5, "bf16": 1e-2}[dt]
+    a = I.geometric_matrix(100_000, 8.0, 66, np.float64)
+    A = M.DeviceMatrix.from_host(a, fmt, dt)
+    part = M.DevicePartition(A, 148)
+    M.msrep_partition(A, part)
+    ws = M.alloc_workspace(A, part)
+    for call in range(2):
+        x64 = I.vector(a.n, 67 + call)
+        x = torch.from_numpy(I.to_f32(x64)).cuda()
+        y_ref = torch.empty(a.m, dtype=torch.float32, device="cuda")
+        M.msrep_spmv(A, part, 1.0, x, 0.0, y_ref, workspace=ws)
+        y = torch.full((a.m,), float("nan"), dtype=torch.float32, device="cuda")
+        M.native.msrep_spmv_noalloc(A, part, 1.0, x, 0.0, y)
+        torch.cuda.synchronize()
+        yh = y.cpu().numpy().astype(np.float64)
+        assert normwise(yh, y_ref.cpu().numpy().astype(np.float64)) <= 1e-6, call
+        assert normwise(yh, oracle_spmv(a, "csr", x64)) <= tol, call
