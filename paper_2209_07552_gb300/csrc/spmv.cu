@@ -311,47 +311,90 @@ __global__ void __launch_bounds__(kThreads) coo_stream(CooArgs<Pol> a) {
     for (int j = i + 1; j < i + S && first + j * W < T; ++j) mbar_wait(bar + j % S, (j / S) & 1, a.err);
 }
 
+// Longest column for which a CSC tile of a matrix without hub rows takes
+// the interleaved walk (csc_tile_interleaved); tiles with longer columns
+// split their nonzeros evenly over the lanes (csc_tile_compute).
+constexpr int kColumnWalkMax = 32;
+
+// Dynamic shared memory of csc_direct: per warp the tile's column pointers,
+// then one region that holds either the frequent-row table (matrices with
+// hub rows) or, per warp, the column of each of the tile's nonzeros (int16,
+// for the interleaved walk of the others).
+template <int IPT>
+struct CscSmem {
+  static constexpr int CAP = 32 * IPT + 8;
+  static constexpr size_t CP = size_t(kWarps) * CAP * sizeof(int32_t);
+  static constexpr size_t COL = size_t(kWarps) * CAP * sizeof(int16_t);
+  static constexpr size_t WARM = size_t(kWarm) * (sizeof(int32_t) + sizeof(double));
+  static constexpr size_t BYTES = CP + (COL > WARM ? COL : WARM);
+};
+
 template <class Pol, int IPT>
-// Four resident blocks (64 registers a thread); the column-pointer stages
-// and the frequent-row table fit four blocks' shared memory.
+// Four resident blocks (64 registers a thread); the column-pointer stages,
+// the column tables and the frequent-row table fit four blocks' shared
+// memory.
 __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const int32_t *n_tiles,
                                                        int64_t nnz) {
+  using SM = CscSmem<IPT>;
   grid_dependency_wait();
-  // dynamic shared memory: per warp, the tile's column pointers
   extern __shared__ __align__(16) unsigned char dsm[];
-  constexpr int CAP = 32 * IPT + 8;
   const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int32_t *s_cp = reinterpret_cast<int32_t *>(dsm) + wid * CAP;
-  __shared__ int32_t s_wtag[kWarm];
-  __shared__ double s_wacc[kWarm];
+  int32_t *s_cp = reinterpret_cast<int32_t *>(dsm) + wid * SM::CAP;
+  int16_t *s_col = reinterpret_cast<int16_t *>(dsm + SM::CP) + wid * SM::CAP;
+  int32_t *s_wtag = reinterpret_cast<int32_t *>(dsm + SM::CP);
+  double *s_wacc = reinterpret_cast<double *>(dsm + SM::CP + sizeof(int32_t) * kWarm);
   const bool skew = csc_skewed(a.hot, a.yperm);
-  WarmRows warm;
-  if (skew) warm.load(a.warm, s_wtag, s_wacc);
-  auto tiles = [&](auto with_hot) {
-    for (int b = blockIdx.x * kWarps + wid; b < T; b += gridDim.x * kWarps) {
-      const int32_t c0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
-      const int32_t c1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
-      const int32_t cend = min(c1 + 1, a.n + 1);
-      for (int32_t c = c0 + lane; c < cend; c += 32) s_cp[c - c0] = __ldg(a.col_ptr + c);
-      __syncwarp();
-      // scale * x of tile column c, read when a lane reaches the column
-      const auto xat = [&a, c0](int c) {
-        const int32_t g = c0 + c;
-        if (g >= a.n) return 0.0;
-        const double xv = double(load_x(a.x, g));
-        return a.scaled ? __dmul_rn(xv, a.scale) : xv;
-      };
-      csc_tile_compute<Pol, decltype(with_hot)::value>(
-          a, c0, k0, c1, k1, s_cp, xat, Seg<int32_t>{a.row_idx, 0},
-          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{}, warm);
-      __syncwarp();
-    }
+  // The next tile's coordinates and first 64 column pointers are loaded
+  // while the current tile is processed (as in csr_direct).
+  const int stride = gridDim.x * kWarps;
+  int32_t n0 = 0, nk0 = 0, n1 = 0, nk1 = 0, p0 = 0, p1 = 0;
+  auto fetch = [&](int t) {
+    n0 = __ldg(a.tile_row + t);
+    nk0 = __ldg(a.tile_k + t);
+    n1 = __ldg(a.tile_row + t + 1);
+    nk1 = __ldg(a.tile_k + t + 1);
+    const int32_t cend = min(n1 + 1, a.n + 1);
+    p0 = n0 + lane < cend ? __ldg(a.col_ptr + n0 + lane) : 0;
+    p1 = n0 + 32 + lane < cend ? __ldg(a.col_ptr + n0 + 32 + lane) : 0;
+  };
+  // one tile (its coordinates fetched): stage its column pointers, fetch
+  // the next tile's, then scatter its products to sink
+  auto tile = [&](int b, const auto &sink, bool column_walk) {
+    const int32_t c0 = n0, k0 = nk0, c1 = n1, k1 = nk1;
+    const int32_t cend = min(c1 + 1, a.n + 1);
+    if (c0 + lane < cend) s_cp[lane] = p0;
+    if (c0 + 32 + lane < cend) s_cp[32 + lane] = p1;
+    for (int32_t c = c0 + 64 + lane; c < cend; c += 32) s_cp[c - c0] = __ldg(a.col_ptr + c);
+    __syncwarp();
+    if (b + stride < T) fetch(b + stride);
+    // scale * x of tile column c, read when a lane reaches the column
+    const auto xat = [&a, c0](int c) {
+      const int32_t g = c0 + c;
+      if (g >= a.n) return 0.0;
+      const double xv = double(load_x(a.x, g));
+      return a.scaled ? __dmul_rn(xv, a.scale) : xv;
+    };
+    if (column_walk && csc_tile_max_col(c0, k0, c1, k1, a.n, s_cp) <= kColumnWalkMax)
+      csc_tile_interleaved<Pol>(a, c0, k0, c1, k1, s_cp, sink, s_col);
+    else
+      csc_tile_compute<Pol>(a, c0, k0, c1, k1, s_cp, xat, Seg<int32_t>{a.row_idx, 0},
+                            Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{}, sink);
+    __syncwarp();
   };
   if (skew) {
-    tiles(std::true_type{});
+    // power-law rows: the frequent-row sums and the permuted accumulator
+    WarmRows warm;
+    warm.load(a.warm, s_wtag, s_wacc);
+    const SkewSink<WarmRows> sink{&warm, a.yperm, a.pmask};
+    const int first = blockIdx.x * kWarps + wid;
+    if (first < T) fetch(first);
+    for (int b = first; b < T; b += stride) tile(b, sink, false);
     warm.flush(a.yperm, a.pmask);
   } else {
-    tiles(std::false_type{});
+    const DirectSink sink{a.yacc};
+    const int first = blockIdx.x * kWarps + wid;
+    if (first < T) fetch(first);
+    for (int b = first; b < T; b += stride) tile(b, sink, true);
   }
 }
 
@@ -427,13 +470,13 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
     __syncwarp();
     const auto xat = [xs](int j) { return xs[j]; };
     if (skew)
-      csc_tile_compute<Pol, true>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xat,
-                                  Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base},
-                                  nnz, SharedSrc{}, hot);
+      csc_tile_compute<Pol>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xat,
+                            Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base}, nnz,
+                            SharedSrc{}, SkewSink<HotRows>{&hot, a.yperm, a.pmask});
     else
-      csc_tile_compute<Pol, false>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xat,
-                                   Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base},
-                                   nnz, SharedSrc{}, hot);
+      csc_tile_compute<Pol>(a, c.x, c.y, c.z, c.w, cp_s(s) + (c.x - p.base), xat,
+                            Seg<int32_t>{row_s(s), r.base}, Seg<V>{val_s(s), v.base}, nnz,
+                            SharedSrc{}, DirectSink{a.yacc});
     __syncwarp();
     if (lane == 0 && b + S * W < T) {
       fence_proxy_async();
@@ -823,8 +866,8 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   MSREP_TRY(launch_tiles(csc_stream<Pol, IPT>, csc_direct<Pol, IPT>,
                          StageGeom<typename Pol::V, IPT, 2>::BLOCK +
                              sizeof(double) * kWarps * (32 * IPT + 8),
-                         sizeof(int32_t) * kWarps * (32 * IPT + 8), 0,
-                         (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
+                         CscSmem<IPT>::BYTES, 0, (flags & MSREP_STREAM_TMA) == 0, L.tmax, st,
+                         a, n_tiles, A->nnz));
   if (kF64) {
     if (w.perm)
       MSREP_TRY(launch_dependent(csc_unpermute, sg, 256, st, 0, a.hot,

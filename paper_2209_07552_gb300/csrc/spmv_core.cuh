@@ -667,15 +667,35 @@ struct WarmRows {
   }
 };
 
+// Where a scatter's products go (Alg. 5's column merge, done in place).
+// DirectSink: one FP64 atomic add per product into the row-ordered target.
+struct DirectSink {
+  double *y;
+  __device__ __forceinline__ void add(int32_t row, double v) const { atomicAdd(y + row, v); }
+};
+
+// A skewed matrix: the hub or frequent rows' sums in shared memory (Hot is
+// HotRows or WarmRows), the other rows into the permuted accumulator.
+template <class Hot>
+struct SkewSink {
+  Hot *hot;
+  double *yperm;
+  uint32_t pmask;
+  __device__ __forceinline__ void add(int32_t row, double v) const {
+    if (!hot->take(row, v)) atomicAdd(yperm + perm_slot(row, pmask), v);
+  }
+};
+
 // cp[j] = col_ptr[c0 + j], j = 0..c1-c0, in shared memory; xat(j) = scale *
-// x[c0 + j] for the columns that hold nonzeros of the tile.  Hot is HotRows
-// or WarmRows.
-template <class Pol, bool kSkew, class Src, class Hot, class XAt>
+// x[c0 + j] for the columns that hold nonzeros of the tile.  Every product
+// goes to sink.add(row, product).  The lanes split the tile's nonzeros
+// evenly, so long columns spread over the warp.
+template <class Pol, class Src, class Sink, class XAt>
 __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t c0, int32_t k0,
                                                  int32_t c1, int32_t k1, const int32_t *cp,
                                                  XAt xat, Seg<int32_t> row,
                                                  Seg<typename Pol::V> val, int64_t nnz, Src src,
-                                                 Hot &hot) {
+                                                 const Sink &sink) {
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
   const int ncols = c1 - c0;
@@ -706,12 +726,84 @@ __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t 
         xc = xat(c);
       }
       const double prod = __dmul_rn(double(v[u]), in ? xc : 0.0);
-      if (in) {
-        if (!kSkew)
-          atomicAdd(a.yacc + rw[u], prod);
-        else if (!hot.take(rw[u], prod))
-          atomicAdd(a.yperm + perm_slot(rw[u], a.pmask), prod);
-      }
+      if (in) sink.add(rw[u], prod);
+    }
+  }
+}
+
+// Nonzeros [kb, ke) of tile column j (column c0 + j < n) inside the tile's
+// range [k0, k1).  cp holds col_ptr[c0 .. c1]; the last column c1 ends at
+// k1 (a merge-path coordinate has col_ptr[c1] <= k1 <= col_ptr[c1 + 1]).
+__device__ __forceinline__ void csc_col_range(int j, int32_t c0, int32_t k0, int32_t c1,
+                                              int32_t k1, const int32_t *cp, int32_t &kb,
+                                              int32_t &ke) {
+  kb = max(cp[j], k0);
+  ke = c0 + j < c1 ? min(cp[j + 1], k1) : k1;
+}
+
+// Longest column of a CSC tile inside its nonzero range [k0, k1) (every
+// lane of the warp gets it).  cp as for csc_tile_compute.
+__device__ __forceinline__ int csc_tile_max_col(int32_t c0, int32_t k0, int32_t c1, int32_t k1,
+                                                int32_t n, const int32_t *cp) {
+  const int lane = threadIdx.x & 31;
+  int longest = 0;
+  for (int j = lane; j <= c1 - c0 && c0 + j < n; j += 32) {
+    int32_t kb, ke;
+    csc_col_range(j, c0, k0, c1, k1, cp, kb, ke);
+    longest = max(longest, ke - kb);
+  }
+  return __reduce_max_sync(0xffffffffu, longest);
+}
+
+// CSC tiles of short columns, lane-interleaved: step i of the warp takes
+// the tile's nonzeros k0 + 32 i + lane, so every load instruction reads 32
+// consecutive elements (one or two 128-byte lines) and every atomic add
+// covers the rows of a few neighbouring columns.  In a banded matrix those
+// rows fall in a few short runs (a 2D Laplacian's 32 consecutive nonzeros,
+// about six columns, add into three runs of about eight rows), so one
+// warp-wide atomic add touches a few 32-byte sectors of y instead of 32
+// scattered ones; on GB300 the L2 takes such coalesced FP64 adds far faster
+// than scattered ones, and the add itself stays in L2 (the SM's FP64 pipe,
+// about two lane operations per clock, does only the multiply).  The
+// column of each nonzero comes from colof (this warp's 32 * IPT + 8 int16
+// entries of shared memory), filled first by a walk of the tile's columns
+// (one lane per column: the tile's columns must be short, see
+// csc_tile_max_col).  Seven steps are loaded ahead (eight spill registers
+// at four resident blocks; four keep too few loads in flight).
+template <class Pol, class Sink>
+__device__ __forceinline__ void csc_tile_interleaved(const CscArgs<Pol> &a, int32_t c0,
+                                                     int32_t k0, int32_t c1, int32_t k1,
+                                                     const int32_t *cp, const Sink &sink,
+                                                     int16_t *colof) {
+  using LV = typename LoadT<typename Pol::V>::type;
+  constexpr int B = 7;
+  const int lane = threadIdx.x & 31;
+  const int ncols = c1 - c0 + 1;
+  for (int j = lane; j < ncols && c0 + j < a.n; j += 32) {
+    int32_t kb, ke;
+    csc_col_range(j, c0, k0, c1, k1, cp, kb, ke);
+    for (int32_t k = kb; k < ke; ++k) colof[k - k0] = static_cast<int16_t>(j);
+  }
+  __syncwarp();
+  const int32_t len = k1 - k0;
+  for (int32_t i0 = 0; i0 < len; i0 += 32 * B) {
+    int32_t rw[B];
+    LV v[B];
+    double xv[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int32_t p = i0 + 32 * u + lane;
+      const bool in = p < len;
+      rw[u] = in ? ld_stream(a.row_idx + k0 + p) : 0;
+      v[u] = in ? LV(ld_stream(a.val + k0 + p)) : LV(0);
+      xv[u] = in ? double(load_x(a.x, c0 + colof[p])) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      if (i0 + 32 * u >= len) break;  // warp-uniform
+      const double xs = a.scaled ? __dmul_rn(xv[u], a.scale) : xv[u];
+      const double prod = __dmul_rn(double(v[u]), xs);
+      if (i0 + 32 * u + lane < len) sink.add(rw[u], prod);
     }
   }
 }
