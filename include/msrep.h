@@ -109,9 +109,10 @@ typedef struct {
  *                             (tiles, hub and frequent rows), COO_BY_COL
  *                             and COO_UNSORTED (hub and frequent rows);
  *                             plan_bytes >= msrep_plan_size().
- *   tile                      nonzeros+rows per thread-block tile of the
- *                             plan, 0 = library default; must be a
- *                             supported size (msrep_tile_supported()).
+ *   tile                      nonzeros+rows per warp tile of the plan,
+ *                             0 = the format's default (256 for CSC, 512
+ *                             for the others); must be a supported size
+ *                             (msrep_tile_supported()).
  * An empty partition (np > nnz) has start_major = 0, end_major = -1,
  * start_flag = 0 and a one-entry local pointer {0}. */
 typedef struct {

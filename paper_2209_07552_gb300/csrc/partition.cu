@@ -737,7 +737,7 @@ static msrep_status partition_compressed(const msrep_matrix *A,
   cudaStream_t st = as_stream(stream);
   if (flags & MSREP_VALIDATE) MSREP_TRY(run_validation(A, st));
   const int32_t n_major = A->fmt == MSREP_CSR ? A->m : A->n;
-  const int32_t tile = effective_tile(p->tile);
+  const int32_t tile = effective_tile_fmt(p->tile, A->fmt);
   PlanLayout L = plan_layout(n_major, A->nnz, p->np, tile, A->fmt == MSREP_CSC);
   if (p->plan && p->plan_bytes < static_cast<int64_t>(L.bytes))
     return fail(MSREP_ERR_WORKSPACE, "plan buffer has %lld bytes, needs %zu",
@@ -820,7 +820,7 @@ msrep_status msrep_plan_size(const msrep_matrix *A, int32_t np, int32_t tile,
                              int64_t *bytes) {
   MSREP_TRY(check_matrix(A));
   if (np < 1 || !bytes) return fail(MSREP_ERR_INVALID_ARG, "bad np or bytes");
-  const int32_t t = effective_tile(tile);
+  const int32_t t = effective_tile_fmt(tile, A->fmt);
   if (!tile_supported(t)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", tile);
   if (A->fmt == MSREP_COO) {
     *bytes = 0;

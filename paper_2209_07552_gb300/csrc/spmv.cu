@@ -311,22 +311,23 @@ __global__ void __launch_bounds__(kThreads) coo_stream(CooArgs<Pol> a) {
     for (int j = i + 1; j < i + S && first + j * W < T; ++j) mbar_wait(bar + j % S, (j / S) & 1, a.err);
 }
 
-// Longest column for which a CSC tile of a matrix without hub rows takes
-// the interleaved walk (csc_tile_interleaved); tiles with longer columns
-// split their nonzeros evenly over the lanes (csc_tile_compute).
-constexpr int kColumnWalkMax = 32;
+// Longest column for which a CSC tile takes the interleaved walk
+// (csc_tile_interleaved, whose column table is filled one lane per
+// column); tiles with longer columns split their nonzeros evenly over the
+// lanes (csc_tile_compute).  On the R-MAT workload at tile 256 the limit
+// 128 gave 105 us, 32 gave 115 us and 256 gave 142 us.
+constexpr int kColumnWalkMax = 128;
 
-// Dynamic shared memory of csc_direct: per warp the tile's column pointers,
-// then one region that holds either the frequent-row table (matrices with
-// hub rows) or, per warp, the column of each of the tile's nonzeros (int16,
-// for the interleaved walk of the others).
+// Dynamic shared memory of csc_direct: per warp the tile's column pointers
+// (int32) and the column of each of its nonzeros (int16, for the
+// interleaved walk), then the frequent-row table of matrices with hub rows.
 template <int IPT>
 struct CscSmem {
   static constexpr int CAP = 32 * IPT + 8;
   static constexpr size_t CP = size_t(kWarps) * CAP * sizeof(int32_t);
   static constexpr size_t COL = size_t(kWarps) * CAP * sizeof(int16_t);
   static constexpr size_t WARM = size_t(kWarm) * (sizeof(int32_t) + sizeof(double));
-  static constexpr size_t BYTES = CP + (COL > WARM ? COL : WARM);
+  static constexpr size_t BYTES = CP + COL + WARM;
 };
 
 template <class Pol, int IPT>
@@ -341,8 +342,8 @@ __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const 
   const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int32_t *s_cp = reinterpret_cast<int32_t *>(dsm) + wid * SM::CAP;
   int16_t *s_col = reinterpret_cast<int16_t *>(dsm + SM::CP) + wid * SM::CAP;
-  int32_t *s_wtag = reinterpret_cast<int32_t *>(dsm + SM::CP);
-  double *s_wacc = reinterpret_cast<double *>(dsm + SM::CP + sizeof(int32_t) * kWarm);
+  int32_t *s_wtag = reinterpret_cast<int32_t *>(dsm + SM::CP + SM::COL);
+  double *s_wacc = reinterpret_cast<double *>(dsm + SM::CP + SM::COL + sizeof(int32_t) * kWarm);
   const bool skew = csc_skewed(a.hot, a.yperm);
   // The next tile's coordinates and first 64 column pointers are loaded
   // while the current tile is processed (as in csr_direct).
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const 
   };
   // one tile (its coordinates fetched): stage its column pointers, fetch
   // the next tile's, then scatter its products to sink
-  auto tile = [&](int b, const auto &sink, bool column_walk) {
+  auto tile = [&](int b, const auto &sink) {
     const int32_t c0 = n0, k0 = nk0, c1 = n1, k1 = nk1;
     const int32_t cend = min(c1 + 1, a.n + 1);
     if (c0 + lane < cend) s_cp[lane] = p0;
@@ -374,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const 
       const double xv = double(load_x(a.x, g));
       return a.scaled ? __dmul_rn(xv, a.scale) : xv;
     };
-    if (column_walk && csc_tile_max_col(c0, k0, c1, k1, a.n, s_cp) <= kColumnWalkMax)
+    if (csc_tile_max_col(c0, k0, c1, k1, a.n, s_cp) <= kColumnWalkMax)
       csc_tile_interleaved<Pol>(a, c0, k0, c1, k1, s_cp, sink, s_col);
     else
       csc_tile_compute<Pol>(a, c0, k0, c1, k1, s_cp, xat, Seg<int32_t>{a.row_idx, 0},
@@ -388,13 +389,13 @@ __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const 
     const SkewSink<WarmRows> sink{&warm, a.yperm, a.pmask};
     const int first = blockIdx.x * kWarps + wid;
     if (first < T) fetch(first);
-    for (int b = first; b < T; b += stride) tile(b, sink, false);
+    for (int b = first; b < T; b += stride) tile(b, sink);
     warm.flush(a.yperm, a.pmask);
   } else {
     const DirectSink sink{a.yacc};
     const int first = blockIdx.x * kWarps + wid;
     if (first < T) fetch(first);
-    for (int b = first; b < T; b += stride) tile(b, sink, true);
+    for (int b = first; b < T; b += stride) tile(b, sink);
   }
 }
 
@@ -754,7 +755,7 @@ template <class Pol, int IPT>
 static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
                             double alpha, const void *x, double beta, void *y,
                             unsigned flags, const Workspace &w, cudaStream_t st) {
-  const int32_t tile = effective_tile(p->tile);
+  const int32_t tile = effective_tile_fmt(p->tile, A->fmt);
   PlanLayout L = plan_layout(A->m, A->nnz, p->np, tile);
   const char *plan = static_cast<const char *>(p->plan);
   CsrArgs<Pol> a;
@@ -789,7 +790,7 @@ template <class Pol, int IPT>
 static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
                             double alpha, const void *x, double beta, void *y,
                             unsigned flags, const Workspace &w, cudaStream_t st) {
-  const int32_t tile = effective_tile(p->tile);
+  const int32_t tile = effective_tile_fmt(p->tile, A->fmt);
   CooArgs<Pol> a;
   a.row_idx = A->idx2;
   a.col_idx = A->idx;
@@ -825,7 +826,7 @@ template <class Pol, int IPT>
 static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
                             double alpha, const void *x, double beta, void *y,
                             unsigned flags, const Workspace &w, cudaStream_t st) {
-  const int32_t tile = effective_tile(p->tile);
+  const int32_t tile = effective_tile_fmt(p->tile, A->fmt);
   PlanLayout L = plan_layout(A->n, A->nnz, p->np, tile, true);
   const char *plan = static_cast<const char *>(p->plan);
   constexpr bool kF64 = sizeof(typename Pol::X) == 8;
@@ -944,7 +945,7 @@ static msrep_status dispatch_tile(const msrep_matrix *A, const msrep_partition *
                                   void *y, unsigned flags, const Workspace &w,
                                   cudaStream_t st) {
   if (coo_scatter_format(A->fmt)) return run_coo_scatter<Pol>(A, p, alpha, x, beta, y, w, st);
-  const int32_t tile = effective_tile(p->tile);
+  const int32_t tile = effective_tile_fmt(p->tile, A->fmt);
 #define MSREP_FMT_CASE(IPT)                                                   \
   switch (A->fmt) {                                                           \
     case MSREP_CSR: return run_csr<Pol, IPT>(A, p, alpha, x, beta, y, flags, w, st); \
@@ -1021,7 +1022,7 @@ msrep_status spmv_workspace_bytes(const msrep_matrix *A, const msrep_partition *
   MSREP_TRY(check_matrix(A));
   if (!part || part->np < 1 || !bytes)
     return fail(MSREP_ERR_INVALID_ARG, "bad partition or bytes pointer");
-  const int32_t tile = effective_tile(part->tile);
+  const int32_t tile = effective_tile_fmt(part->tile, A->fmt);
   if (!tile_supported(tile)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", part->tile);
   const int64_t tiles = tiles_for(A, part, tile);
   *bytes = ws_layout(tiles, csc_acc_len(A, perm_ok), nullptr, nullptr);
@@ -1034,7 +1035,7 @@ msrep_status spmv_run(const msrep_matrix *A, const msrep_partition *part, double
   MSREP_TRY(check_matrix(A));
   if (!part || part->np < 1 || !part->start_idx || !part->end_idx)
     return fail(MSREP_ERR_INVALID_ARG, "bad partition");
-  const int32_t tile = effective_tile(part->tile);
+  const int32_t tile = effective_tile_fmt(part->tile, A->fmt);
   if (!tile_supported(tile)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", part->tile);
   if ((flags & MSREP_STREAM_TMA) && tile > 512)
     return fail(MSREP_ERR_INVALID_ARG, "MSREP_STREAM_TMA supports tiles up to 512");
