@@ -500,9 +500,10 @@ __global__ void __launch_bounds__(kThreads) csc_stream(CscArgs<Pol> a, const int
 // and the merge is their sum.  Here each product is one FP64 atomic add into
 // the row's entry of y (or of the accumulator): the atomic adds form the sum
 // of the partials in place, so the result does not depend on the partition
-// boundaries, and the nonzeros are spread over the grid in equal runs of 8
-// per lane.  Hub rows (from the plan) are summed per warp in shared memory
-// and the other rows go to the permuted accumulator, as for CSC.
+// boundaries, and the nonzeros are spread over the warps of the grid in
+// runs of consecutive nonzeros (coo_scatter).  Hub and frequent rows (from the plan) are summed per block in
+// shared memory and the other rows go to the permuted accumulator, as for
+// CSC.
 template <class Pol>
 struct ScatterArgs {
   const int32_t *row_idx;
@@ -519,43 +520,52 @@ struct ScatterArgs {
   int64_t nnz;
 };
 
+// Lane-interleaved, as CSC's interleaved walk: each warp takes runs of
+// 32 * B consecutive nonzeros, step u of a run the 32 nonzeros
+// base + 32 u + lane, so every load reads 32 consecutive elements and, in
+// column order, the x gathers of a step touch a few columns and its atomic
+// adds (for a banded matrix) a few short runs of rows.  B steps are loaded
+// ahead.
 template <class Pol>
 __global__ void __launch_bounds__(kThreads, 4) coo_scatter(ScatterArgs<Pol> a) {
   grid_dependency_wait();
   using LV = typename LoadT<typename Pol::V>::type;
+  constexpr int B = 7;
   __shared__ int32_t s_wtag[kWarm];
   __shared__ double s_wacc[kWarm];
   const bool skew = a.hot != nullptr && csc_skewed(a.hot, a.yperm);
-  WarmRows hot;
-  if (skew) hot.load(a.warm, s_wtag, s_wacc);
-  const int64_t groups = (a.nnz + 7) >> 3;
-  const int64_t step = int64_t(gridDim.x) * blockDim.x;
-  auto run = [&](auto with_hot) {
-    constexpr bool kSkew = decltype(with_hot)::value;
-    for (int64_t g = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; g < groups; g += step) {
-      const int64_t g8 = g << 3;
-      int32_t r[8], c[8];
-      LV v[8];
-      load_group(a.row_idx, g8, a.nnz, r);
-      load_group(a.col_idx, g8, a.nnz, c);
-      load_group(a.val, g8, a.nnz, v);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  auto run = [&](const auto &sink) {
+    for (int64_t base = warp * 32 * B; base < a.nnz; base += nwarps * 32 * B) {
+      int32_t r[B];
+      LV v[B];
+      double xv[B];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        if (g8 + u >= a.nnz) break;
-        const double xv = double(load_x(a.x, c[u]));
-        const double prod = __dmul_rn(double(v[u]), a.scaled ? __dmul_rn(xv, a.scale) : xv);
-        if (!kSkew)
-          atomicAdd(a.yacc + r[u], prod);
-        else if (!hot.take(r[u], prod))
-          atomicAdd(a.yperm + perm_slot(r[u], a.pmask), prod);
+      for (int u = 0; u < B; ++u) {
+        const int64_t k = base + 32 * u + lane;
+        const bool in = k < a.nnz;
+        r[u] = in ? ld_stream(a.row_idx + k) : 0;
+        v[u] = in ? LV(ld_stream(a.val + k)) : LV(0);
+        xv[u] = in ? double(load_x(a.x, ld_stream(a.col_idx + k))) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < B; ++u) {
+        if (base + 32 * u >= a.nnz) break;  // warp-uniform
+        const double xs = a.scaled ? __dmul_rn(xv[u], a.scale) : xv[u];
+        const double prod = __dmul_rn(double(v[u]), xs);
+        if (base + 32 * u + lane < a.nnz) sink.add(r[u], prod);
       }
     }
   };
   if (skew) {
-    run(std::true_type{});
+    WarmRows hot;
+    hot.load(a.warm, s_wtag, s_wacc);
+    run(SkewSink<WarmRows>{&hot, a.yperm, a.pmask});
     hot.flush(a.yperm, a.pmask);
   } else {
-    run(std::false_type{});
+    run(DirectSink{a.yacc});
   }
 }
 
@@ -921,7 +931,7 @@ static msrep_status run_coo_scatter(const msrep_matrix *A, const msrep_partition
   int nb = 1;
   MSREP_TRY(kernel_occupancy(coo_scatter<Pol>, 0, 0, &nb));
   const int64_t grid = std::max<int64_t>(
-      1, std::min<int64_t>(ceil_div(ceil_div(A->nnz, 8), kThreads), int64_t(nb) * sm_count()));
+      1, std::min<int64_t>(ceil_div(A->nnz, 7 * kThreads), int64_t(nb) * sm_count()));
   prof_begin(st);
   MSREP_TRY(launch_dependent(coo_scatter<Pol>, grid, kThreads, st, 0, a));
   prof_end(st);
