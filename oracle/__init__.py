@@ -65,6 +65,14 @@ def _lib():
                 ctypes.c_int32, ctypes.c_int64, _i32p, ctypes.c_int32,
                 _i32p, _i32p, _i32p, _i32p, _u8p, _i32p]
             lib.ref_partition_merge_path.restype = ctypes.c_int
+            lib.ref_partition_row_block.argtypes = [
+                ctypes.c_int32, ctypes.c_int64, _i32p, ctypes.c_int32,
+                _i32p, _i32p, _i32p, _i32p, _u8p]
+            lib.ref_partition_row_block.restype = ctypes.c_int
+            lib.ref_partition_coo_row_block.argtypes = [
+                ctypes.c_int64, _i32p, ctypes.c_int32, ctypes.c_int32, _i32p, _i32p,
+                _i32p, _i32p, _u8p]
+            lib.ref_partition_coo_row_block.restype = ctypes.c_int
             lib.ref_local_offsets.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p]
             lib.ref_local_offsets.restype = ctypes.c_int64
             lib.ref_partition_local_compressed.argtypes = [
@@ -129,7 +137,7 @@ def _c(a, dtype) -> np.ndarray:
 # --------------------------------------------------------------------------
 
 def _partition_compressed(ptr, nnz: int, np_: int, with_local: bool,
-                          merge_path: bool = False):
+                          merge_path: bool = False, row_block: bool = False):
     ptr = _c(ptr, np.int32)
     n_major = ptr.shape[0] - 1
     out = {k: np.empty(np_, np.int32) for k in
@@ -142,6 +150,11 @@ def _partition_compressed(ptr, nnz: int, np_: int, with_local: bool,
             _p(out["end_idx"], _i32p), _p(out["start_major"], _i32p),
             _p(out["end_major"], _i32p), _p(out["start_flag"], _u8p),
             _p(out["cut_row"], _i32p))
+    elif row_block:
+        rc = _lib().ref_partition_row_block(
+            n_major, nnz, _p(ptr, _i32p), np_, _p(out["start_idx"], _i32p),
+            _p(out["end_idx"], _i32p), _p(out["start_major"], _i32p),
+            _p(out["end_major"], _i32p), _p(out["start_flag"], _u8p))
     else:
         rc = _lib().ref_partition_compressed(
             n_major, nnz, _p(ptr, _i32p), np_, _p(out["start_idx"], _i32p),
@@ -184,6 +197,39 @@ def partition_merge_path(ptr, nnz: int, np_: int, with_local: bool = False):
     nonzeros, metadata as Alg. 2 for each cut's nonzero range.  Also returns
     ``cut_row``, the row coordinate of each of the np+1 cuts."""
     return _partition_compressed(ptr, nnz, np_, with_local, merge_path=True)
+
+
+def partition_row_block(ptr, nnz: int, np_: int, with_local: bool = False):
+    """The Baseline row-block partitioning of Sec. 5.1 (reading R11) of CSR
+    (row_ptr) or CSC (col_ptr): np blocks of equal row (column) count, each
+    with all of its nonzeros; metadata as Alg. 2 gives them for each block's
+    nonzero range."""
+    return _partition_compressed(ptr, nnz, np_, with_local, row_block=True)
+
+
+def partition_coo_row_block(row_idx, m: int, np_: int, with_local: bool = False):
+    """The Baseline row-block partitioning (reading R11) of row-sorted COO:
+    block i holds the nonzeros of rows floor(i*m/np) .. floor((i+1)*m/np)-1,
+    found by scanning row_idx."""
+    row_idx = _c(row_idx, np.int32)
+    nnz = row_idx.shape[0]
+    out = {k: np.empty(np_, np.int32) for k in
+           ("start_idx", "end_idx", "start_major", "end_major")}
+    out["start_flag"] = np.empty(np_, np.uint8)
+    rc = _lib().ref_partition_coo_row_block(
+        nnz, _p(row_idx, _i32p), m, np_, _p(out["start_idx"], _i32p),
+        _p(out["end_idx"], _i32p), _p(out["start_major"], _i32p),
+        _p(out["end_major"], _i32p), _p(out["start_flag"], _u8p))
+    if rc != 0:
+        raise ValueError("invalid partition arguments")
+    if with_local:
+        lrow = np.empty(max(nnz, 1), np.int32)
+        _lib().ref_partition_local_coo(
+            _p(row_idx, _i32p), np_, _p(out["start_idx"], _i32p),
+            _p(out["end_idx"], _i32p), _p(out["start_major"], _i32p),
+            _p(lrow, _i32p))
+        out["local"] = lrow[:nnz]
+    return out
 
 
 def partition_coo(row_idx, np_: int, with_local: bool = False):

@@ -44,6 +44,18 @@
  *       between cuts i and i+1, and its metadata follow Alg. 2 (R3, R4) for
  *       that nonzero range.  Optional variant: Alg. 2's pure nonzero split
  *       stays the default.
+ *   R11 The Baseline partitioning of Sec. 5.1 (and the row-block split of
+ *       Sec. 2.3) cuts the rows (CSR, COO) or columns (CSC) into np blocks
+ *       of equal size without looking at the nonzeros: block i holds rows
+ *       floor(i*n_major/np) .. floor((i+1)*n_major/np)-1 (64-bit product)
+ *       and all of their nonzeros.  In the augmented metadata that is the
+ *       nonzero range ptr[r_i] .. ptr[r_{i+1}]-1, with start/end major and
+ *       flag as Alg. 2 gives them for that range (R3; a block starts at a
+ *       row start, so its flag is 0) and R4 for a block whose rows are all
+ *       empty.  For row-sorted COO the block's range is found by scanning
+ *       the row index (Sec. 5.3 searches for each row block's start and
+ *       end).  A comparison partitioning: its blocks carry as many
+ *       nonzeros as their rows happen to hold.
  *   R9  COO sorted by (col, row) (Sec. 3.2.3 names it, with cost
  *       O(np log n)): Alg. 6 with the column index as the major index, so
  *       start_major/end_major are columns and the flag marks a split
@@ -156,6 +168,67 @@ int ref_partition_merge_path(int32_t n_major, int64_t nnz, const int32_t *ptr,
     start_flag[i] = (s > (int64_t)ptr[sr]) ? 1 : 0;
   }
   free(cut_k);
+  return 0;
+}
+
+/* Baseline row-block (column-block) partitioning of a compressed pointer
+ * array, reading R11. */
+int ref_partition_row_block(int32_t n_major, int64_t nnz, const int32_t *ptr,
+                            int32_t np, int32_t *start_idx, int32_t *end_idx,
+                            int32_t *start_major, int32_t *end_major,
+                            uint8_t *start_flag) {
+  if (np < 1 || n_major < 0 || nnz < 0) return 1;
+  int32_t hint = 0;
+  for (int32_t i = 0; i < np; i++) {
+    const int32_t r0 = (int32_t)(((int64_t)i * n_major) / np);
+    const int32_t r1 = (int32_t)(((int64_t)(i + 1) * n_major) / np);
+    const int64_t s = ptr[r0], e = (int64_t)ptr[r1] - 1;
+    start_idx[i] = (int32_t)s;
+    end_idx[i] = (int32_t)e;
+    if (e < s) { /* reading R4 */
+      start_major[i] = 0;
+      end_major[i] = -1;
+      start_flag[i] = 0;
+      continue;
+    }
+    int32_t sr = owner_scan(ptr, n_major, s, hint);
+    int32_t er = owner_scan(ptr, n_major, e, sr);
+    hint = sr;
+    start_major[i] = sr;
+    end_major[i] = er;
+    start_flag[i] = (s > (int64_t)ptr[sr]) ? 1 : 0;
+  }
+  return 0;
+}
+
+/* Baseline row-block partitioning of row-sorted COO, reading R11: the rows
+ * of block i are found by scanning row_idx forward. */
+int ref_partition_coo_row_block(int64_t nnz, const int32_t *row_idx, int32_t m,
+                                int32_t np, int32_t *start_idx, int32_t *end_idx,
+                                int32_t *start_row, int32_t *end_row,
+                                uint8_t *start_flag) {
+  if (np < 1 || nnz < 0 || m < 0) return 1;
+  int64_t k = 0;
+  for (int32_t i = 0; i < np; i++) {
+    const int32_t r0 = (int32_t)(((int64_t)i * m) / np);
+    const int32_t r1 = (int32_t)(((int64_t)(i + 1) * m) / np);
+    while (k < nnz && row_idx[k] < r0) k++;
+    const int64_t s = k;
+    int64_t t = s;
+    while (t < nnz && row_idx[t] < r1) t++;
+    const int64_t e = t - 1;
+    start_idx[i] = (int32_t)s;
+    end_idx[i] = (int32_t)e;
+    if (e < s) {
+      start_row[i] = 0;
+      end_row[i] = -1;
+      start_flag[i] = 0;
+      continue;
+    }
+    start_row[i] = row_idx[s];
+    end_row[i] = row_idx[e];
+    start_flag[i] = (s > 0 && row_idx[s - 1] == row_idx[s]) ? 1 : 0;
+  }
   return 0;
 }
 

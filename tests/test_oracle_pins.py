@@ -602,3 +602,103 @@ def test_compensated_sum_recovers_small_terms():
     gam = (len(w) - 1) * eps / (1 - (len(w) - 1) * eps)
     bound = eps * abs(exact) + gam * gam * sum(abs(Fraction(t)) for t in w.tolist())
     assert abs(got - exact) <= bound
+
+
+# --------------------------------------------------------------------------
+# Baseline row-block partitioning (Sec. 5.1, reading R11)
+# --------------------------------------------------------------------------
+
+def test_hand_example_row_block():
+    g = _hand()
+    e = g["pcsr_row_block"]
+    p = O.partition_row_block(g["csr"]["row_ptr"], 9, e["np"], with_local=True)
+    assert p["start_idx"].tolist() == e["start_idx"]
+    assert p["end_idx"].tolist() == e["end_idx"]
+    assert p["start_major"].tolist() == e["start_row"]
+    assert p["end_major"].tolist() == e["end_row"]
+    assert p["start_flag"].tolist() == e["start_flag"]
+    assert p["local"].tolist() == [v for part in e["local_row_ptr"] for v in part]
+    q = O.partition_coo_row_block(g["coo"]["row_idx"], g["m"], e["np"], with_local=True)
+    assert q["start_idx"].tolist() == e["start_idx"]
+    assert q["start_major"].tolist() == e["start_row"]
+    assert q["end_major"].tolist() == e["end_row"]
+    assert q["local"].tolist() == e["pcoo_local_row_idx"]
+    c = g["pcsc_row_block"]
+    r = O.partition_row_block(g["csc"]["col_ptr"], 9, c["np"], with_local=True)
+    assert r["start_idx"].tolist() == c["start_idx"]
+    assert r["end_idx"].tolist() == c["end_idx"]
+    assert r["start_major"].tolist() == c["start_col"]
+    assert r["end_major"].tolist() == c["end_col"]
+    assert r["start_flag"].tolist() == c["start_flag"]
+    assert r["local"].tolist() == [v for part in c["local_col_ptr"] for v in part]
+
+
+def _brute_row_block(row_ptr, m, P):
+    """Block i = rows [floor(i m / P), floor((i+1) m / P)); its nonzero range
+    read off row_ptr, its first and last owning row by numpy's
+    searchsorted (the last r with row_ptr[r] <= k)."""
+    ptr = np.asarray(row_ptr, np.int64)
+    out = {"start_idx": [], "end_idx": [], "start_major": [], "end_major": [],
+           "start_flag": []}
+    for i in range(P):
+        r0, r1 = (i * m) // P, ((i + 1) * m) // P
+        s, e = int(ptr[r0]), int(ptr[r1]) - 1
+        out["start_idx"].append(s)
+        out["end_idx"].append(e)
+        if e < s:
+            out["start_major"].append(0)
+            out["end_major"].append(-1)
+            out["start_flag"].append(0)
+            continue
+        sr = int(np.searchsorted(ptr[:m], s, side="right")) - 1
+        er = int(np.searchsorted(ptr[:m], e, side="right")) - 1
+        out["start_major"].append(sr)
+        out["end_major"].append(er)
+        out["start_flag"].append(int(s > ptr[sr]))
+    return out
+
+
+@pytest.mark.parametrize("k", range(6))
+def test_row_block_partition_brute_force(k):
+    a = _adversarial()[k]
+    coo = I.csr_to_coo(a)
+    for P in sorted({1, 2, 3, 4, 7, 16, max(1, a.m - 1), a.m, a.m + 5}):
+        want = _brute_row_block(a.row_ptr, a.m, P)
+        got = O.partition_row_block(a.row_ptr, a.nnz, P, with_local=True)
+        for key in want:
+            assert got[key].tolist() == want[key], (key, P)
+        # row blocks never split a row, and the ranges tile [0, nnz) in order
+        assert not got["start_flag"].any()
+        assert got["start_idx"][0] == 0 and got["end_idx"][-1] == a.nnz - 1
+        assert np.all(got["start_idx"][1:] == got["end_idx"][:-1] + 1)
+        # pCOO's row blocks (found by scanning row_idx) equal pCSR's
+        q = O.partition_coo_row_block(coo.row_idx, a.m, P, with_local=True)
+        for key in want:
+            assert q[key].tolist() == want[key], (key, P)
+        if a.nnz:
+            owner = np.repeat(np.arange(P), got["end_idx"] - got["start_idx"] + 1)
+            sm = got["start_major"][owner]
+            assert np.array_equal(q["local"], coo.row_idx - sm)
+
+
+def test_row_block_csc_is_row_block_of_transpose():
+    a = I.rmat(scale=9, nnz=3000, seed=17)
+    c = I.csr_to_csc(a)
+    t = I.transpose_csr(a)
+    for P in (1, 5, 64, 600):
+        p = O.partition_row_block(c.col_ptr, a.nnz, P)
+        q = O.partition_row_block(t.row_ptr, a.nnz, P)
+        for key in p:
+            assert np.array_equal(p[key], q[key]), (key, P)
+
+
+def test_row_block_partitioned_spmv_equals_dense():
+    """The partitioned SpMV of Alg. 3 over row blocks (no row is split, so
+    the merge only writes each block's rows) gives the dense product."""
+    for seed in (3, 4):
+        d, a = _tiny(seed, 16, 13, 0.25)
+        x = I.vector(a.n, seed + 100)
+        for P in (1, 3, 7, 16, 20):
+            part = O.partition_row_block(a.row_ptr, a.nnz, P)
+            y = O.pspmv_csr(a.m, a.row_ptr, a.col_idx, a.val, part, x)
+            assert np.allclose(y, d @ x, rtol=0, atol=1e-13)
