@@ -134,6 +134,16 @@ typedef struct {
 #define MSREP_PART_MERGE_PATH 0x2u /* CSR/CSC: row+nonzero merge-path cuts
                                       instead of Alg. 2's nonzero cuts (see
                                       msrep_partition_csr) */
+#define MSREP_PART_ROW_BLOCK 0x4u  /* the Baseline of Sec. 5.1: equal blocks
+                                      of rows (CSR, COO; columns for CSC and
+                                      COO_BY_COL) whatever their nonzeros;
+                                      partition i holds rows floor(i*m/np) ..
+                                      floor((i+1)*m/np)-1 and the metadata of
+                                      their nonzero range (start_flag 0; R4 of
+                                      the empty case for blocks of empty rows).
+                                      A comparison partitioning for the
+                                      imbalance Sec. 2.3 describes.  Not with
+                                      MSREP_PART_MERGE_PATH or COO_UNSORTED. */
 
 /* Library version string. */
 const char *msrep_version(void);
@@ -220,6 +230,14 @@ msrep_status msrep_spmv_workspace_size(const msrep_matrix *A,
 #define MSREP_STREAM_TMA 0x40u /* stage the nonzeros through shared memory
                                   with bulk copies (TMA) instead of direct
                                   256-bit loads; tiles up to 512         */
+#define MSREP_SCHED_PER_PARTITION 0x80u /* CSR, CSC, row-sorted COO: one
+                                  thread block per partition, which walks
+                                  that partition's tiles alone (as the paper
+                                  gives each partition one GPU), instead of
+                                  spreading every partition's tiles over all
+                                  blocks; the kernel then lasts as long as
+                                  its largest partition.  Same results.
+                                  Not with MSREP_STREAM_TMA. */
 
 /* y = alpha*A*x + beta*y over the partitions of `part` (Alg. 3 for CSR,
  * Alg. 5 for CSC, Alg. 7 for COO).  `part` must come from the matching

@@ -9,7 +9,7 @@ from .native import (MSREP_BF16, MSREP_COMP_ALL, MSREP_COMP_NONE, MSREP_COO,
                      MSREP_COO_BY_COL, MSREP_COO_UNSORTED,
                      MSREP_STREAM_TMA, msrep_device_status, msrep_wait_selftest,
                      MSREP_CSC, MSREP_CSR, MSREP_F32, MSREP_F64, MSREP_VALIDATE,
-                     MSREP_PART_MERGE_PATH,
+                     MSREP_PART_MERGE_PATH, MSREP_PART_ROW_BLOCK, MSREP_SCHED_PER_PARTITION,
                      DeviceMatrix, DevicePartition, MsrepError, alloc_workspace,
                      msrep_partition, msrep_partition_coo, msrep_partition_csc,
                      msrep_partition_csr, msrep_partition_local_bound,

@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(kBThreads, 3) batched_csr(const BatchItem *ite
     const int64_t base = __ldg(toff + j);
     const int b = static_cast<int>(g - base);
     CsrArgs<Pol> a;
+    a.part_toff = nullptr;
     a.row_ptr = it.row_ptr;
     a.col_idx = it.col_idx;
     a.val = static_cast<const typename Pol::V *>(it.val);

@@ -116,22 +116,39 @@ __device__ __forceinline__ int32_t path_row(const int32_t *__restrict__ ptr,
 // Alg. 2 / Alg. 4: metadata, one thread per partition
 // ---------------------------------------------------------------------------
 
+// Cut rules of part_meta_compressed.
+enum : int { kCutNonzeros = 0, kCutMergePath = 1, kCutRowBlock = 2 };
+
 // One warp per partition i (and one for the closing cut i = np).
-// merge_path = 0: Alg. 2's nonzero split, cut i at nonzero floor(i nnz/np).
-// merge_path = 1: cut i at item floor(i (n_major + nnz) / np) of the merged
+// kCutNonzeros: Alg. 2's nonzero split, cut i at nonzero floor(i nnz/np).
+// kCutMergePath: cut i at item floor(i (n_major + nnz) / np) of the merged
 // sequence of row ends and nonzeros; partition i then holds the nonzeros
 // between cuts i and i+1, with Alg. 2's metadata for that range.
+// kCutRowBlock: the Baseline of Sec. 5.1, cut i at row floor(i n_major /
+// np), so partition i holds rows [r_i, r_{i+1}) and all their nonzeros
+// (ptr[r_i] .. ptr[r_{i+1}] - 1), with Alg. 2's metadata for that range;
+// its tile-plan cut is the merge-path point (r_i, ptr[r_i]).
 __global__ void part_meta_compressed(const int32_t *__restrict__ ptr,
                                      int32_t n_major, int64_t nnz, int32_t np,
                                      int32_t *start_idx, int32_t *end_idx,
                                      int32_t *start_major, int32_t *end_major,
                                      uint8_t *start_flag, int64_t *plan_D,
-                                     int32_t *plan_R, int merge_path) {
+                                     int32_t *plan_R, int cut) {
   const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const bool lead = (threadIdx.x & 31) == 0;
   if (i > np) return;  // warp-uniform
   int64_t s, e;
-  if (merge_path) {
+  if (cut == kCutRowBlock) {
+    const int32_t r0 = static_cast<int32_t>((i * n_major) / np);
+    s = __ldg(ptr + r0);
+    if (plan_D && lead) {
+      plan_R[i] = r0;
+      plan_D[i] = s + r0;
+    }
+    if (i == np) return;
+    const int32_t r1 = static_cast<int32_t>(((i + 1) * n_major) / np);
+    e = int64_t(__ldg(ptr + r1)) - 1;
+  } else if (cut == kCutMergePath) {
     const int64_t total = int64_t(n_major) + nnz;
     const int64_t d = (i * total) / np;
     const int32_t R = path_row_warp(ptr, static_cast<int32_t>(d > nnz ? d - nnz : 0),
@@ -185,15 +202,39 @@ __global__ void part_meta_compressed(const int32_t *__restrict__ ptr,
   }
 }
 
-// Alg. 6 (reading for sorted COO): metadata from row_idx directly.
+// first k in [0, nnz) with idx[k] >= v (idx ascending), nnz if none
+__device__ __forceinline__ int64_t lower_bound_idx(const int32_t *__restrict__ idx, int64_t nnz,
+                                                   int32_t v) {
+  int64_t lo = 0, hi = nnz;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(idx + mid) < v)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// Alg. 6 (reading for sorted COO): metadata from row_idx directly.  With
+// row_block (the Baseline of Sec. 5.1), partition i holds the rows
+// [floor(i m / np), floor((i+1) m / np)) and the nonzero range is found by
+// a binary search of row_idx for those rows (Sec. 5.3 searches for each row
+// block's start and end).
 __global__ void part_meta_coo(const int32_t *__restrict__ row_idx, int64_t nnz,
                               int32_t np, int32_t *start_idx, int32_t *end_idx,
                               int32_t *start_major, int32_t *end_major,
-                              uint8_t *start_flag) {
+                              uint8_t *start_flag, int32_t m, int row_block) {
   int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i >= np) return;
-  int64_t s = (i * nnz) / np;
-  int64_t e = ((i + 1) * nnz) / np - 1;
+  int64_t s, e;
+  if (row_block) {
+    s = lower_bound_idx(row_idx, nnz, static_cast<int32_t>((i * m) / np));
+    e = lower_bound_idx(row_idx, nnz, static_cast<int32_t>(((i + 1) * m) / np)) - 1;
+  } else {
+    s = (i * nnz) / np;
+    e = ((i + 1) * nnz) / np - 1;
+  }
   start_idx[i] = static_cast<int32_t>(s);
   end_idx[i] = static_cast<int32_t>(e);
   if (e < s) {
@@ -346,8 +387,20 @@ __global__ void __launch_bounds__(256)
   const int64_t stride = int64_t(gridDim.x) * blockDim.x * 8;
   for (int64_t k0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) * 8; k0 < nnz;
        k0 += stride) {
+    // Alg. 2's split gives the owner directly; for other cuts (row blocks)
+    // the last partition starting at or before k0 is searched for
     int32_t i = static_cast<int32_t>(((k0 + 1) * np - 1) / nnz);
-    while (i > 0 && __ldg(start_idx + i) > k0) --i;
+    if (__ldg(start_idx + i) > k0 || (i + 1 < np && __ldg(start_idx + i + 1) <= k0)) {
+      int32_t lo = 0, hi = np - 1;
+      while (lo < hi) {
+        const int32_t mid = lo + (hi - lo + 1) / 2;
+        if (__ldg(start_idx + mid) <= k0)
+          lo = mid;
+        else
+          hi = mid - 1;
+      }
+      i = lo;
+    }
     int64_t next = i + 1 < np ? __ldg(start_idx + i + 1) : nnz;
     int32_t r0 = __ldg(start_major + i);
     int32_t r[8];
@@ -749,10 +802,15 @@ static msrep_status partition_compressed(const msrep_matrix *A,
   int32_t *R = plan ? reinterpret_cast<int32_t *>(plan + L.off_R) : nullptr;
   const int threads = 256;
   const int blocks = static_cast<int>(ceil_div(int64_t(p->np + 1) * 32, threads));
+  if ((flags & MSREP_PART_MERGE_PATH) && (flags & MSREP_PART_ROW_BLOCK))
+    return fail(MSREP_ERR_INVALID_ARG,
+                "MSREP_PART_MERGE_PATH and MSREP_PART_ROW_BLOCK exclude each other");
   part_meta_compressed<<<blocks, threads, 0, st>>>(
       A->ptr, n_major, A->nnz, p->np, p->start_idx, p->end_idx,
       p->start_major, p->end_major, p->start_flag, D, R,
-      (flags & MSREP_PART_MERGE_PATH) ? 1 : 0);
+      (flags & MSREP_PART_MERGE_PATH) ? kCutMergePath
+                                      : (flags & MSREP_PART_ROW_BLOCK) ? kCutRowBlock
+                                                                       : kCutNonzeros);
   MSREP_CUDA_TRY(cudaGetLastError());
   if (p->local_off) {
     local_off_scan<<<1, 1024, 0, st>>>(p->start_major, p->end_major, p->np,
@@ -853,6 +911,8 @@ msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
   MSREP_TRY(check_partition(p));
   if (flags & MSREP_PART_MERGE_PATH)
     return fail(MSREP_ERR_INVALID_ARG, "merge-path partitioning takes CSR or CSC");
+  if ((flags & MSREP_PART_ROW_BLOCK) && A->fmt == MSREP_COO_UNSORTED)
+    return fail(MSREP_ERR_INVALID_ARG, "row-block partitioning needs sorted COO");
   const bool scatter = coo_scatter_format(A->fmt);
   if (scatter && p->plan) {
     if (p->plan_bytes < static_cast<int64_t>(kScatterPlanBytes))
@@ -873,7 +933,9 @@ msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
                                                        p->end_major, p->start_flag);
   else
     part_meta_coo<<<blocks, threads, 0, st>>>(major, A->nnz, p->np, p->start_idx, p->end_idx,
-                                              p->start_major, p->end_major, p->start_flag);
+                                              p->start_major, p->end_major, p->start_flag,
+                                              A->fmt == MSREP_COO_BY_COL ? A->n : A->m,
+                                              (flags & MSREP_PART_ROW_BLOCK) ? 1 : 0);
   MSREP_CUDA_TRY(cudaGetLastError());
   if (p->local && A->nnz > 0) {
     const int grid = static_cast<int>(

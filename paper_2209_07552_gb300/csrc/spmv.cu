@@ -101,12 +101,13 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) csr_direct(CsrArgs<Pol> 
                                                        int64_t nnz) {
   grid_dependency_wait();
   __shared__ int32_t s_rp[kWarps][32 * IPT + 8];
-  const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int stride = gridDim.x * kWarps;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TileWalk tw = tile_walk(*n_tiles, kWarps, a.part_toff);
+  const int T = tw.end, stride = tw.step;
   // The next tile's coordinates and its first 64 row pointers are loaded
   // while the current tile is processed, so a tile does not start with two
   // dependent global round trips (coordinates, then row pointers).
-  int b = blockIdx.x * kWarps + wid;
+  int b = tw.first;
   int32_t r0 = 0, k0 = 0, r1 = 0, k1 = 0, p0 = 0, p1 = 0;
   auto fetch = [&](int t) {
     r0 = __ldg(a.tile_row + t);
@@ -218,10 +219,14 @@ __global__ void __launch_bounds__(kThreads) csr_stream(CsrArgs<Pol> a, const int
 template <class Pol, int IPT>
 __global__ void __launch_bounds__(kThreads, MSREP_MINB) coo_direct(CooArgs<Pol> a) {
   grid_dependency_wait();
-  const int T = a.np * a.G, wid = threadIdx.x >> 5;
-  const int stride = gridDim.x * kWarps;
+  const int wid = threadIdx.x >> 5;
+  int T = a.np * a.G, stride = gridDim.x * kWarps, b = blockIdx.x * kWarps + wid;
+  if (a.per_part) {  // block i walks partition i's G tiles alone
+    T = (blockIdx.x + 1) * a.G;
+    stride = kWarps;
+    b = blockIdx.x * a.G + wid;
+  }
   // the next tile's range is loaded while the current one is processed
-  int b = blockIdx.x * kWarps + wid;
   int32_t k0 = 0, k1 = 0;
   if (b < T) coo_tile_range(a, b, k0, k1);
   for (; b < T; b += stride) {
@@ -339,7 +344,9 @@ __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const 
   using SM = CscSmem<IPT>;
   grid_dependency_wait();
   extern __shared__ __align__(16) unsigned char dsm[];
-  const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TileWalk tw = tile_walk(*n_tiles, kWarps, a.part_toff);
+  const int T = tw.end, stride = tw.step, first = tw.first;
   int32_t *s_cp = reinterpret_cast<int32_t *>(dsm) + wid * SM::CAP;
   int16_t *s_col = reinterpret_cast<int16_t *>(dsm + SM::CP) + wid * SM::CAP;
   int32_t *s_wtag = reinterpret_cast<int32_t *>(dsm + SM::CP + SM::COL);
@@ -347,7 +354,6 @@ __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const 
   const bool skew = csc_skewed(a.hot, a.yperm);
   // The next tile's coordinates and first 64 column pointers are loaded
   // while the current tile is processed (as in csr_direct).
-  const int stride = gridDim.x * kWarps;
   int32_t n0 = 0, nk0 = 0, n1 = 0, nk1 = 0, p0 = 0, p1 = 0;
   auto fetch = [&](int t) {
     n0 = __ldg(a.tile_row + t);
@@ -387,13 +393,11 @@ __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const 
     WarmRows warm;
     warm.load(a.warm, s_wtag, s_wacc);
     const SkewSink<WarmRows> sink{&warm, a.yperm, a.pmask};
-    const int first = blockIdx.x * kWarps + wid;
     if (first < T) fetch(first);
     for (int b = first; b < T; b += stride) tile(b, sink);
     warm.flush(a.yperm, a.pmask);
   } else {
     const DirectSink sink{a.yacc};
-    const int first = blockIdx.x * kWarps + wid;
     if (first < T) fetch(first);
     for (int b = first; b < T; b += stride) tile(b, sink);
   }
@@ -741,16 +745,18 @@ static msrep_status kernel_occupancy(K kernel, size_t smem, int want_blocks, int
 // Launches the streaming kernel (dynamic shared-memory stages) unless the
 // caller asked for direct loads.  Grid: resident blocks x SMs, capped by the
 // number of tiles.
+// With per_part > 0 the grid is one block per partition (per_part blocks).
 template <class KS, class KD, class... Args>
 static msrep_status launch_tiles(KS kstream, KD kdirect, size_t stream_smem, size_t direct_smem,
-                                 int direct_blocks, bool direct, int64_t tiles, cudaStream_t st,
-                                 Args... args) {
+                                 int direct_blocks, bool direct, int64_t tiles, int per_part,
+                                 cudaStream_t st, Args... args) {
   int nb = 1;
   if (direct)
     MSREP_TRY(kernel_occupancy(kdirect, direct_smem, direct_blocks, &nb));
   else
     MSREP_TRY(kernel_occupancy(kstream, stream_smem, 0, &nb));
   int64_t grid = std::min<int64_t>(ceil_div(tiles, kWarps), int64_t(nb) * sm_count());
+  if (per_part > 0) grid = per_part;
   if (grid < 1) grid = 1;
   prof_begin(st);
   if (direct)
@@ -786,9 +792,12 @@ static msrep_status run_csr(const msrep_matrix *A, const msrep_partition *p,
   a.comp_mode = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
   a.err = kernel_err_ptr();
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
+  const bool per_part = (flags & MSREP_SCHED_PER_PARTITION) != 0;
+  a.part_toff = per_part ? reinterpret_cast<const int32_t *>(plan + L.off_toff) : nullptr;
   MSREP_TRY(launch_tiles(csr_stream<Pol, IPT>, csr_direct<Pol, IPT>,
                          StageGeom<typename Pol::V, IPT, 2>::BLOCK, 0, MSREP_MINB,
-                         (flags & MSREP_STREAM_TMA) == 0, L.tmax, st, a, n_tiles, A->nnz));
+                         (flags & MSREP_STREAM_TMA) == 0, L.tmax, per_part ? p->np : 0, st, a,
+                         n_tiles, A->nnz));
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   int64_t fg = std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count());
   MSREP_TRY(launch_dependent(fixup_split_rows<typename Pol::X, CsrTileView>, fg, 256, st, 0, v,
@@ -822,9 +831,10 @@ static msrep_status run_coo(const msrep_matrix *A, const msrep_partition *p,
   a.err = kernel_err_ptr();
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
   const int64_t T = int64_t(a.np) * a.G;
+  a.per_part = (flags & MSREP_SCHED_PER_PARTITION) != 0;
   MSREP_TRY(launch_tiles(coo_stream<Pol, IPT>, coo_direct<Pol, IPT>,
                          StageGeom<typename Pol::V, IPT, 2>::BLOCK, 0, MSREP_MINB,
-                         (flags & MSREP_STREAM_TMA) == 0, T, st, a));
+                         (flags & MSREP_STREAM_TMA) == 0, T, a.per_part ? p->np : 0, st, a));
   CooTileView v{A->idx2, p->start_idx, p->end_idx, A->nnz, a.G, a.np, A->m};
   int64_t fg = std::min<int64_t>(ceil_div(T, 256), 4 * sm_count());
   MSREP_TRY(launch_dependent(fixup_split_rows<typename Pol::X, CooTileView>, fg, 256, st, 0, v,
@@ -848,6 +858,8 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   a.tile_row = reinterpret_cast<const int32_t *>(plan + L.off_row);
   a.tile_k = reinterpret_cast<const int32_t *>(plan + L.off_k);
   const int32_t *n_tiles = reinterpret_cast<const int32_t *>(plan + L.off_toff) + p->np;
+  const bool per_part = (flags & MSREP_SCHED_PER_PARTITION) != 0;
+  a.part_toff = per_part ? reinterpret_cast<const int32_t *>(plan + L.off_toff) : nullptr;
   a.n = A->n;
   a.err = kernel_err_ptr();
   if (!a.err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
@@ -877,8 +889,8 @@ static msrep_status run_csc(const msrep_matrix *A, const msrep_partition *p,
   MSREP_TRY(launch_tiles(csc_stream<Pol, IPT>, csc_direct<Pol, IPT>,
                          StageGeom<typename Pol::V, IPT, 2>::BLOCK +
                              sizeof(double) * kWarps * (32 * IPT + 8),
-                         CscSmem<IPT>::BYTES, 0, (flags & MSREP_STREAM_TMA) == 0, L.tmax, st,
-                         a, n_tiles, A->nnz));
+                         CscSmem<IPT>::BYTES, 0, (flags & MSREP_STREAM_TMA) == 0, L.tmax,
+                         per_part ? p->np : 0, st, a, n_tiles, A->nnz));
   if (kF64) {
     if (w.perm)
       MSREP_TRY(launch_dependent(csc_unpermute, sg, 256, st, 0, a.hot,
@@ -1049,6 +1061,11 @@ msrep_status spmv_run(const msrep_matrix *A, const msrep_partition *part, double
   if (!tile_supported(tile)) return fail(MSREP_ERR_INVALID_ARG, "unsupported tile %d", part->tile);
   if ((flags & MSREP_STREAM_TMA) && tile > 512)
     return fail(MSREP_ERR_INVALID_ARG, "MSREP_STREAM_TMA supports tiles up to 512");
+  if ((flags & MSREP_SCHED_PER_PARTITION) &&
+      ((flags & MSREP_STREAM_TMA) || coo_scatter_format(A->fmt)))
+    return fail(MSREP_ERR_INVALID_ARG,
+                "MSREP_SCHED_PER_PARTITION takes CSR, CSC or row-sorted COO, without "
+                "MSREP_STREAM_TMA");
   if ((A->m > 0 && !y) || (A->n > 0 && !x && A->nnz > 0))
     return fail(MSREP_ERR_INVALID_ARG, "x or y is NULL");
   const bool f64 = A->val_dtype == MSREP_F64;

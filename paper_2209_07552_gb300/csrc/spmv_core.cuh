@@ -259,6 +259,21 @@ __device__ __forceinline__ LaneRange lane_range(int64_t k0, int64_t k1, int lane
   return r;
 }
 
+// The tiles warp `wid` of this block walks: by default tiles wid + 8 k,
+// wid + 8 k + 8 G, ... over all T tiles (block k of G blocks), so every
+// partition's tiles spread over the whole grid; with one block per
+// partition, block i walks tiles [toff_i, toff_{i+1}) of partition i only.
+struct TileWalk {
+  int first, end, step;
+};
+__device__ __forceinline__ TileWalk tile_walk(int T, int warps, const int32_t *part_toff) {
+  const int wid = threadIdx.x >> 5;
+  if (part_toff)
+    return TileWalk{__ldg(part_toff + blockIdx.x) + wid, __ldg(part_toff + blockIdx.x + 1), warps};
+  return TileWalk{static_cast<int>(blockIdx.x) * warps + wid, T,
+                  static_cast<int>(gridDim.x) * warps};
+}
+
 // ---------------------------------------------------------------------------
 // CSR tile
 // ---------------------------------------------------------------------------
@@ -278,6 +293,7 @@ struct CsrArgs {
   int32_t m;
   unsigned comp_mode;
   int *err;                 // device error word
+  const int32_t *part_toff; // one block per partition: its first tile, or null
 };
 
 template <class Pol>
@@ -407,6 +423,7 @@ struct CooArgs {
   double *head, *tail;
   unsigned comp_mode;
   int *err;
+  bool per_part;  // one block per partition (tiles i*G .. i*G+G-1)
 };
 
 template <class Pol>
@@ -576,6 +593,7 @@ struct CscArgs {
   const unsigned long long *warm;  // frequent-row table, kWarm entries
   int32_t n;
   int *err;
+  const int32_t *part_toff;  // one block per partition: its first tile, or null
 };
 
 // A skewed CSC matrix (hub rows found and a permuted accumulator given)

@@ -338,6 +338,33 @@ def geometric_matrix(m: int, mu: float, seed: int, dtype=np.float32) -> CSR:
     Values ~ U(-1, 1)."""
     g = rng(seed, _S_COLS)
     lens = np.minimum(g.geometric(1.0 / mu, m), m).astype(np.int64)
+    return _rows_of_lengths(m, lens, g, seed, dtype, {"kind": "geometric", "mu": mu,
+                                                      "seed": seed})
+
+
+def block_imbalance_matrix(m: int, blocks: int, heavy_len: int, ratio: float, seed: int,
+                           dtype=np.float64) -> CSR:
+    """The two-level nonzero distribution of the paper's imbalance experiment
+    (Sec. 2.3, Fig. 5): the m rows fall in `blocks` equal row blocks; rows
+    of the first half of the blocks hold heavy_len nonzeros each, rows of
+    the other half round(heavy_len / ratio) (at least 1), so that an equal
+    split of the rows gives half the blocks 1/ratio of the others' nonzeros.
+    Columns distinct, sorted and uniform over the m columns; values
+    U(-1, 1)."""
+    light = max(1, int(round(heavy_len / ratio)))
+    r = np.arange(m, dtype=np.int64)
+    blk = (r * blocks) // m  # the row block of each row, as floor(i m / blocks) cuts it
+    lens = np.where(blk < blocks // 2, heavy_len, light).astype(np.int64)
+    g = rng(seed, _S_COLS)
+    return _rows_of_lengths(m, lens, g, seed, dtype,
+                            {"kind": "block_imbalance", "blocks": blocks,
+                             "heavy_len": heavy_len, "light_len": light, "ratio": ratio,
+                             "seed": seed})
+
+
+def _rows_of_lengths(m, lens, g, seed, dtype, meta) -> CSR:
+    """Square m x m CSR whose row r has lens[r] distinct sorted uniform
+    columns (the order-statistics construction of geometric_matrix)."""
     ptr = row_ptr_from_counts(lens)
     nnz = int(ptr[-1])
     starts = ptr[:-1].astype(np.int64)
@@ -355,8 +382,7 @@ def geometric_matrix(m: int, mu: float, seed: int, dtype=np.float32) -> CSR:
     draw = np.minimum(np.floor(u * span).astype(np.int64), span - 1)
     cols = (draw + within).astype(np.int32)
     val = rng(seed, _S_VALS).uniform(-1.0, 1.0, nnz).astype(dtype)
-    return CSR(m, m, ptr, cols, val, meta={"kind": "geometric", "mu": mu,
-                                            "seed": seed})
+    return CSR(m, m, ptr, cols, val, meta=meta)
 
 
 def _batched_one(job):

@@ -25,9 +25,11 @@ COO_FORMATS = (MSREP_COO, MSREP_COO_BY_COL, MSREP_COO_UNSORTED)
 MSREP_F64, MSREP_F32, MSREP_BF16 = 0, 1, 2
 MSREP_VALIDATE = 0x1
 MSREP_PART_MERGE_PATH = 0x2
+MSREP_PART_ROW_BLOCK = 0x4
 MSREP_COMP_ALL = 0x10
 MSREP_COMP_NONE = 0x20
 MSREP_STREAM_TMA = 0x40
+MSREP_SCHED_PER_PARTITION = 0x80
 MSREP_SPMM_MAX_K = 8
 
 STATUS = {0: "OK", 1: "INVALID_ARG", 2: "BAD_MATRIX", 3: "OOM", 4: "CUDA",
