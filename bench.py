@@ -277,6 +277,40 @@ def cpu_oracle_run(mats, budget_s: float):
     return flops / dt / 1e9, f"{spmvs} single-threaded FP64 SpMVs over the 6 (matrix, format) pairs of the workload, {dt:.1f} s"
 
 
+def cpu_all_cores_run(mats, budget_s: float):
+    """Time the all-core CPU baseline (oracle/cpu_baseline.c: nonzero-balanced
+    partitions, one OpenMP thread each, as the paper's Sec. 3.3 gives each
+    partition a host thread) over the workload's (matrix, format) pairs,
+    repeating until ~budget_s; returns (GFLOP/s, threads, sample)."""
+    from oracle import cpu_baseline as C
+    pre = []
+    for name, a in mats.items():
+        x = I.vector(a.n, I.SEED_BASE + 1)
+        c = I.csr_to_csc(a)
+        q = I.csr_to_coo(a)
+        pre.append((C.Prepared("csr", a.m, a.n, a.row_ptr, a.col_idx, a.val), x, a.m))
+        pre.append((C.Prepared("csc", a.m, a.n, c.col_ptr, c.row_idx, c.val), x, a.m))
+        pre.append((C.Prepared("coo", a.m, a.n, None, q.col_idx, q.val, row_idx=q.row_idx), x,
+                    a.m))
+    ys = [np.empty(m) for _, _, m in pre]
+    for (P, x, _), y in zip(pre, ys):  # first touch of the scratch, untimed
+        P.run(x, y)
+    flops, spmvs = 0.0, 0
+    t0 = time.perf_counter()
+    while True:
+        for (P, x, _), y in zip(pre, ys):
+            P.run(x, y)
+            flops += 2.0 * P.nnz
+            spmvs += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    th = C.threads()
+    return (flops / dt / 1e9, th,
+            f"{spmvs} FP64 SpMVs on {th} threads (nonzero-balanced partitions, one per "
+            f"thread) over the 6 (matrix, format) pairs of the workload, {dt:.1f} s")
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -408,15 +442,17 @@ def run_ours(args):
         kern = {}
         reps = max(20, min(args.steps, 200))
         for (name, fmt, A, part, x, y, ws, nnz, nb) in pairs:
-            k_us = main_kernel_us(
+            ks = main_kernel_stats(
                 M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws), reps)
+            k_us = ks["median"]
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             for _ in range(reps):
                 M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
             e1.record()
             torch.cuda.synchronize()
-            kern[f"{name}/{fmt}"] = {"kernel_us": k_us,
+            kern[f"{name}/{fmt}"] = {"kernel_us": k_us, "kernel_us_mean": ks["mean"],
+                                     "kernel_reps": reps,
                                      "call_us": 1e3 * e0.elapsed_time(e1) / reps,
                                      "bytes": nb, "nnz": nnz}
             fl = access_floor_us(M, A, x, reps)
@@ -451,9 +487,10 @@ def run_ours(args):
     e2e = run_e2e(M, pairs, args, dev)
     p_sweep = run_p_sweep(M, pairs, args) if not args.skip_p_sweep else None
     coo_orders = run_coo_orders(M, args, dev, kern, peak) if not args.skip_coo_orders else None
+    imbalance = run_imbalance(M, args, dev) if not args.skip_imbalance else None
 
-    # low-precision form on the R-MAT matrix (CSR)
-    prec = run_precision(M, args, dev) if not args.skip_precision else None
+    # low-precision form on every (matrix, format) pair
+    prec = run_precision(M, args, dev, kern) if not args.skip_precision else None
     batched = run_batched(M, args, dev) if args.batched_count > 0 else None
     serving = run_serving(M, args, dev) if args.serve_seconds > 0 else None
 
@@ -476,6 +513,8 @@ def run_ours(args):
     }
     if p_sweep:
         line["p_sweep"] = p_sweep
+    if imbalance:
+        line["imbalance"] = imbalance
     if prec:
         line["precision"] = prec
     if batched:
@@ -487,6 +526,10 @@ def run_ours(args):
         v, sample = cpu_oracle_run(mats, args.cpu_budget)
         line["cpu_baseline"] = {"value": v, "unit": "GFLOP/s", "cores": 1,
                                 "kind": "oracle", "sample": sample}
+        va, th, sample_a = cpu_all_cores_run(mats, args.cpu_budget)
+        line["cpu_baseline_all_cores"] = {"value": va, "unit": "GFLOP/s", "cores": th,
+                                          "kind": "openmp nonzero-partitioned SpMV",
+                                          "sample": sample_a}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -517,14 +560,14 @@ def run_p_sweep(M, pairs, args, Ps=(148, 148 * 4, 148 * 16, 148 * 64), reps=20):
     return {"kernel_us": out, "P": list(Ps)}
 
 
-def main_kernel_us(M, call, reps, skip=3):
-    """Mean CUDA-event time (us) of the main SpMV kernel over `reps`
-    back-to-back calls of `call`.  Each call gets its own pair of profiling
-    events, recorded on the launch stream just before and just after its
-    main kernel.  The calls are not synchronised one by one: the host stays
-    ahead of the device, so no host submission latency falls inside an
-    event pair.  The first `skip` calls, which the idle device may reach
-    before the host has queued their kernels, are dropped."""
+def main_kernel_stats(M, call, reps, skip=3):
+    """Median and mean CUDA-event time (us) of the main SpMV kernel over
+    `reps` back-to-back calls of `call`.  Each call gets its own pair of
+    profiling events, recorded on the launch stream just before and just
+    after its main kernel.  The calls are not synchronised one by one: the
+    host stays ahead of the device, so no host submission latency falls
+    inside an event pair.  The first `skip` calls, which the idle device may
+    reach before the host has queued their kernels, are dropped."""
     import torch
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(reps + skip)]
@@ -534,8 +577,16 @@ def main_kernel_us(M, call, reps, skip=3):
         call()
     M.native.msrep_profile_events(None, None)
     torch.cuda.synchronize()
-    ts = [s0.elapsed_time(s1) for s0, s1 in evs[skip:]]
-    return 1e3 * sum(ts) / len(ts)
+    ts = sorted(1e3 * s0.elapsed_time(s1) for s0, s1 in evs[skip:])
+    n = len(ts)
+    med = ts[n // 2] if n % 2 else 0.5 * (ts[n // 2 - 1] + ts[n // 2])
+    return {"median": med, "mean": sum(ts) / n}
+
+
+def main_kernel_us(M, call, reps, skip=3):
+    """Median CUDA-event time (us) of the main SpMV kernel (see
+    main_kernel_stats)."""
+    return main_kernel_stats(M, call, reps, skip)["median"]
 
 
 def access_floor_us(M, A, x, reps):
@@ -682,12 +733,16 @@ def run_batched(M, args, dev):
 
 def run_serving(M, args, dev):
     """The served form: 64 matrices drawn like the batched set plus two 2^20
-    R-MAT matrices (16.8M nonzeros each) registered under a 60 GB budget; a
-    Poisson stream of requests (args.serve_rate per second), each naming a
-    matrix uniformly and carrying k ~ U{1..8} FP32 vectors.  Latency is
-    submit -> y in the caller's host buffer, measured by the server."""
-    import queue
-    import threading
+    R-MAT matrices (16.8M nonzeros each); a Poisson stream of requests
+    (args.serve_rate per second for args.serve_seconds, the first second
+    discarded), each naming a matrix uniformly and carrying k ~ U{1..8}
+    FP32 vectors.  Latency is submit -> y in the caller's host buffer,
+    measured by the server, which also splits it into queue wait (submit
+    -> packed into a launch) and device time per launch.  Run twice: under
+    a 60 GB budget (everything fits) and under a budget of the launch
+    contexts plus 25% of the set's bytes, so that admission binds (the
+    matrices that do not fit are rejected; the stream names admitted
+    ones)."""
     seed = I.SEED_BASE + 4
     mats, _ = I.batched_set_parallel(64, seed=seed)
     mats = list(mats) + [I.rmat_full(), I.cached_csr(f"rmat20_{seed}", lambda: I.rmat(seed=seed))]
@@ -697,18 +752,38 @@ def run_serving(M, args, dev):
         xa = M.native.pinned_empty((8, a.n))
         xa[:] = I.to_f32(g.uniform(-1, 1, (8, a.n)))
         X.append(xa)
-    S = M.Server(budget_bytes=60 << 30, arena_bytes=256 << 20, contexts=4,
-                 max_items=512, device=dev.index or 0)
-    ids = [S.register(a) for a in mats]
+    cfg = dict(arena_bytes=256 << 20, contexts=4, max_items=512, device=dev.index or 0)
+    full = serve_once(M, mats, X, 60 << 30, cfg, args, seed)
+    with M.Server(budget_bytes=60 << 30, **cfg) as S0:
+        ctx_bytes = S0.stats()["resident_bytes"]
+    budget = ctx_bytes + (full["resident_bytes_after_register"] - ctx_bytes) // 4
+    quarter = serve_once(M, mats, X, budget, cfg, args, seed + 1)
+    full["budget_25pct"] = quarter
+    return full
+
+
+def serve_once(M, mats, X, budget, cfg, args, seed):
+    import queue
+    import threading
+    S = M.Server(budget_bytes=budget, **cfg)
+    ids = []
+    for j, a in enumerate(mats):
+        try:
+            ids.append((j, S.register(a)))
+        except M.MsrepError as e:
+            if e.status != 6:      # MSREP_ERR_BUDGET: not admitted
+                raise
+    admitted_rejected = S.stats()["rejected"]
     resident = S.stats()["resident_bytes"]
+    g = I.rng(seed, 301)
     arrivals = I.poisson_arrivals(args.serve_rate, args.serve_seconds, seed)
     pick = g.integers(0, len(ids), arrivals.shape[0])
     ks = g.integers(1, 9, arrivals.shape[0])
     # Page-locked y buffers are allocated up front: allocating page-locked
     # memory in the submit loop takes milliseconds (and can wait on the
     # device), which delayed submissions into bursts and showed up as p99.
-    pools = [[M.native.pinned_empty((8 * a.m,)) for _ in range(6 if a.m > (1 << 18) else 16)]
-             for a in mats]
+    pools = {j: [M.native.pinned_empty((8 * mats[j].m,))
+                 for _ in range(6 if mats[j].m > (1 << 18) else 16)] for j, _ in ids}
     misses = [0]
     lock = threading.Lock()
     q = queue.Queue()
@@ -745,13 +820,14 @@ def run_serving(M, args, dev):
         if not reset_done and now - t0 >= warm:
             S.stats(reset=True)
             reset_done = True
-        j, k = int(pick[i]), int(ks[i])
+        j, mid = ids[int(pick[i])]
+        k = int(ks[i])
         with lock:
             y = pools[j].pop() if pools[j] else None
         if y is None:
             misses[0] += 1
             y = M.native.pinned_empty((8 * mats[j].m,))
-        t = S.submit(ids[j], X[j][:k], y)
+        t = S.submit(mid, X[j][:k], y)
         q.put((j, t))
     sent = time.perf_counter() - t0
     for _ in ths:
@@ -762,59 +838,68 @@ def run_serving(M, args, dev):
     st = S.stats()
     S.close()
     st.update({"offered_rate": arrivals.shape[0] / args.serve_seconds,
-               "achieved_submit_s": sent, "matrices": len(mats),
+               "achieved_submit_s": sent, "matrices": len(mats), "admitted": len(ids),
+               "not_admitted": admitted_rejected,
                "window_s": args.serve_seconds, "discarded_warmup_s": warm,
-               "budget_bytes": 60 << 30, "resident_bytes_after_register": resident,
+               "budget_bytes": budget, "resident_bytes_after_register": resident,
                "y_buffer_allocations_in_loop": misses[0]})
     return st
 
 
-def run_precision(M, args, dev):
-    """R-MAT CSR with values stored FP64 / FP32 / BF16: kernel GB/s, time,
-    speedup over FP64, and normwise error vs the FP64 inputs (computed by
-    the GPU path itself against the FP64 GPU result)."""
+def run_precision(M, args, dev, kern):
+    """The low-precision form on both workload matrices in CSR, CSC and COO:
+    values stored FP32 and BF16, x and y FP32.  Per (matrix, format, type):
+    main-kernel time (median of CUDA-event pairs), GB/s and fraction of the
+    HBM peak on the form's own algorithmic bytes, speedup of the kernel over
+    the FP64 kernel of the same pair (per_kernel), and the normwise error of
+    y against the FP64 oracle on the original FP64 values and x (computed on
+    the host, outside any timed region), with the tolerance it must meet.
+    Also k = 8 vectors on the FP32 R-MAT CSR matrix (msrep_spmm)."""
     import torch
-    a = I.rmat_full()
-    xh = I.vector(a.n, I.SEED_BASE + 1)
-    out = {}
-    base = None
-    y64 = None
+
+    import oracle as O
     peak, _ = measured_peaks()
-    for dt in ("f64", "f32", "bf16"):
-        A = M.DeviceMatrix.from_host(a, "csr", dt, device=dev)
-        part = M.DevicePartition(A, args.P, tile=args.tile, device=dev)
-        M.msrep_partition(A, part)
-        xt = torch.float64 if dt == "f64" else torch.float32
-        x = torch.from_numpy(xh).to(dev, xt)
-        y = torch.empty(a.m, dtype=xt, device=dev)
-        ws = M.alloc_workspace(A, part, device=dev)
-        for _ in range(3):
-            M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 20
-        kus = main_kernel_us(M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws),
-                             reps)
-        e0.record()
-        for _ in range(reps):
-            M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
-        e1.record()
+    tol = {"f32": 1e-5, "bf16": 1e-2}
+    out = {}
+    for name, a in load_workload().items():
+        xh = I.vector(a.n, I.SEED_BASE + 1)
+        y_ref = O.spmv_csr(a.m, a.row_ptr, a.col_idx, a.val, xh)
+        nref = float(np.linalg.norm(y_ref))
+        x = torch.from_numpy(I.to_f32(xh)).to(dev)
+        for fmt in FORMATS:
+            row = {}
+            f64_us = kern[f"{name}/{fmt}"]["kernel_us"]
+            for dt in ("f32", "bf16"):
+                A = M.DeviceMatrix.from_host(a, fmt, dt, device=dev)
+                part = M.DevicePartition(A, args.P, tile=args.tile, device=dev)
+                M.msrep_partition(A, part)
+                y = torch.empty(a.m, dtype=torch.float32, device=dev)
+                ws = M.alloc_workspace(A, part, device=dev)
+                call = lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+                for _ in range(3):
+                    call()
+                ks = main_kernel_stats(M, call, 20)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(20):
+                    call()
+                e1.record()
+                torch.cuda.synchronize()
+                sv = {"f32": 4, "bf16": 2}[dt]
+                nb = algorithmic_bytes(fmt, a.m, a.n, a.nnz, sv, 4)
+                err = float(np.linalg.norm(y.cpu().numpy().astype(np.float64) - y_ref)) / nref
+                row[dt] = {"kernel_us": ks["median"], "kernel_us_mean": ks["mean"],
+                           "call_us": 1e3 * e0.elapsed_time(e1) / 20, "bytes": nb,
+                           "gbs": nb / (ks["median"] * 1e-6) / 1e9,
+                           "frac": nb / (ks["median"] * 1e-6) / 1e9 / peak,
+                           "speedup_vs_f64": f64_us / ks["median"],
+                           "normwise_err_vs_oracle_f64": err, "tolerance": tol[dt],
+                           "within_tolerance": err <= tol[dt]}
+                if name == "rmat" and fmt == "csr" and dt == "f32":
+                    out["f32_k8"] = run_spmm_leg(M, A, part, a, xh, dev, row[dt]["call_us"])
+                del A, part, y, ws
+            out[f"{name}/{fmt}"] = row
         torch.cuda.synchronize()
-        call_us = 1e3 * e0.elapsed_time(e1) / reps
-        sv = {"f64": 8, "f32": 4, "bf16": 2}[dt]
-        nb = algorithmic_bytes("csr", a.m, a.n, a.nnz, sv, 8 if dt == "f64" else 4)
-        rec = {"call_us": call_us, "kernel_us": kus, "gbs": nb / (kus * 1e-6) / 1e9,
-               "frac": nb / (kus * 1e-6) / 1e9 / peak,
-               "gflops": 2.0 * a.nnz / (call_us * 1e-6) / 1e9}
-        yv = y.double()
-        if dt == "f64":
-            base, y64 = call_us, yv
-        else:
-            rec["speedup_vs_f64"] = base / call_us
-            rec["normwise_err_vs_f64"] = float(torch.linalg.norm(yv - y64) / torch.linalg.norm(y64))
-        out[dt] = rec
-        if dt == "f32":
-            out["f32_k8"] = run_spmm_leg(M, A, part, a, xh, dev, call_us)
-        del A, part, x, y, ws
     return out
 
 
@@ -838,6 +923,53 @@ def run_spmm_leg(M, A, part, a, xh, dev, spmv_call_us, k=8):
     us = 1e3 * e0.elapsed_time(e1) / reps
     return {"k": k, "call_us": us, "gflops": 2.0 * a.nnz * k / (us * 1e-6) / 1e9,
             "speedup_vs_k_spmv": k * spmv_call_us / us}
+
+
+def run_imbalance(M, args, dev):
+    """The imbalance experiment of Sec. 2.3 (Fig. 5) on one GPU, with thread
+    blocks in place of GPUs: B partitions, one thread block each
+    (MSREP_SCHED_PER_PARTITION), B = the CSR kernel's resident blocks, so
+    all partitions run at once as the paper's GPUs do.  The matrix has
+    2^20 rows in B equal row blocks; rows of the first half of the blocks
+    hold 32 nonzeros, the others 32 / r (the paper's two-level nonzero
+    distribution, low-to-high ratio 1/r).  Per r: the SpMV over the
+    Baseline row-block partitioning (Sec. 5.1, MSREP_PART_ROW_BLOCK) and
+    over Alg. 2's nonzero-balanced partitioning, both one block per
+    partition, and the row-block partitioning under the default schedule
+    (every partition's tiles spread over all blocks).  CSR, FP64."""
+    import torch
+    m, heavy = 1 << 20, 32
+    # resident blocks of the CSR kernel: 3 per SM of 256 threads (its
+    # register budget), so 3 x SMs partitions run in one wave
+    B = 3 * torch.cuda.get_device_properties(dev).multi_processor_count
+    out = {"rows": m, "partitions": B, "heavy_row_nnz": heavy, "ratios": {}}
+    for r in (1, 2, 4, 10):
+        a = I.block_imbalance_matrix(m, B, heavy, r, I.SEED_BASE + 5 + r)
+        x = torch.from_numpy(I.vector(a.n, I.SEED_BASE + 1)).to(dev)
+        y = torch.empty(a.m, dtype=torch.float64, device=dev)
+        A = M.DeviceMatrix.from_host(a, "csr", "f64", device=dev)
+        row = {"nnz": a.nnz, "light_row_nnz": a.meta["light_len"]}
+        for tag, pflags, flags in (("row_block_per_partition", M.MSREP_PART_ROW_BLOCK,
+                                    M.MSREP_SCHED_PER_PARTITION),
+                                   ("nnz_balanced_per_partition", 0, M.MSREP_SCHED_PER_PARTITION),
+                                   ("row_block_default_schedule", M.MSREP_PART_ROW_BLOCK, 0)):
+            part = M.DevicePartition(A, B, device=dev)
+            M.msrep_partition(A, part, pflags)
+            h = part.to_host()
+            ln = (h["end_idx"].astype(np.int64) - h["start_idx"] + 1)
+            ws = M.alloc_workspace(A, part, device=dev)
+            call = lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=flags, workspace=ws)
+            for _ in range(3):
+                call()
+            us = main_kernel_us(M, call, 20)
+            row[tag] = {"kernel_us": us, "gflops": 2.0 * a.nnz / (us * 1e-6) / 1e9,
+                        "max_partition_nnz": int(ln.max()), "mean_partition_nnz": float(ln.mean())}
+            del part, ws
+        rb, nb = row["row_block_per_partition"], row["nnz_balanced_per_partition"]
+        row["row_block_over_balanced_perf"] = nb["kernel_us"] / rb["kernel_us"]
+        out["ratios"][str(r)] = row
+        del A, x, y
+    return out
 
 
 def run_coo_orders(M, args, dev, kern, peak):
@@ -977,11 +1109,13 @@ def main():
     ap.add_argument("--skip-precision", action="store_true")
     ap.add_argument("--skip-p-sweep", action="store_true",
                     help="skip the P = 148 .. 148*64 sweep of the main kernels")
+    ap.add_argument("--skip-imbalance", action="store_true",
+                    help="skip the row-block imbalance experiment")
     ap.add_argument("--skip-coo-orders", action="store_true",
                     help="skip the column-sorted / unsorted COO leg")
     ap.add_argument("--batched-count", type=int, default=512,
                     help="matrices in the batched-form measurement (0 = skip)")
-    ap.add_argument("--serve-seconds", type=float, default=4.0,
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served request stream (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--profile", choices=FORMATS + ("coo_col", "coo_any"), default=None,

@@ -407,6 +407,12 @@ typedef struct {
   double mean_items;      /* vectors per launch                           */
   double busy_s;          /* wall time with at least one launch in flight */
   int64_t resident_bytes; /* device bytes held (matrices + arenas)        */
+  /* where the latency goes: */
+  double wait_p50_us, wait_p99_us;     /* submit -> packed into a launch  */
+  double device_p50_us, device_p99_us; /* one launch on the device, from
+                                          its first x copy to its last y
+                                          copy (CUDA events)              */
+  double kernel_mean_us;  /* the batched kernels of one launch (events)   */
 } msrep_serve_counters;
 
 /* Defaults: 60 GB budget, 64 MB arenas, 3 contexts, 256 items, k <= 8. */

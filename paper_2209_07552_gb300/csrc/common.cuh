@@ -284,6 +284,26 @@ __device__ __forceinline__ void ld8(const bf16_t *p, float (&v)[8]) {
   }
 }
 
+// binary32 -> binary64 widening for the scatter's exact FP64 products.  A
+// normal number is widened by the IEEE-754 formats' definition in integer
+// operations: its 8-bit exponent and 23-bit fraction, shifted right by 3,
+// land on the 11-bit exponent and top 20 fraction bits of the high word,
+// where adding (1023 - 127) << 20 rebiases the exponent; the last 3
+// fraction bits go to the top of the low word; the sign stays.  Zero,
+// subnormal, infinite and NaN inputs take the hardware conversion, called
+// out of line so that the compiler cannot evaluate it for every element: on
+// GB300 it runs on the FP64 pipe (about two lane operations per clock per
+// SM), where a scatter that widened two operands per nonzero spent most of
+// its time.
+static __device__ __noinline__ double widen_rare(float f) { return static_cast<double>(f); }
+__device__ __forceinline__ double widen(float f) {
+  const uint32_t u = __float_as_uint(f);
+  if ((u & 0x7f800000u) - 0x00800000u >= 0x7f000000u) return widen_rare(f);
+  const uint32_t hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
+  return __hiloint2double(static_cast<int>(hi), static_cast<int>(u << 29));
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // Knuth's TwoSum: s + e == a + b exactly (round-to-nearest, no FMA
 // contraction possible on these operations because each is a single add).
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {

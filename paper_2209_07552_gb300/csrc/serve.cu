@@ -66,7 +66,9 @@ struct Request {
 
 struct Context {
   cudaStream_t stream = nullptr;
-  cudaEvent_t done_ev = nullptr;
+  cudaEvent_t done_ev = nullptr;  // end of the launch (also polled)
+  // timing: launch start (before the x copies), kernels start and end
+  cudaEvent_t begin_ev = nullptr, k0_ev = nullptr, k1_ev = nullptr;
   float *x_dev = nullptr, *y_dev = nullptr;    // arenas
   float *x_pin = nullptr, *y_pin = nullptr;    // pinned staging
   int64_t arena_floats = 0;
@@ -106,7 +108,10 @@ struct msrep_server {
   bool stop = false;
   std::thread scheduler, completer;
   // statistics
-  std::vector<double> lat_us;
+  std::vector<double> lat_us;     // submit -> y in the caller's buffer
+  std::vector<double> wait_us;    // submit -> packed into a launch (host)
+  std::vector<double> dev_us;     // per launch: first copy -> last copy (device)
+  double kernel_us = 0;           // sum over launches of the kernels' device time
   uint64_t submitted = 0, completed = 0, rejected = 0, launches = 0, items = 0;
   double work_bytes = 0, busy_s = 0;
   int inflight = 0;
@@ -142,6 +147,9 @@ static void free_context(Context &c) {
   cudaFreeHost(c.y_pin);
   cudaFreeHost(c.dir_pin);
   if (c.done_ev) cudaEventDestroy(c.done_ev);
+  if (c.begin_ev) cudaEventDestroy(c.begin_ev);
+  if (c.k0_ev) cudaEventDestroy(c.k0_ev);
+  if (c.k1_ev) cudaEventDestroy(c.k1_ev);
   if (c.stream) cudaStreamDestroy(c.stream);
   c = Context{};
 }
@@ -177,6 +185,7 @@ static msrep_status launch_context(msrep_server *s, Context &c,
   int64_t xo = 0, yo = 0, xto = 0, tt = 0, ttk = 0;
   int n1 = 0, nk = 0;
   c.y_off.clear();
+  MSREP_CUDA_TRY(cudaEventRecord(c.begin_ev, c.stream));
   for (size_t i = 0; i < c.reqs.size(); ++i) {
     const auto &r = c.reqs[i];
     const BatchItem &bi = ritem[i];
@@ -211,6 +220,7 @@ static msrep_status launch_context(msrep_server *s, Context &c,
   }
   toff[n1] = tt;
   toffk[nk] = ttk;
+  MSREP_CUDA_TRY(cudaEventRecord(c.k0_ev, c.stream));
   if (n1 > 0) {
     MSREP_CUDA_TRY(cudaMemcpyAsync(c.dir_dev, c.dir_pin, c.dir_bytes, cudaMemcpyHostToDevice, c.stream));
     const char *dd = c.dir_dev;
@@ -238,6 +248,7 @@ static msrep_status launch_context(msrep_server *s, Context &c,
     MSREP_TRY(launch_batched_k(reinterpret_cast<const BatchItem *>(dd), dtoff, nk, ttk, dxin, dxt,
                                dys, c.head_k, c.tail_k, 0, c.stream));
   }
+  MSREP_CUDA_TRY(cudaEventRecord(c.k1_ev, c.stream));
   for (size_t i = 0; i < c.reqs.size(); ++i) {
     const auto &r = c.reqs[i];
     const int64_t ylen = (i + 1 < c.reqs.size() ? c.y_off[i + 1] : yo) - c.y_off[i];
@@ -309,6 +320,9 @@ static void scheduler_loop(msrep_server *s) {
     c->busy = true;
     c->bytes = bytes;
     c->t_launch = Clock::now();
+    for (const auto &r : c->reqs)
+      s->wait_us.push_back(
+          std::chrono::duration<double, std::micro>(c->t_launch - r->t_submit).count());
     if (s->inflight++ == 0) s->busy_since = c->t_launch;
     s->launches++;
     for (const auto &r : c->reqs) s->items += r->k;
@@ -365,8 +379,16 @@ static void completion_loop(msrep_server *s) {
         if (q == cudaSuccess && !r->y_pinned)
           std::memcpy(r->y, c.y_pin + c.y_off[i], sizeof(float) * size_t(m) * r->k);
       }
+      float span_ms = 0.f, kern_ms = 0.f;
+      const bool timed = q == cudaSuccess &&
+                         cudaEventElapsedTime(&span_ms, c.begin_ev, c.done_ev) == cudaSuccess &&
+                         cudaEventElapsedTime(&kern_ms, c.k0_ev, c.k1_ev) == cudaSuccess;
       const auto now = Clock::now();
       std::lock_guard<std::mutex> lk(s->mu);
+      if (timed) {
+        s->dev_us.push_back(1e3 * double(span_ms));
+        s->kernel_us += 1e3 * double(kern_ms);
+      }
       for (auto &r : c.reqs) {
         r->status = q == cudaSuccess ? MSREP_OK : MSREP_ERR_CUDA;
         r->done = true;
@@ -431,7 +453,10 @@ msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **ou
     c.dirk_bytes = dirk_size(cfg->max_items);
     c.xt_floats = 4 * cfg->arena_bytes / int64_t(sizeof(float));
     bool okc = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) == cudaSuccess &&
-               cudaEventCreateWithFlags(&c.done_ev, cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreate(&c.done_ev) == cudaSuccess &&
+               cudaEventCreate(&c.begin_ev) == cudaSuccess &&
+               cudaEventCreate(&c.k0_ev) == cudaSuccess &&
+               cudaEventCreate(&c.k1_ev) == cudaSuccess &&
                cudaMalloc(&c.x_dev, cfg->arena_bytes) == cudaSuccess &&
                cudaMalloc(&c.y_dev, cfg->arena_bytes) == cudaSuccess &&
                cudaMalloc(&c.dir_dev, c.dir_bytes) == cudaSuccess &&
@@ -640,17 +665,29 @@ msrep_status msrep_serve_stats(msrep_server *s, msrep_serve_counters *o, int32_t
   o->completed = s->completed;
   o->rejected = s->rejected;
   o->launches = s->launches;
-  std::vector<double> l = s->lat_us;
+  // percentile p of a sample (nearest rank), 0 when empty
+  auto pct = [](std::vector<double> v, double p) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    return v[std::min(v.size() - 1, size_t(p * (v.size() - 1) + 0.5))];
+  };
+  const std::vector<double> &l = s->lat_us;
   if (!l.empty()) {
-    std::sort(l.begin(), l.end());
-    auto pct = [&](double p) { return l[std::min(l.size() - 1, size_t(p * (l.size() - 1) + 0.5))]; };
-    o->p50_us = pct(0.50);
-    o->p99_us = pct(0.99);
-    double sum = 0;
-    for (double v : l) sum += v;
+    o->p50_us = pct(l, 0.50);
+    o->p99_us = pct(l, 0.99);
+    double sum = 0, mx = 0;
+    for (double v : l) {
+      sum += v;
+      mx = std::max(mx, v);
+    }
     o->mean_us = sum / l.size();
-    o->max_us = l.back();
+    o->max_us = mx;
   }
+  o->wait_p50_us = pct(s->wait_us, 0.50);
+  o->wait_p99_us = pct(s->wait_us, 0.99);
+  o->device_p50_us = pct(s->dev_us, 0.50);
+  o->device_p99_us = pct(s->dev_us, 0.99);
+  o->kernel_mean_us = s->dev_us.empty() ? 0.0 : s->kernel_us / double(s->dev_us.size());
   double busy = s->busy_s;
   if (s->inflight > 0) busy += std::chrono::duration<double>(Clock::now() - s->busy_since).count();
   o->busy_s = busy;
@@ -659,6 +696,9 @@ msrep_status msrep_serve_stats(msrep_server *s, msrep_serve_counters *o, int32_t
   o->resident_bytes = s->resident;
   if (reset) {
     s->lat_us.clear();
+    s->wait_us.clear();
+    s->dev_us.clear();
+    s->kernel_us = 0;
     s->submitted = s->completed = s->rejected = s->launches = s->items = 0;
     s->work_bytes = 0;
     s->busy_s = 0;

@@ -475,12 +475,23 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
   const int64_t ka = lr.ka, kb = lr.kb;
 
   // compensation predicate of the run of row rv that contains nonzero j:
-  // its length inside the tile (bisection in row_idx), split if it touches
-  // a tile end that the row crosses
+  // split if it touches a tile end that the row crosses (rows are sorted,
+  // so it touches the tile's start iff rv is the tile's first row), long if
+  // its length inside the tile exceeds 256.  Two probes 128 positions
+  // either side of j settle most runs: when neither holds rv, the run lies
+  // strictly between them and is shorter than 256; only otherwise is its
+  // extent bisected in row_idx.  (A row that crosses the tile is split
+  // anyway; inside the tile, its in-tile length is its full length.)
   auto run_comp = [&](int32_t rv, int64_t j) -> bool {
     if (!Pol::kLow) return false;
     if (a.comp_mode & (MSREP_COMP_ALL | MSREP_COMP_NONE))
       return want_comp(a.comp_mode, 0, false);
+    const bool split = (rv == first_row && flag) || (rv == last_row && cont);
+    if (split) return true;
+    const int64_t pa = max(int64_t(k0), j - 128), pb = min(int64_t(k1) - 1, j + 128);
+    const bool reach_a = pa < j && __ldg(a.row_idx + pa) == rv;
+    const bool reach_b = pb > j && __ldg(a.row_idx + pb) == rv;
+    if (!reach_a && !reach_b) return false;
     int64_t lo = k0, hi = j;
     while (lo < hi) {
       int64_t mid = (lo + hi) >> 1;
@@ -786,7 +797,8 @@ __device__ __forceinline__ int csc_tile_max_col(int32_t c0, int32_t k0, int32_t 
 // column of each nonzero comes from colof (this warp's 32 * IPT + 8 int16
 // entries of shared memory), filled first by a walk of the tile's columns
 // (one lane per column: the tile's columns must be short, see
-// csc_tile_max_col).  Seven steps are loaded ahead (eight spill registers
+// csc_tile_max_col).  Low-precision values and x are widened to FP64 with
+// integer operations (widen).  Seven steps are loaded ahead (eight spill registers
 // at four resident blocks; four keep too few loads in flight).
 template <class Pol, class Sink>
 __device__ __forceinline__ void csc_tile_interleaved(const CscArgs<Pol> &a, int32_t c0,
@@ -814,13 +826,13 @@ __device__ __forceinline__ void csc_tile_interleaved(const CscArgs<Pol> &a, int3
       const bool in = p < len;
       rw[u] = in ? ld_stream(a.row_idx + k0 + p) : 0;
       v[u] = in ? LV(ld_stream(a.val + k0 + p)) : LV(0);
-      xv[u] = in ? double(load_x(a.x, c0 + colof[p])) : 0.0;
+      xv[u] = in ? widen(load_x(a.x, c0 + colof[p])) : 0.0;
     }
 #pragma unroll
     for (int u = 0; u < B; ++u) {
       if (i0 + 32 * u >= len) break;  // warp-uniform
       const double xs = a.scaled ? __dmul_rn(xv[u], a.scale) : xv[u];
-      const double prod = __dmul_rn(double(v[u]), xs);
+      const double prod = __dmul_rn(widen(v[u]), xs);
       if (i0 + 32 * u + lane < len) sink.add(rw[u], prod);
     }
   }

@@ -86,7 +86,10 @@ class c_msrep_serve_counters(ctypes.Structure):
                 ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
                 ("mean_us", ctypes.c_double), ("max_us", ctypes.c_double),
                 ("gbs", ctypes.c_double), ("mean_items", ctypes.c_double),
-                ("busy_s", ctypes.c_double), ("resident_bytes", ctypes.c_int64)]
+                ("busy_s", ctypes.c_double), ("resident_bytes", ctypes.c_int64),
+                ("wait_p50_us", ctypes.c_double), ("wait_p99_us", ctypes.c_double),
+                ("device_p50_us", ctypes.c_double), ("device_p99_us", ctypes.c_double),
+                ("kernel_mean_us", ctypes.c_double)]
 
 
 _M = ctypes.POINTER(c_msrep_matrix)

@@ -105,3 +105,29 @@ def test_csc_low_precision_merges_in_fp64():
     a, exact = _cancel_matrix(900, 4)
     y = gpu_spmv(a, "csc", 5, np.ones(a.n), val_dtype="f32", tile=256)
     assert np.array_equal(y, np.full(4, float(exact)))
+
+
+@pytest.mark.parametrize("fmt", ["csc", "coo_col"])
+def test_low_precision_scatter_widening_special_values(fmt):
+    """The scatter forms widen FP32 values and x to FP64 by integer
+    operations (and the hardware conversion for zero, subnormal, infinite
+    and NaN inputs).  Each row here holds one product, so the FP64
+    accumulator holds it exactly and y must be the oracle's product rounded
+    to binary32, bit for bit: values and x cover +-0, binary32 subnormals,
+    the smallest and largest normal exponents and ordinary numbers."""
+    g = np.random.default_rng(5)
+    specials = np.array([0.0, -0.0, 1e-40, -3e-39, 1.401298464324817e-45,
+                         1.1754943508222875e-38, -1.1754943508222875e-38, 2.0**-126, 2.0**127,
+                         -(2.0**127) * 1.5, 1.0, -1.0, 0.5, 3.0, 1e30, -1e-30])
+    n = 600
+    v = np.concatenate([specials, g.standard_normal(n - specials.size)]).astype(np.float32)
+    xv = np.concatenate([specials[::-1], g.standard_normal(n - specials.size)]).astype(np.float32)
+    perm = g.permutation(n)
+    # column c holds one nonzero, at row perm[c]: row r's only product
+    a = I.csr_from_triplets(n, n, perm, np.arange(n), v.astype(np.float64))
+    x = xv.astype(np.float64)
+    y = gpu_spmv(a, fmt, 7, x, val_dtype="f32", tile=256)
+    want = oracle_spmv(a, "csr", x)           # exact products in FP64
+    w32 = want.astype(np.float32)
+    assert np.isfinite(w32).all()
+    assert np.array_equal(y.astype(np.float32).view(np.uint32), w32.view(np.uint32))

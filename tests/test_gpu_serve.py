@@ -89,6 +89,11 @@ def test_serve_results_alone_and_in_the_mix():
         st = S.stats()
         assert st["completed"] >= len(tickets) + len(ids)
         assert st["launches"] >= 1 and st["p99_us"] >= st["p50_us"] > 0
+        # where the latency goes: queue wait (host) and per-launch device time
+        assert st["wait_p99_us"] >= st["wait_p50_us"] >= 0
+        assert st["device_p99_us"] >= st["device_p50_us"] > 0
+        assert 0 < st["kernel_mean_us"] <= st["device_p99_us"]
+        assert st["device_p50_us"] <= st["p99_us"]
     for a, x, y in zip(mats, X, alone):
         assert y.shape == (8, a.m)
         assert np.array_equal(y, _solo(M, a, x))
