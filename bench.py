@@ -752,17 +752,31 @@ def run_serving(M, args, dev):
         xa = M.native.pinned_empty((8, a.n))
         xa[:] = I.to_f32(g.uniform(-1, 1, (8, a.n)))
         X.append(xa)
-    cfg = dict(arena_bytes=256 << 20, contexts=4, max_items=512, device=dev.index or 0)
-    full = serve_once(M, mats, X, 60 << 30, cfg, args, seed)
+    cfg = dict(arena_bytes=256 << 20, contexts=args.serve_contexts, max_items=512,
+               device=dev.index or 0)
+    # Page-locked y buffers for every matrix, carved from one slab allocated
+    # up front (16 per matrix, each large enough for 8 vectors):
+    # allocating page-locked memory while submitting takes milliseconds (and
+    # can wait on the device), which bunched submissions and inflated p99.
+    per = 16
+    sizes = [8 * a.m for a in mats]
+    slab = M.native.pinned_empty((per * sum(sizes),))
+    pools, o = [], 0
+    for sz in sizes:
+        pools.append([slab[o + i * sz:o + (i + 1) * sz] for i in range(per)])
+        o += per * sz
+    full = serve_once(M, mats, X, 60 << 30, cfg, args, seed, pools)
     with M.Server(budget_bytes=60 << 30, **cfg) as S0:
         ctx_bytes = S0.stats()["resident_bytes"]
     budget = ctx_bytes + (full["resident_bytes_after_register"] - ctx_bytes) // 4
-    quarter = serve_once(M, mats, X, budget, cfg, args, seed + 1)
+    quarter = serve_once(M, mats, X, budget, cfg, args, seed + 1, pools)
     full["budget_25pct"] = quarter
+    full["y_buffers_per_matrix"] = per
+    del slab
     return full
 
 
-def serve_once(M, mats, X, budget, cfg, args, seed):
+def serve_once(M, mats, X, budget, cfg, args, seed, all_pools):
     import queue
     import threading
     S = M.Server(budget_bytes=budget, **cfg)
@@ -779,11 +793,7 @@ def serve_once(M, mats, X, budget, cfg, args, seed):
     arrivals = I.poisson_arrivals(args.serve_rate, args.serve_seconds, seed)
     pick = g.integers(0, len(ids), arrivals.shape[0])
     ks = g.integers(1, 9, arrivals.shape[0])
-    # Page-locked y buffers are allocated up front: allocating page-locked
-    # memory in the submit loop takes milliseconds (and can wait on the
-    # device), which delayed submissions into bursts and showed up as p99.
-    pools = {j: [M.native.pinned_empty((8 * mats[j].m,))
-                 for _ in range(6 if mats[j].m > (1 << 18) else 16)] for j, _ in ids}
+    pools = {j: list(all_pools[j]) for j, _ in ids}
     misses = [0]
     lock = threading.Lock()
     q = queue.Queue()
@@ -1118,6 +1128,8 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the served request stream (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=20000.0)
+    ap.add_argument("--serve-contexts", type=int, default=4,
+                    help="launch contexts of the server (launches in flight at once)")
     ap.add_argument("--profile", choices=FORMATS + ("coo_col", "coo_any"), default=None,
                     help="run only a short fixed case (for ncu captures)")
     ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")
