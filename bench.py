@@ -727,7 +727,8 @@ def run_batched(M, args, dev):
             "gflops": 2.0 * nnz / (us * 1e-6) / 1e9,
             "gbs": nbytes / (us * 1e-6) / 1e9, "frac": nbytes / (us * 1e-6) / 1e9 / peak,
             "bytes_per_launch": nbytes, "total_tiles": B.total_tiles,
-            "tune": {str(b): tiles[b] for b in used}, "gen_s": gen_s, "autotune_s": tune_s,
+            "tune": {str(b): tiles[b] for b in used}, "cta_threads": int(tune.cta_threads),
+            "gen_s": gen_s, "autotune_s": tune_s,
             "graph": "one CUDA graph: persistent batched kernel + fix-up"}
 
 

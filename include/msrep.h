@@ -312,12 +312,16 @@ msrep_status msrep_spmm(const msrep_matrix *A, const msrep_partition *part, int3
 /* ---------------------------------------------------------------------- */
 
 /* Tuning table: a matrix falls in bucket floor(log2(max(nnz, 1))); bucket
- * b uses thread-block tile tile[b] (0 = default) and np = ceil(nnz /
- * part_nnz[b]) partitions (part_nnz[b] = 0: one partition). */
+ * b uses warp tile tile[b] (0 = default) and np = ceil(nnz / part_nnz[b])
+ * partitions (part_nnz[b] = 0: one partition).  One launch runs every
+ * matrix of a batch, so the thread-block shape is one per batch:
+ * cta_threads threads per block (128, 256 or 512; 0 = 256). */
 #define MSREP_TUNE_BUCKETS 32
 typedef struct {
   int32_t tile[MSREP_TUNE_BUCKETS];
   int64_t part_nnz[MSREP_TUNE_BUCKETS];
+  int32_t cta_threads;
+  int32_t reserved;
 } msrep_tune_table;
 
 /* A prepared batch (filled by msrep_batch_prepare; host memory, owned by
@@ -332,6 +336,8 @@ typedef struct {
   int64_t dev_bytes;
   int64_t items_off;   /* byte offsets of the directory in dev     */
   int64_t toff_off;
+  int32_t cta_threads; /* threads per block of the launch          */
+  int32_t max_tile;    /* largest warp tile of the batch           */
 } msrep_batch;
 
 /* Host only: the library's default table (default tile, one partition). */
@@ -365,11 +371,14 @@ msrep_status msrep_spmv_batched(const msrep_batch *B, const void *const *xs,
 msrep_status msrep_autotune_scratch_size(int32_t count, const msrep_matrix *As,
                                          int64_t *bytes);
 
-/* Project-written autotuner: for every size bucket present in As, times
- * msrep_spmv on up to three of the bucket's largest matrices for each
- * candidate (tile 256/512/1024 x part_nnz 0/2^14/2^18) with CUDA events and
- * keeps the fastest; absent buckets keep the default.  xs/ys: HOST arrays
- * of device pointers (ys are overwritten).  Syncs `stream`. */
+/* Project-written autotuner.  First, for every size bucket present in As,
+ * it times msrep_spmv on up to three of the bucket's largest matrices for
+ * each candidate (tile 256/512/1024 x part_nnz 0/2^14/2^18) with CUDA
+ * events and keeps the fastest; absent buckets keep the default.  Then it
+ * prepares the whole batch with that table in the scratch and times
+ * msrep_spmv_batched with 128, 256 and 512 threads per block, keeping the
+ * fastest as cta_threads.  xs/ys: HOST arrays of device pointers (ys are
+ * overwritten).  Syncs `stream`. */
 msrep_status msrep_autotune(int32_t count, const msrep_matrix *As,
                             const void *const *xs, void *const *ys,
                             void *scratch, int64_t scratch_bytes,

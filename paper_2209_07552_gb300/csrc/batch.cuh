@@ -31,11 +31,13 @@ constexpr int kBatchWidth = 8;
 // Persistent batched kernel + fix-up over `count` items whose tiles are
 // numbered toff[j] .. toff[j+1]-1 (toff has count+1 entries, device).
 // xs, ys: device arrays of count device pointers; head, tail: device
-// arrays of total_tiles doubles.  Asynchronous on st.
+// arrays of total_tiles doubles.  cta_threads: 128, 256 or 512 threads
+// per block; max_tile: the largest tile of any item.  Asynchronous on st.
 msrep_status launch_batched(const BatchItem *items, const int64_t *toff, int count,
                             int64_t total_tiles, int32_t val_dtype, const void *const *xs,
                             void *const *ys, double *head, double *tail, double alpha,
-                            double beta, unsigned flags, cudaStream_t st);
+                            double beta, unsigned flags, cudaStream_t st,
+                            int cta_threads = 256, int max_tile = 1024);
 
 // Batched k-vector form (FP32 values and vectors): item j carries k_j <= 8
 // vectors, xin[j] = its k_j x vectors of n_j values each (device),

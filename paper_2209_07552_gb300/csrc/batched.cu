@@ -9,6 +9,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -22,9 +23,16 @@ int32_t effective_tile(int32_t tile);
 int *kernel_err_ptr();
 
 
-constexpr int kBWarps = 8;
-constexpr int kBThreads = 32 * kBWarps;
-constexpr int kBMaxIPT = 32;  // the largest tile (1024) fits the warp buffers
+// Thread-block shapes of the batched kernel (warps per block) and the
+// resident blocks asked of the register allocator for each: the same budget
+// of about 80 registers a thread as the single-matrix CSR kernel for 4 and
+// 8 warps (24 warps per SM); 16-warp blocks get one block per SM and more
+// registers.  The autotuner picks one shape per batch.
+template <int W>
+struct BShape {
+  static constexpr int kThreads = 32 * W;
+  static constexpr int kMinBlocks = W == 4 ? 6 : W == 8 ? 3 : 1;
+};
 
 // matrix that owns global tile g: last j with toff[j] <= g
 __device__ __forceinline__ int owner_item(const int64_t *toff, int count, int64_t g) {
@@ -39,21 +47,19 @@ __device__ __forceinline__ int owner_item(const int64_t *toff, int count, int64_
   return lo;
 }
 
-// Three resident blocks per SM (80 registers a thread), as for the
-// single-matrix CSR kernel.
-template <class Pol>
-__global__ void __launch_bounds__(kBThreads, 3) batched_csr(const BatchItem *items,
-                                                         const int64_t *toff, int count,
-                                                         const void *const *xs, void *const *ys,
-                                                         double *head, double *tail, double alpha,
-                                                         double beta, int finish,
-                                                         unsigned comp_mode, int *err) {
-  __shared__ int32_t s_rp[kBWarps][32 * kBMaxIPT + 8];
+// W warps per block; dynamic shared memory: per warp the row pointers of
+// its tile, rp_cap = largest tile + 8 entries.
+template <class Pol, int W>
+__global__ void __launch_bounds__(BShape<W>::kThreads, BShape<W>::kMinBlocks)
+    batched_csr(const BatchItem *items, const int64_t *toff, int count, const void *const *xs,
+                void *const *ys, double *head, double *tail, double alpha, double beta,
+                int finish, unsigned comp_mode, int *err, int rp_cap) {
+  extern __shared__ __align__(16) int32_t s_rp_all[];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int32_t *s_rp = s_rp_all + wid * rp_cap;
   const int64_t total = __ldg(toff + count);
   int j = 0;
-  for (int64_t g = int64_t(blockIdx.x) * kBWarps + wid; g < total;
-       g += int64_t(gridDim.x) * kBWarps) {
+  for (int64_t g = int64_t(blockIdx.x) * W + wid; g < total; g += int64_t(gridDim.x) * W) {
     // a warp's tiles increase: step forward from the previous owner, and
     // search only when the tile is more than a few matrices ahead
     int step = 0;
@@ -85,9 +91,9 @@ __global__ void __launch_bounds__(kBThreads, 3) batched_csr(const BatchItem *ite
     const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
     const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
     const int32_t rend = min(r1 + 2, a.m + 1);
-    for (int32_t r = r0 + lane; r < rend; r += 32) s_rp[wid][r - r0] = __ldg(a.row_ptr + r);
+    for (int32_t r = r0 + lane; r < rend; r += 32) s_rp[r - r0] = __ldg(a.row_ptr + r);
     __syncwarp();
-    csr_tile_compute<Pol>(a, b, r0, k0, r1, k1, s_rp[wid], Seg<int32_t>{a.col_idx, 0},
+    csr_tile_compute<Pol>(a, b, r0, k0, r1, k1, s_rp, Seg<int32_t>{a.col_idx, 0},
                           Seg<typename Pol::V>{a.val, 0}, it.nnz, GlobalSrc{});
     __syncwarp();
   }
@@ -178,45 +184,76 @@ static size_t batch_bytes(int32_t count, const msrep_matrix *As, const msrep_tun
 msrep_status launch_batched(const BatchItem *items, const int64_t *toff, int count,
                             int64_t total_tiles, int32_t val_dtype, const void *const *xs,
                             void *const *ys, double *head, double *tail, double alpha,
-                            double beta, unsigned flags, cudaStream_t st) {
+                            double beta, unsigned flags, cudaStream_t st, int cta_threads,
+                            int max_tile) {
   int *err = kernel_err_ptr();
   if (!err) return fail(MSREP_ERR_CUDA, "cannot resolve the device error word");
+  if (cta_threads != 128 && cta_threads != 256 && cta_threads != 512)
+    return fail(MSREP_ERR_INVALID_ARG, "cta_threads must be 128, 256 or 512 (got %d)",
+                cta_threads);
+  if (!tile_supported(max_tile))
+    return fail(MSREP_ERR_INVALID_ARG, "unsupported largest tile %d", max_tile);
   const int finish = finish_mode(alpha, beta);
   const unsigned comp = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
   const int64_t T = total_tiles;
   if (T == 0) return MSREP_OK;
   const int sms = sm_count();
-  auto launch = [&](auto kern, auto fix) -> msrep_status {
-    // resident blocks per device, after the smallest carveout for 3 blocks
+  const int rp_cap = max_tile + 8;
+  auto launch = [&](auto kern, auto fix, int warps, int min_blocks) -> msrep_status {
+    const int threads = 32 * warps;
+    const size_t smem = sizeof(int32_t) * size_t(warps) * rp_cap;
+    // The kernel's attributes are set once per device for its largest
+    // buffer (tile 1024): the dynamic shared-memory limit, and the smallest
+    // carveout that holds the blocks it asks for.  (Setting the limit to a
+    // launch's own size would lower it for later launches with larger
+    // tiles.)  Resident blocks are then known per shared-memory size.
     static std::mutex mu;
-    static std::map<int, int> blocks;
+    static std::map<std::pair<int, const void *>, bool> prepared;
+    static std::map<std::tuple<int, const void *, size_t>, int> blocks;
     int dev = 0, nb = 1;
     MSREP_CUDA_TRY(cudaGetDevice(&dev));
     {
       std::lock_guard<std::mutex> lk(mu);
-      auto it = blocks.find(dev);
+      const void *kp = reinterpret_cast<const void *>(kern);
+      if (!prepared[std::make_pair(dev, kp)]) {
+        const size_t most = sizeof(int32_t) * size_t(warps) * (1024 + 8);
+        MSREP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            static_cast<int>(most)));
+        MSREP_TRY(set_min_carveout(kp, most, min_blocks));
+        prepared[std::make_pair(dev, kp)] = true;
+      }
+      const auto key = std::make_tuple(dev, kp, smem);
+      auto it = blocks.find(key);
       if (it == blocks.end()) {
-        MSREP_TRY(set_min_carveout(reinterpret_cast<const void *>(kern), 0, 3));
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, kBThreads, 0) != cudaSuccess || nb < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, threads, smem) !=
+                cudaSuccess ||
+            nb < 1)
           nb = 1;
-        blocks[dev] = nb;
+        blocks[key] = nb;
       } else {
         nb = it->second;
       }
     }
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(T, kBWarps), int64_t(nb) * sms));
-    kern<<<static_cast<int>(grid), kBThreads, 0, st>>>(items, toff, count, xs, ys, head, tail,
-                                                       alpha, beta, finish, comp, err);
+    const int64_t grid =
+        std::max<int64_t>(1, std::min<int64_t>(ceil_div(T, warps), int64_t(nb) * sms));
+    kern<<<static_cast<int>(grid), threads, smem, st>>>(items, toff, count, xs, ys, head, tail,
+                                                        alpha, beta, finish, comp, err, rp_cap);
     MSREP_CUDA_TRY(cudaGetLastError());
     const int64_t fg = std::max<int64_t>(1, std::min<int64_t>(ceil_div(T, 256), 4 * sms));
     MSREP_TRY(launch_dependent(fix, fg, 256, st, 0, items, toff, count, ys, head, tail, alpha,
                                beta));
     return MSREP_OK;
   };
+  auto shaped = [&](auto pol, auto fix) -> msrep_status {
+    using Pol = decltype(pol);
+    if (cta_threads == 128) return launch(batched_csr<Pol, 4>, fix, 4, BShape<4>::kMinBlocks);
+    if (cta_threads == 512) return launch(batched_csr<Pol, 16>, fix, 16, BShape<16>::kMinBlocks);
+    return launch(batched_csr<Pol, 8>, fix, 8, BShape<8>::kMinBlocks);
+  };
   switch (val_dtype) {
-    case MSREP_F64: return launch(batched_csr<PolF64>, batched_fixup<double>);
-    case MSREP_F32: return launch(batched_csr<PolF32<float>>, batched_fixup<float>);
-    default: return launch(batched_csr<PolF32<bf16_t>>, batched_fixup<float>);
+    case MSREP_F64: return shaped(PolF64{}, batched_fixup<double>);
+    case MSREP_F32: return shaped(PolF32<float>{}, batched_fixup<float>);
+    default: return shaped(PolF32<bf16_t>{}, batched_fixup<float>);
   }
 }
 
@@ -232,6 +269,8 @@ msrep_status msrep_tune_default(msrep_tune_table *t) {
     t->tile[b] = kDefaultTile;
     t->part_nnz[b] = 0;
   }
+  t->cta_threads = 256;
+  t->reserved = 0;
   return ok();
 }
 
@@ -252,6 +291,9 @@ msrep_status msrep_batch_prepare(int32_t count, const msrep_matrix *As,
                                  msrep_batch *out, void *stream) {
   MSREP_TRY(check_batch_inputs(count, As));
   if (!dev || !out) return fail(MSREP_ERR_INVALID_ARG, "dev or out is NULL");
+  if (tune && tune->cta_threads != 0 && tune->cta_threads != 128 && tune->cta_threads != 256 &&
+      tune->cta_threads != 512)
+    return fail(MSREP_ERR_INVALID_ARG, "cta_threads must be 0, 128, 256 or 512");
   if (reinterpret_cast<uintptr_t>(dev) & 255)
     return fail(MSREP_ERR_INVALID_ARG, "dev must be 256-byte aligned");
   std::vector<ItemLayout> lay;
@@ -305,6 +347,10 @@ msrep_status msrep_batch_prepare(int32_t count, const msrep_matrix *As,
   out->dev_bytes = dev_bytes;
   out->items_off = static_cast<int64_t>(items_off);
   out->toff_off = static_cast<int64_t>(toff_off);
+  out->cta_threads = tune && tune->cta_threads ? tune->cta_threads : 256;
+  int32_t mt = 0;
+  for (const ItemLayout &L : lay) mt = std::max(mt, L.tile);
+  out->max_tile = mt;
   return ok();
 }
 
@@ -322,7 +368,8 @@ msrep_status msrep_spmv_batched(const msrep_batch *B, const void *const *xs, voi
   MSREP_TRY(launch_batched(reinterpret_cast<const BatchItem *>(base + B->items_off),
                            reinterpret_cast<const int64_t *>(base + B->toff_off), B->count,
                            B->total_tiles, B->val_dtype, xs, ys, head, tail, alpha, beta, flags,
-                           as_stream(stream)));
+                           as_stream(stream), B->cta_threads ? B->cta_threads : 256,
+                           B->max_tile ? B->max_tile : 1024));
   return ok();
 }
 
@@ -354,11 +401,42 @@ static size_t trial_bytes(const msrep_matrix *A) {
   return worst;
 }
 
+// The table that makes a batch's plan and workspace largest: the smallest
+// tile and the most partitions of the autotuner's candidates.
+static msrep_tune_table largest_table() {
+  msrep_tune_table t;
+  for (int b = 0; b < MSREP_TUNE_BUCKETS; ++b) {
+    t.tile[b] = kTuneTiles[0];
+    t.part_nnz[b] = kTuneParts[1];
+  }
+  t.cta_threads = 256;
+  t.reserved = 0;
+  return t;
+}
+
+// Scratch of the autotuner's thread-block phase: the prepared batch (at a
+// 256-byte boundary), the device arrays of x and y pointers and the
+// batched workspace, under the largest table.
+static size_t cta_phase_bytes(int32_t count, const msrep_matrix *As) {
+  const msrep_tune_table t = largest_table();
+  size_t io, to;
+  const size_t bb = batch_bytes(count, As, &t, nullptr, &io, &to);
+  int64_t tiles = 0;
+  for (int32_t j = 0; j < count; ++j) {
+    int32_t tile, np;
+    tuned(&t, As[j].nnz, &tile, &np);
+    tiles += plan_layout(As[j].m, As[j].nnz, np, tile).tmax;
+  }
+  return 256 + align256(bb) + 2 * align256(sizeof(void *) * size_t(count)) +
+         2 * align256(sizeof(double) * size_t(std::max<int64_t>(tiles, 1)));
+}
+
 msrep_status msrep_autotune_scratch_size(int32_t count, const msrep_matrix *As, int64_t *bytes) {
   MSREP_TRY(check_batch_inputs(count, As));
   if (!bytes) return fail(MSREP_ERR_INVALID_ARG, "bytes is NULL");
   size_t w = 0;
   for (int32_t j = 0; j < count; ++j) w = std::max(w, trial_bytes(As + j));
+  w = std::max(w, cta_phase_bytes(count, As));
   *bytes = static_cast<int64_t>(w);
   return ok();
 }
@@ -430,6 +508,48 @@ msrep_status msrep_autotune(int32_t count, const msrep_matrix *As, const void *c
           out->part_nnz[bkt] = pn;
         }
       }
+  }
+  // Thread-block shape: one per batch, since one launch runs every matrix.
+  // The whole batch is prepared with the table chosen above and the
+  // batched launch timed with each shape.
+  if (status == MSREP_OK) {
+    char *b0 = reinterpret_cast<char *>(align256(reinterpret_cast<uintptr_t>(base)));
+    size_t io, to;
+    const size_t bb = batch_bytes(count, As, out, nullptr, &io, &to);
+    msrep_batch B{};
+    status = msrep_batch_prepare(count, As, out, b0, static_cast<int64_t>(bb), &B, stream);
+    char *p = b0 + align256(bb);
+    void **dxs = reinterpret_cast<void **>(p);
+    p += align256(sizeof(void *) * size_t(count));
+    void **dys = reinterpret_cast<void **>(p);
+    p += align256(sizeof(void *) * size_t(count));
+    if (status == MSREP_OK &&
+        (cudaMemcpyAsync(dxs, xs, sizeof(void *) * count, cudaMemcpyHostToDevice, st) !=
+             cudaSuccess ||
+         cudaMemcpyAsync(dys, ys, sizeof(void *) * count, cudaMemcpyHostToDevice, st) !=
+             cudaSuccess))
+      status = fail(MSREP_ERR_CUDA, "autotune: copying the vector pointers failed");
+    float best_ms = INFINITY;
+    for (int cta : {128, 256, 512}) {
+      if (status != MSREP_OK) break;
+      B.cta_threads = cta;
+      for (int rep = 0; rep < 4 && status == MSREP_OK; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, st);
+        status = msrep_spmv_batched(&B, dxs, dys, 1.0, 0.0, 0, p, stream);
+      }
+      if (status != MSREP_OK) break;
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        status = fail(MSREP_ERR_CUDA, "autotune timing failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        out->cta_threads = cta;
+      }
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

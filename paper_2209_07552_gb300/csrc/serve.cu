@@ -23,6 +23,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -62,6 +63,7 @@ struct Request {
   bool x_pinned = false, y_pinned = false;  // page-locked: DMA directly
   bool done = false;
   msrep_status status = MSREP_OK;
+  std::string error;  // why the request failed, when it did
 };
 
 struct Context {
@@ -333,8 +335,10 @@ static void scheduler_loop(msrep_server *s) {
     if (st != MSREP_OK) {
       // fail the requests of this launch; the context stays usable
       cudaStreamSynchronize(c->stream);
+      const std::string why = msrep_last_error();
       for (auto &r : c->reqs) {
         r->status = st;
+        r->error = why;
         r->done = true;
         s->mats[r->matrix].refs--;
       }
@@ -391,6 +395,7 @@ static void completion_loop(msrep_server *s) {
       }
       for (auto &r : c.reqs) {
         r->status = q == cudaSuccess ? MSREP_OK : MSREP_ERR_CUDA;
+        if (q != cudaSuccess) r->error = cudaGetErrorString(q);
         r->done = true;
         s->mats[r->matrix].refs--;
         s->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r->t_submit).count());
@@ -653,7 +658,8 @@ msrep_status msrep_serve_wait(msrep_server *s, uint64_t req_id, int64_t timeout_
     return fail(MSREP_ERR_TIMEOUT, "request %llu not finished", (unsigned long long)req_id);
   }
   s->reqs.erase(req_id);
-  if (r->status != MSREP_OK) return fail(r->status, "request %llu failed", (unsigned long long)req_id);
+  if (r->status != MSREP_OK)
+    return fail(r->status, "request %llu failed: %s", (unsigned long long)req_id, r->error.c_str());
   return ok();
 }
 

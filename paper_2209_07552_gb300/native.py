@@ -63,14 +63,16 @@ class c_msrep_partition(ctypes.Structure):
 
 
 class c_msrep_tune_table(ctypes.Structure):
-    _fields_ = [("tile", ctypes.c_int32 * 32), ("part_nnz", ctypes.c_int64 * 32)]
+    _fields_ = [("tile", ctypes.c_int32 * 32), ("part_nnz", ctypes.c_int64 * 32),
+                ("cta_threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class c_msrep_batch(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("val_dtype", ctypes.c_int32),
                 ("total_tiles", ctypes.c_int64), ("ws_bytes", ctypes.c_int64),
                 ("dev", ctypes.c_void_p), ("dev_bytes", ctypes.c_int64),
-                ("items_off", ctypes.c_int64), ("toff_off", ctypes.c_int64)]
+                ("items_off", ctypes.c_int64), ("toff_off", ctypes.c_int64),
+                ("cta_threads", ctypes.c_int32), ("max_tile", ctypes.c_int32)]
 
 
 class c_msrep_serve_config(ctypes.Structure):

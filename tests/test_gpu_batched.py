@@ -49,8 +49,9 @@ def _tuned(tune, nnz):
     return (max(1, -(-nnz // pn)) if pn > 0 else 1), tile
 
 
+@pytest.mark.parametrize("cta", [128, 256, 512])
 @pytest.mark.parametrize("dt", ["f64", "f32"])
-def test_batched_equals_solo_and_oracle(dt):
+def test_batched_equals_solo_and_oracle(dt, cta):
     import torch
 
     import paper_2209_07552_gb300 as M
@@ -63,7 +64,9 @@ def test_batched_equals_solo_and_oracle(dt):
     for b in range(8, 20):            # vary partitions and tiles across buckets
         tune.tile[b] = (256, 512, 1024)[b % 3]
         tune.part_nnz[b] = (0, 1 << 12, 1 << 15)[b % 3]
+    tune.cta_threads = cta            # thread-block shape of the launch
     B = M.DeviceBatch(D, X, Y, tune)
+    assert B.c.cta_threads == cta and B.c.max_tile == 1024
     B.run()
     torch.cuda.synchronize()
     for a, x, y in zip(mats, xs, Y):
@@ -90,6 +93,7 @@ def test_autotune_then_batch():
     for b in range(32):
         assert tune.tile[b] in (256, 512, 1024)
         assert tune.part_nnz[b] in (0, 1 << 14, 1 << 18)
+    assert tune.cta_threads in (128, 256, 512)
     B = M.DeviceBatch(D, X, Y, tune)
     B.run()
     torch.cuda.synchronize()
