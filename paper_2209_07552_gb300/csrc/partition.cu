@@ -134,6 +134,7 @@ __global__ void part_meta_compressed(const int32_t *__restrict__ ptr,
                                      int32_t *start_major, int32_t *end_major,
                                      uint8_t *start_flag, int64_t *plan_D,
                                      int32_t *plan_R, int cut) {
+  grid_dependency_wait();
   const int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
   const bool lead = (threadIdx.x & 31) == 0;
   if (i > np) return;  // warp-uniform
@@ -225,6 +226,7 @@ __global__ void part_meta_coo(const int32_t *__restrict__ row_idx, int64_t nnz,
                               int32_t np, int32_t *start_idx, int32_t *end_idx,
                               int32_t *start_major, int32_t *end_major,
                               uint8_t *start_flag, int32_t m, int row_block) {
+  grid_dependency_wait();
   int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i >= np) return;
   int64_t s, e;
@@ -255,6 +257,7 @@ __global__ void part_meta_coo(const int32_t *__restrict__ row_idx, int64_t nnz,
 __global__ void part_meta_coo_unsorted(int64_t nnz, int32_t m, int32_t np, int32_t *start_idx,
                                        int32_t *end_idx, int32_t *start_major,
                                        int32_t *end_major, uint8_t *start_flag) {
+  grid_dependency_wait();
   const int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
   if (i >= np) return;
   const int64_t s = (i * nnz) / np;
@@ -303,6 +306,7 @@ __device__ T block_exclusive_scan(T v, T &total) {
 __global__ void __launch_bounds__(1024)
     local_off_scan(const int32_t *start_major, const int32_t *end_major,
                    int32_t np, int64_t *local_off) {
+  grid_dependency_wait();
   int64_t carry = 0;
   for (int32_t base = 0; base < np; base += blockDim.x) {
     int32_t i = base + threadIdx.x;
@@ -329,6 +333,7 @@ __global__ void __launch_bounds__(256)
                           const int32_t *end_idx, const int32_t *start_major,
                           const int32_t *end_major, const int64_t *local_off, int32_t np,
                           int32_t *local) {
+  grid_dependency_wait();
   const int64_t total = local_off[np];
   const int lane = threadIdx.x & 31;
   const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
@@ -384,6 +389,7 @@ template <bool kVec>
 __global__ void __launch_bounds__(256)
     local_fill_coo(const int32_t *__restrict__ row_idx, int64_t nnz, int32_t np,
                    const int32_t *start_idx, const int32_t *start_major, int32_t *local) {
+  grid_dependency_wait();
   const int64_t stride = int64_t(gridDim.x) * blockDim.x * 8;
   for (int64_t k0 = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) * 8; k0 < nnz;
        k0 += stride) {
@@ -441,6 +447,7 @@ __global__ void __launch_bounds__(256)
 
 __global__ void __launch_bounds__(1024)
     plan_scan(const int64_t *D, int32_t np, int32_t tile, int32_t *tile_off) {
+  grid_dependency_wait();
   int64_t carry = 0;
   for (int32_t base = 0; base < np; base += blockDim.x) {
     int32_t i = base + threadIdx.x;
@@ -458,6 +465,7 @@ __global__ void plan_tiles(const int32_t *__restrict__ ptr, int32_t n_major,
                            int64_t nnz, int32_t np, const int64_t *D,
                            const int32_t *R, const int32_t *tile_off,
                            int32_t *tile_row, int32_t *tile_k) {
+  grid_dependency_wait();
   const int32_t i = blockIdx.x;
   const int32_t t0 = tile_off[i], G = tile_off[i + 1] - t0;
   const int64_t d0 = D[i], len = D[i + 1] - d0;
@@ -494,6 +502,7 @@ constexpr size_t kHotSmem = 2 * sizeof(int32_t) * kHotSlots;
 
 __global__ void __launch_bounds__(1024) hot_rows(const int32_t *__restrict__ row_idx,
                                                  int64_t nnz, int32_t *hot) {
+  grid_dependency_wait();
   extern __shared__ int32_t hs[];
   int32_t *tkey = hs, *tcnt = hs + kHotSlots;
   __shared__ unsigned long long wbest[32];
@@ -582,6 +591,7 @@ __device__ __forceinline__ unsigned long long warm_entry(uint32_t prio, int32_t 
 // ends), which holds row + 1 (0 = empty).  Everything starts all zero.
 __global__ void warm_count(const int32_t *__restrict__ row_idx, int64_t nnz, const int32_t *hot,
                            unsigned long long *warm, int32_t *key, int32_t *cnt) {
+  grid_dependency_wait();
   const int nh = hot[0];
   if (nh == 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0)
@@ -608,6 +618,7 @@ __global__ void warm_count(const int32_t *__restrict__ row_idx, int64_t nnz, con
 // 255) into hist[256].  Rows seen fewer times never qualify; they are most
 // rows and would all land in one bin.
 __global__ void warm_hist(const int32_t *hot, const int32_t *cnt, int32_t *hist) {
+  grid_dependency_wait();
   __shared__ int h[256];
   if (hot[0] == 0) return;
   for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
@@ -626,6 +637,7 @@ __global__ void warm_hist(const int32_t *hot, const int32_t *cnt, int32_t *hist)
 // rows reach.
 __global__ void warm_select(const int32_t *hot, const int32_t *key, const int32_t *cnt,
                             const int32_t *hist, unsigned long long *warm) {
+  grid_dependency_wait();
   __shared__ int thresh;
   if (hot[0] == 0) return;
   if (threadIdx.x == 0) {
@@ -647,6 +659,16 @@ __global__ void warm_select(const int32_t *hot, const int32_t *key, const int32_
   }
 }
 
+// Clears the frequent-row table and the scratch of its search (n words)
+// when the matrix has hub rows; the others never read them.
+__global__ void warm_clear(const int32_t *hot, uint32_t *p, int64_t n) {
+  grid_dependency_wait();
+  if (__ldg(hot) == 0) return;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+       i += int64_t(gridDim.x) * blockDim.x)
+    p[i] = 0u;
+}
+
 // Hub rows, then the frequent-row table, of a scatter (CSC, or COO sorted by
 // column or in no order): hot, warm and the search scratch (key, cnt) are
 // in the plan.
@@ -654,21 +676,27 @@ static msrep_status find_frequent_rows(const int32_t *row_idx, int64_t nnz, int3
                                        unsigned long long *warm, int32_t *key, int32_t *cnt,
                                        cudaStream_t st) {
   MSREP_TRY(hot_rows_smem_opt_in());
-  hot_rows<<<1, 1024, kHotSmem, st>>>(row_idx, nnz, hot);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_dependent(hot_rows, 1, 1024, st, kHotSmem, row_idx, nnz, hot));
   // table, scratch and histogram lie back to back, all starting at zero
+  // (cleared only for a matrix with hub rows, which alone uses them)
   int32_t *hist = cnt + kWarmTab;
-  MSREP_CUDA_TRY(cudaMemsetAsync(warm, 0, reinterpret_cast<char *>(hist + 256) -
-                                              reinterpret_cast<char *>(warm), st));
+  const int64_t words = (reinterpret_cast<char *>(hist + 256) - reinterpret_cast<char *>(warm)) /
+                        int64_t(sizeof(uint32_t));
+  MSREP_TRY(launch_dependent(warm_clear, 2 * sm_count(), 256, st, 0, hot,
+                             reinterpret_cast<uint32_t *>(warm), words));
   const int S = static_cast<int>(nnz < kWarmSample ? nnz : kWarmSample);
-  warm_count<<<static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(S, 256),
-                                                                       4 * sm_count()))),
-               256, 0, st>>>(row_idx, nnz, hot, warm, key, cnt);
-  MSREP_CUDA_TRY(cudaGetLastError());
-  warm_hist<<<kWarmTab / 256, 256, 0, st>>>(hot, cnt, hist);
-  MSREP_CUDA_TRY(cudaGetLastError());
-  warm_select<<<kWarmTab / 256, 256, 0, st>>>(hot, key, cnt, hist, warm);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_dependent(warm_count,
+                             std::max<int64_t>(1, std::min<int64_t>(ceil_div(S, 256),
+                                                                    4 * sm_count())),
+                             256, st, 0, row_idx, nnz, static_cast<const int32_t *>(hot), warm,
+                             key, cnt));
+  MSREP_TRY(launch_dependent(warm_hist, kWarmTab / 256, 256, st, 0,
+                             static_cast<const int32_t *>(hot), static_cast<const int32_t *>(cnt),
+                             hist));
+  MSREP_TRY(launch_dependent(warm_select, kWarmTab / 256, 256, st, 0,
+                             static_cast<const int32_t *>(hot), static_cast<const int32_t *>(key),
+                             static_cast<const int32_t *>(cnt), static_cast<const int32_t *>(hist),
+                             warm));
   return MSREP_OK;
 }
 
@@ -805,42 +833,38 @@ static msrep_status partition_compressed(const msrep_matrix *A,
   if ((flags & MSREP_PART_MERGE_PATH) && (flags & MSREP_PART_ROW_BLOCK))
     return fail(MSREP_ERR_INVALID_ARG,
                 "MSREP_PART_MERGE_PATH and MSREP_PART_ROW_BLOCK exclude each other");
-  part_meta_compressed<<<blocks, threads, 0, st>>>(
-      A->ptr, n_major, A->nnz, p->np, p->start_idx, p->end_idx,
-      p->start_major, p->end_major, p->start_flag, D, R,
-      (flags & MSREP_PART_MERGE_PATH) ? kCutMergePath
-                                      : (flags & MSREP_PART_ROW_BLOCK) ? kCutRowBlock
-                                                                       : kCutNonzeros);
-  MSREP_CUDA_TRY(cudaGetLastError());
+  MSREP_TRY(launch_dependent(
+      part_meta_compressed, blocks, threads, st, 0, A->ptr, n_major, A->nnz, p->np, p->start_idx,
+      p->end_idx, p->start_major, p->end_major, p->start_flag, D, R,
+      (flags & MSREP_PART_MERGE_PATH) ? int(kCutMergePath)
+                                      : (flags & MSREP_PART_ROW_BLOCK) ? int(kCutRowBlock)
+                                                                       : int(kCutNonzeros)));
   if (p->local_off) {
-    local_off_scan<<<1, 1024, 0, st>>>(p->start_major, p->end_major, p->np,
-                                       p->local_off);
-    MSREP_CUDA_TRY(cudaGetLastError());
+    MSREP_TRY(launch_dependent(local_off_scan, 1, 1024, st, 0,
+                               static_cast<const int32_t *>(p->start_major),
+                               static_cast<const int32_t *>(p->end_major), p->np, p->local_off));
     if (p->local) {
       // at most m + 2 np entries (n + 2 np for CSC)
       const int64_t most = int64_t(n_major) + 2 * int64_t(p->np);
       const int grid = static_cast<int>(
           std::max<int64_t>(1, std::min<int64_t>(ceil_div(most, 8 * 256), 8 * sm_count())));
       if ((reinterpret_cast<uintptr_t>(p->local) & 15) == 0)
-        local_fill_compressed<true><<<grid, 256, 0, st>>>(
-            A->ptr, p->start_idx, p->end_idx, p->start_major, p->end_major, p->local_off,
-            p->np, p->local);
+        MSREP_TRY(launch_dependent(local_fill_compressed<true>, grid, 256, st, 0, A->ptr,
+                                   p->start_idx, p->end_idx, p->start_major, p->end_major,
+                                   p->local_off, p->np, p->local));
       else
-        local_fill_compressed<false><<<grid, 256, 0, st>>>(
-            A->ptr, p->start_idx, p->end_idx, p->start_major, p->end_major, p->local_off,
-            p->np, p->local);
-      MSREP_CUDA_TRY(cudaGetLastError());
+        MSREP_TRY(launch_dependent(local_fill_compressed<false>, grid, 256, st, 0, A->ptr,
+                                   p->start_idx, p->end_idx, p->start_major, p->end_major,
+                                   p->local_off, p->np, p->local));
     }
   }
   if (plan) {
     int32_t *toff = reinterpret_cast<int32_t *>(plan + L.off_toff);
     int32_t *trow = reinterpret_cast<int32_t *>(plan + L.off_row);
     int32_t *tk = reinterpret_cast<int32_t *>(plan + L.off_k);
-    plan_scan<<<1, 1024, 0, st>>>(D, p->np, tile, toff);
-    MSREP_CUDA_TRY(cudaGetLastError());
-    plan_tiles<<<p->np, 128, 0, st>>>(A->ptr, n_major, A->nnz, p->np, D, R,
-                                      toff, trow, tk);
-    MSREP_CUDA_TRY(cudaGetLastError());
+    MSREP_TRY(launch_dependent(plan_scan, 1, 1024, st, 0, D, p->np, tile, toff));
+    MSREP_TRY(launch_dependent(plan_tiles, p->np, 128, st, 0, A->ptr, n_major, A->nnz, p->np, D,
+                               R, toff, trow, tk));
     if (A->fmt == MSREP_CSC) {
       int32_t *wtab = reinterpret_cast<int32_t *>(plan + L.off_wtab);
       MSREP_TRY(find_frequent_rows(A->idx, A->nnz, reinterpret_cast<int32_t *>(plan + L.off_hot),
@@ -928,25 +952,23 @@ msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
   const int threads = 256;
   const int blocks = static_cast<int>(ceil_div(p->np, threads));
   if (A->fmt == MSREP_COO_UNSORTED)
-    part_meta_coo_unsorted<<<blocks, threads, 0, st>>>(A->nnz, A->m, p->np, p->start_idx,
-                                                       p->end_idx, p->start_major,
-                                                       p->end_major, p->start_flag);
+    MSREP_TRY(launch_dependent(part_meta_coo_unsorted, blocks, threads, st, 0, A->nnz, A->m,
+                               p->np, p->start_idx, p->end_idx, p->start_major, p->end_major,
+                               p->start_flag));
   else
-    part_meta_coo<<<blocks, threads, 0, st>>>(major, A->nnz, p->np, p->start_idx, p->end_idx,
-                                              p->start_major, p->end_major, p->start_flag,
-                                              A->fmt == MSREP_COO_BY_COL ? A->n : A->m,
-                                              (flags & MSREP_PART_ROW_BLOCK) ? 1 : 0);
-  MSREP_CUDA_TRY(cudaGetLastError());
+    MSREP_TRY(launch_dependent(part_meta_coo, blocks, threads, st, 0, major, A->nnz, p->np,
+                               p->start_idx, p->end_idx, p->start_major, p->end_major,
+                               p->start_flag, A->fmt == MSREP_COO_BY_COL ? A->n : A->m,
+                               (flags & MSREP_PART_ROW_BLOCK) ? 1 : 0));
   if (p->local && A->nnz > 0) {
     const int grid = static_cast<int>(
         std::max<int64_t>(1, std::min<int64_t>(ceil_div(A->nnz, 8 * 256), 8 * sm_count())));
     if (((reinterpret_cast<uintptr_t>(p->local) | reinterpret_cast<uintptr_t>(major)) & 15) == 0)
-      local_fill_coo<true><<<grid, 256, 0, st>>>(major, A->nnz, p->np, p->start_idx,
-                                                 p->start_major, p->local);
+      MSREP_TRY(launch_dependent(local_fill_coo<true>, grid, 256, st, 0, major, A->nnz, p->np,
+                                 p->start_idx, p->start_major, p->local));
     else
-      local_fill_coo<false><<<grid, 256, 0, st>>>(major, A->nnz, p->np, p->start_idx,
-                                                  p->start_major, p->local);
-    MSREP_CUDA_TRY(cudaGetLastError());
+      MSREP_TRY(launch_dependent(local_fill_coo<false>, grid, 256, st, 0, major, A->nnz, p->np,
+                                 p->start_idx, p->start_major, p->local));
   }
   if (scatter && p->plan) {
     char *plan = static_cast<char *>(p->plan);
