@@ -432,6 +432,17 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.step_only:
+        ev0.record()
+        for _ in range(args.steps):
+            step()
+        ev1.record()
+        torch.cuda.synchronize()
+        if rank == 0:
+            ms = ev0.elapsed_time(ev1) / args.steps
+            print(json.dumps({"step_only": True, "ms_per_step": ms,
+                              "gflops": flops_step / (ms * 1e-3) / 1e9}), flush=True)
+        return
     with ClockSampler(local) as clk:
         ev0.record()
         for _ in range(args.steps):
@@ -1035,6 +1046,22 @@ def run_profile_case(args):
     import paper_2209_07552_gb300 as M
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    if args.profile == "batched":
+        # uneven FP32 CSR matrices drawn like the batched workload, autotuned,
+        # `--reps` batched launches
+        mats, xs = I.batched_set_parallel(args.profile_batch_count)
+        D = [M.DeviceMatrix.from_host(a, "csr", "f32", device=dev) for a in mats]
+        X = [torch.from_numpy(x).to(dev) for x in xs]
+        Y = [torch.empty(a.m, dtype=torch.float32, device=dev) for a in mats]
+        tune = M.msrep_autotune(D, X, Y, device=dev)
+        B = M.DeviceBatch(D, X, Y, tune, device=dev)
+        for _ in range(args.reps):
+            B.run()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "batched", "matrices": len(mats),
+                          "nnz": sum(a.nnz for a in mats), "cta_threads": int(tune.cta_threads),
+                          "reps": args.reps}))
+        return
     a = I.rmat_full() if args.profile_matrix == "rmat" else I.laplace_full()
     dt = args.profile_dtype
     A = M.DeviceMatrix.from_host(a, args.profile, dt, device=dev)
@@ -1131,7 +1158,11 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=20000.0)
     ap.add_argument("--serve-contexts", type=int, default=4,
                     help="launch contexts of the server (launches in flight at once)")
-    ap.add_argument("--profile", choices=FORMATS + ("coo_col", "coo_any"), default=None,
+    ap.add_argument("--step-only", action="store_true",
+                    help="run only the timed step (for an ncu launch list of the step)")
+    ap.add_argument("--profile-batch-count", type=int, default=64,
+                    help="matrices of the batched profile case")
+    ap.add_argument("--profile", choices=FORMATS + ("coo_col", "coo_any", "batched"), default=None,
                     help="run only a short fixed case (for ncu captures)")
     ap.add_argument("--profile-matrix", choices=["rmat", "laplace"], default="rmat")
     ap.add_argument("--profile-dtype", choices=["f64", "f32", "bf16"], default="f64")
