@@ -496,6 +496,9 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers: x up, SpMV, y down
     e2e = run_e2e(M, pairs, args, dev)
+    # the served stream runs first among the extra legs, on a device and
+    # host that the other legs' large allocations have not touched yet
+    serving = run_serving(M, args, dev) if args.serve_seconds > 0 else None
     p_sweep = run_p_sweep(M, pairs, args) if not args.skip_p_sweep else None
     coo_orders = run_coo_orders(M, args, dev, kern, peak) if not args.skip_coo_orders else None
     imbalance = run_imbalance(M, args, dev) if not args.skip_imbalance else None
@@ -503,7 +506,6 @@ def run_ours(args):
     # low-precision form on every (matrix, format) pair
     prec = run_precision(M, args, dev, kern) if not args.skip_precision else None
     batched = run_batched(M, args, dev) if args.batched_count > 0 else None
-    serving = run_serving(M, args, dev) if args.serve_seconds > 0 else None
 
     line = {
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
@@ -770,7 +772,7 @@ def run_serving(M, args, dev):
     # up front (16 per matrix, each large enough for 8 vectors):
     # allocating page-locked memory while submitting takes milliseconds (and
     # can wait on the device), which bunched submissions and inflated p99.
-    per = 16
+    per = 24
     sizes = [8 * a.m for a in mats]
     slab = M.native.pinned_empty((per * sum(sizes),))
     pools, o = [], 0
@@ -815,10 +817,11 @@ def serve_once(M, mats, X, budget, cfg, args, seed, all_pools):
             item = q.get()
             if item is None:
                 return
-            j, t = item
+            j, t, pooled = item
             S.wait(t)
-            with lock:
-                pools[j].append(t.y)
+            if pooled:
+                with lock:
+                    pools[j].append(t.y)
 
     # several waiters, so a slow request holds back only its own buffer
     ths = [threading.Thread(target=waiter, daemon=True) for _ in range(8)]
@@ -830,6 +833,9 @@ def serve_once(M, mats, X, budget, cfg, args, seed, all_pools):
     # interval lets the waiters hand buffers back without 5 ms delays
     switch = sys.getswitchinterval()
     sys.setswitchinterval(1e-4)
+    import gc
+    gc_was = gc.isenabled()
+    gc.disable()   # no collector pauses inside the request stream
     t0 = time.perf_counter()
     for i in range(arrivals.shape[0]):
         target = t0 + arrivals[i]
@@ -846,17 +852,20 @@ def serve_once(M, mats, X, budget, cfg, args, seed, all_pools):
         k = int(ks[i])
         with lock:
             y = pools[j].pop() if pools[j] else None
+        pooled = True
         if y is None:
             misses[0] += 1
             y = M.native.pinned_empty((8 * mats[j].m,))
         t = S.submit(mid, X[j][:k], y)
-        q.put((j, t))
+        q.put((j, t, pooled))
     sent = time.perf_counter() - t0
     for _ in ths:
         q.put(None)
     for th in ths:
         th.join()
     sys.setswitchinterval(switch)
+    if gc_was:
+        gc.enable()
     st = S.stats()
     S.close()
     st.update({"offered_rate": arrivals.shape[0] / args.serve_seconds,
@@ -950,20 +959,23 @@ def run_spmm_leg(M, A, part, a, xh, dev, spmv_call_us, k=8):
 def run_imbalance(M, args, dev):
     """The imbalance experiment of Sec. 2.3 (Fig. 5) on one GPU, with thread
     blocks in place of GPUs: B partitions, one thread block each
-    (MSREP_SCHED_PER_PARTITION), B = the CSR kernel's resident blocks, so
-    all partitions run at once as the paper's GPUs do.  The matrix has
+    (MSREP_SCHED_PER_PARTITION), B = the number of SMs, so that every
+    partition runs at once on an SM of its own, as the paper's partitions
+    run on GPUs of their own.  The matrix has
     2^20 rows in B equal row blocks; rows of the first half of the blocks
     hold 32 nonzeros, the others 32 / r (the paper's two-level nonzero
     distribution, low-to-high ratio 1/r).  Per r: the SpMV over the
     Baseline row-block partitioning (Sec. 5.1, MSREP_PART_ROW_BLOCK) and
-    over Alg. 2's nonzero-balanced partitioning, both one block per
-    partition, and the row-block partitioning under the default schedule
-    (every partition's tiles spread over all blocks).  CSR, FP64."""
+    over Alg. 2's nonzero-balanced partitioning and over the row+nonzero
+    merge-path partitioning (which also balances the rows, whose ends cost
+    the CSR kernel work too), all one block per partition, and the
+    row-block partitioning under the default schedule (every partition's
+    tiles spread over all blocks).  CSR, FP64."""
     import torch
     m, heavy = 1 << 20, 32
-    # resident blocks of the CSR kernel: 3 per SM of 256 threads (its
-    # register budget), so 3 x SMs partitions run in one wave
-    B = 3 * torch.cuda.get_device_properties(dev).multi_processor_count
+    # one partition per SM: each thread block has its SM to itself, as each
+    # of the paper's partitions has its GPU
+    B = torch.cuda.get_device_properties(dev).multi_processor_count
     out = {"rows": m, "partitions": B, "heavy_row_nnz": heavy, "ratios": {}}
     for r in (1, 2, 4, 10):
         a = I.block_imbalance_matrix(m, B, heavy, r, I.SEED_BASE + 5 + r)
@@ -974,6 +986,8 @@ def run_imbalance(M, args, dev):
         for tag, pflags, flags in (("row_block_per_partition", M.MSREP_PART_ROW_BLOCK,
                                     M.MSREP_SCHED_PER_PARTITION),
                                    ("nnz_balanced_per_partition", 0, M.MSREP_SCHED_PER_PARTITION),
+                                   ("merge_path_per_partition", M.MSREP_PART_MERGE_PATH,
+                                    M.MSREP_SCHED_PER_PARTITION),
                                    ("row_block_default_schedule", M.MSREP_PART_ROW_BLOCK, 0)):
             part = M.DevicePartition(A, B, device=dev)
             M.msrep_partition(A, part, pflags)
@@ -988,7 +1002,9 @@ def run_imbalance(M, args, dev):
                         "max_partition_nnz": int(ln.max()), "mean_partition_nnz": float(ln.mean())}
             del part, ws
         rb, nb = row["row_block_per_partition"], row["nnz_balanced_per_partition"]
+        mp = row["merge_path_per_partition"]
         row["row_block_over_balanced_perf"] = nb["kernel_us"] / rb["kernel_us"]
+        row["row_block_over_merge_path_perf"] = mp["kernel_us"] / rb["kernel_us"]
         out["ratios"][str(r)] = row
         del A, x, y
     return out

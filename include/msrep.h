@@ -422,6 +422,9 @@ typedef struct {
                                           its first x copy to its last y
                                           copy (CUDA events)              */
   double kernel_mean_us;  /* the batched kernels of one launch (events)   */
+  double host_launch_p50_us, host_launch_p99_us; /* the scheduler thread
+                                          issuing one launch's copies and
+                                          kernels (host clock)            */
 } msrep_serve_counters;
 
 /* Defaults: 60 GB budget, 64 MB arenas, 3 contexts, 256 items, k <= 8. */

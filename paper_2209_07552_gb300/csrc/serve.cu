@@ -113,6 +113,7 @@ struct msrep_server {
   std::vector<double> lat_us;     // submit -> y in the caller's buffer
   std::vector<double> wait_us;    // submit -> packed into a launch (host)
   std::vector<double> dev_us;     // per launch: first copy -> last copy (device)
+  std::vector<double> host_us;    // per launch: the scheduler issuing its copies and kernels
   double kernel_us = 0;           // sum over launches of the kernels' device time
   uint64_t submitted = 0, completed = 0, rejected = 0, launches = 0, items = 0;
   double work_bytes = 0, busy_s = 0;
@@ -329,8 +330,11 @@ static void scheduler_loop(msrep_server *s) {
     s->launches++;
     for (const auto &r : c->reqs) s->items += r->k;
     lk.unlock();
+    const auto h0 = Clock::now();
     msrep_status st = launch_context(s, *c, ritem, rtiles);
+    const double host = std::chrono::duration<double, std::micro>(Clock::now() - h0).count();
     lk.lock();
+    s->host_us.push_back(host);
     if (st == MSREP_OK) c->in_flight = true;  // only now may its event be polled
     if (st != MSREP_OK) {
       // fail the requests of this launch; the context stays usable
@@ -694,6 +698,8 @@ msrep_status msrep_serve_stats(msrep_server *s, msrep_serve_counters *o, int32_t
   o->device_p50_us = pct(s->dev_us, 0.50);
   o->device_p99_us = pct(s->dev_us, 0.99);
   o->kernel_mean_us = s->dev_us.empty() ? 0.0 : s->kernel_us / double(s->dev_us.size());
+  o->host_launch_p50_us = pct(s->host_us, 0.50);
+  o->host_launch_p99_us = pct(s->host_us, 0.99);
   double busy = s->busy_s;
   if (s->inflight > 0) busy += std::chrono::duration<double>(Clock::now() - s->busy_since).count();
   o->busy_s = busy;
@@ -704,6 +710,7 @@ msrep_status msrep_serve_stats(msrep_server *s, msrep_serve_counters *o, int32_t
     s->lat_us.clear();
     s->wait_us.clear();
     s->dev_us.clear();
+    s->host_us.clear();
     s->kernel_us = 0;
     s->submitted = s->completed = s->rejected = s->launches = s->items = 0;
     s->work_bytes = 0;

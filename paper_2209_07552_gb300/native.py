@@ -91,7 +91,8 @@ class c_msrep_serve_counters(ctypes.Structure):
                 ("busy_s", ctypes.c_double), ("resident_bytes", ctypes.c_int64),
                 ("wait_p50_us", ctypes.c_double), ("wait_p99_us", ctypes.c_double),
                 ("device_p50_us", ctypes.c_double), ("device_p99_us", ctypes.c_double),
-                ("kernel_mean_us", ctypes.c_double)]
+                ("kernel_mean_us", ctypes.c_double), ("host_launch_p50_us", ctypes.c_double),
+                ("host_launch_p99_us", ctypes.c_double)]
 
 
 _M = ctypes.POINTER(c_msrep_matrix)

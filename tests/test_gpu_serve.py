@@ -93,6 +93,7 @@ def test_serve_results_alone_and_in_the_mix():
         assert st["wait_p99_us"] >= st["wait_p50_us"] >= 0
         assert st["device_p99_us"] >= st["device_p50_us"] > 0
         assert 0 < st["kernel_mean_us"] <= st["device_p99_us"]
+        assert st["host_launch_p99_us"] >= st["host_launch_p50_us"] > 0
         assert st["device_p50_us"] <= st["p99_us"]
     for a, x, y in zip(mats, X, alone):
         assert y.shape == (8, a.m)
