@@ -791,8 +791,12 @@ def run_serving(M, args, dev):
 
 
 def serve_once(M, mats, X, budget, cfg, args, seed, all_pools):
-    import queue
-    import threading
+    """One served stream under `budget`: register every matrix (those that
+    do not fit are not admitted), then replay the Poisson stream with the
+    library's native driver (msrep_serve_replay), which submits each
+    request at its arrival time from one native thread; request i writes
+    into the next of its matrix's page-locked y buffers and, before that,
+    the driver waits for the request that last used that buffer."""
     S = M.Server(budget_bytes=budget, **cfg)
     ids = []
     for j, a in enumerate(mats):
@@ -801,79 +805,38 @@ def serve_once(M, mats, X, budget, cfg, args, seed, all_pools):
         except M.MsrepError as e:
             if e.status != 6:      # MSREP_ERR_BUDGET: not admitted
                 raise
-    admitted_rejected = S.stats()["rejected"]
+    not_admitted = S.stats()["rejected"]
     resident = S.stats()["resident_bytes"]
     g = I.rng(seed, 301)
     arrivals = I.poisson_arrivals(args.serve_rate, args.serve_seconds, seed)
-    pick = g.integers(0, len(ids), arrivals.shape[0])
-    ks = g.integers(1, 9, arrivals.shape[0])
-    pools = {j: list(all_pools[j]) for j, _ in ids}
-    misses = [0]
-    lock = threading.Lock()
-    q = queue.Queue()
-
-    def waiter():
-        while True:
-            item = q.get()
-            if item is None:
-                return
-            j, t, pooled = item
-            S.wait(t)
-            if pooled:
-                with lock:
-                    pools[j].append(t.y)
-
-    # several waiters, so a slow request holds back only its own buffer
-    ths = [threading.Thread(target=waiter, daemon=True) for _ in range(8)]
-    for th in ths:
-        th.start()
-    warm = min(1.0, 0.2 * args.serve_seconds)
-    reset_done = False
-    # the submit loop spins between arrivals; a short interpreter switch
-    # interval lets the waiters hand buffers back without 5 ms delays
-    switch = sys.getswitchinterval()
-    sys.setswitchinterval(1e-4)
-    import gc
-    gc_was = gc.isenabled()
-    gc.disable()   # no collector pauses inside the request stream
-    t0 = time.perf_counter()
-    for i in range(arrivals.shape[0]):
-        target = t0 + arrivals[i]
-        while True:
-            now = time.perf_counter()
-            if now >= target:
-                break
-            if target - now > 2e-4:
-                time.sleep((target - now) * 0.5)
-        if not reset_done and now - t0 >= warm:
-            S.stats(reset=True)
-            reset_done = True
+    n = arrivals.shape[0]
+    pick = g.integers(0, len(ids), n)
+    ks = g.integers(1, 9, n).astype(np.int32)
+    mids = np.empty(n, np.int64)
+    xs, ys = [], []
+    reuse = np.full(n, -1, np.int64)
+    used = {}
+    count = {}
+    for i in range(n):
         j, mid = ids[int(pick[i])]
-        k = int(ks[i])
-        with lock:
-            y = pools[j].pop() if pools[j] else None
-        pooled = True
-        if y is None:
-            misses[0] += 1
-            y = M.native.pinned_empty((8 * mats[j].m,))
-        t = S.submit(mid, X[j][:k], y)
-        q.put((j, t, pooled))
-    sent = time.perf_counter() - t0
-    for _ in ths:
-        q.put(None)
-    for th in ths:
-        th.join()
-    sys.setswitchinterval(switch)
-    if gc_was:
-        gc.enable()
+        mids[i] = mid
+        xs.append(X[j][:int(ks[i])])
+        c = count.get(j, 0)
+        slot = c % len(all_pools[j])
+        count[j] = c + 1
+        ys.append(all_pools[j][slot])
+        reuse[i] = used.get((j, slot), -1)
+        used[(j, slot)] = i
+    warm = min(1.0, 0.2 * args.serve_seconds)
+    late, lag = S.replay(arrivals * 1e6, mids, ks, xs, ys, reuse, reset_after_us=warm * 1e6)
     st = S.stats()
     S.close()
-    st.update({"offered_rate": arrivals.shape[0] / args.serve_seconds,
-               "achieved_submit_s": sent, "matrices": len(mats), "admitted": len(ids),
-               "not_admitted": admitted_rejected,
+    st.update({"offered_rate": n / args.serve_seconds, "requests": n,
+               "late_submissions": late, "max_submit_lag_us": lag,
+               "driver": "msrep_serve_replay (native, open loop)",
+               "matrices": len(mats), "admitted": len(ids), "not_admitted": not_admitted,
                "window_s": args.serve_seconds, "discarded_warmup_s": warm,
-               "budget_bytes": budget, "resident_bytes_after_register": resident,
-               "y_buffer_allocations_in_loop": misses[0]})
+               "budget_bytes": budget, "resident_bytes_after_register": resident})
     return st
 
 

@@ -465,6 +465,24 @@ msrep_status msrep_serve_wait(msrep_server *s, uint64_t req_id, int64_t timeout_
  * or the last reset (reset != 0 clears them after reading). */
 msrep_status msrep_serve_stats(msrep_server *s, msrep_serve_counters *out, int32_t reset);
 
+/* Load driver for measuring the server (no counterpart in the paper): from
+ * the calling thread, submits `count` requests at the given arrival times
+ * (t_us[i] microseconds after the call starts, non-decreasing; the thread
+ * spins until then), request i naming matrix_id[i] with k[i] vectors read
+ * from x[i] and written to y[i] (host buffers as for msrep_serve_submit),
+ * then waits for every request.  Before submitting request i it waits for
+ * request reuse[i] (< i; -1 = none), the last one that used the same y
+ * buffer, which lets a caller recycle buffers without a thread of its own.
+ * With reset_after_us >= 0 the server's statistics are reset once the
+ * stream passes that time (to drop a warm-up).  *late counts the requests
+ * submitted more than 100 us after their arrival time, *max_lag_us is the
+ * largest such delay.  The latency statistics are msrep_serve_stats'.
+ * Syncs.  Errors: INVALID_ARG, and those of submit and wait. */
+msrep_status msrep_serve_replay(msrep_server *s, int64_t count, const double *t_us,
+                                const int64_t *matrix_id, const int32_t *k,
+                                const float *const *x, float *const *y, const int64_t *reuse,
+                                double reset_after_us, int64_t *late, double *max_lag_us);
+
 /* Stops the threads after finishing queued work, frees everything. */
 msrep_status msrep_serve_destroy(msrep_server *s);
 

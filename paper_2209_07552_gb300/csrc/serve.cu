@@ -6,7 +6,9 @@
 //
 // Threads: the caller's threads submit and wait; a scheduler thread packs
 // queued requests into a launch whenever a context (stream + x/y arenas +
-// directory buffers) is free; a completion thread polls each context's
+// directory buffers) is free and hands it to the context's own issuing
+// thread, which issues its copies and kernels (so that the issuing of
+// several launches overlaps); a completion thread polls each context's
 // event, copies y back to the callers' buffers and wakes the waiters.
 // Several contexts are in flight at once, so requests that arrive while
 // others run are admitted as soon as a context frees up, and their work
@@ -86,7 +88,10 @@ struct Context {
   size_t dirk_bytes = 0;
   double *head_k = nullptr, *tail_k = nullptr;
   bool busy = false;      // packed by the scheduler (launching or in flight)
+  bool pending = false;   // packed, waiting for its issuing thread
   bool in_flight = false; // its event has been recorded for this launch
+  std::vector<BatchItem> ritem;  // per request: its matrix
+  std::vector<int64_t> rtiles;   // per request: the matrix's tile count
   std::vector<std::shared_ptr<Request>> reqs;  // in this launch
   std::vector<int64_t> y_off;                  // per request, floats into y arena
   double bytes = 0;                            // algorithmic bytes of the launch
@@ -100,6 +105,7 @@ struct msrep_server {
   std::mutex mu;
   std::condition_variable cv_work;   // scheduler: new request or free context
   std::condition_variable cv_done;   // waiters
+  std::condition_variable cv_issue;  // issuing threads: a context was packed
   std::map<int64_t, msrep::Resident> mats;
   std::deque<std::shared_ptr<msrep::Request>> queue;
   std::unordered_map<uint64_t, std::shared_ptr<msrep::Request>> reqs;
@@ -107,8 +113,9 @@ struct msrep_server {
   int64_t next_matrix = 1;
   uint64_t next_req = 1;
   int64_t resident = 0;
-  bool stop = false;
+  bool stop = false, stop_issuers = false;
   std::thread scheduler, completer;
+  std::vector<std::thread> issuers;  // one per context
   // statistics
   std::vector<double> lat_us;     // submit -> y in the caller's buffer
   std::vector<double> wait_us;    // submit -> packed into a launch (host)
@@ -329,28 +336,49 @@ static void scheduler_loop(msrep_server *s) {
     if (s->inflight++ == 0) s->busy_since = c->t_launch;
     s->launches++;
     for (const auto &r : c->reqs) s->items += r->k;
+    // the context's own thread issues the copies and kernels, so that
+    // several contexts' launches are issued at once while this thread packs
+    // the next
+    c->ritem = std::move(ritem);
+    c->rtiles = std::move(rtiles);
+    c->pending = true;
+    s->cv_issue.notify_all();
+  }
+}
+
+// Issuing thread of context `ci`: runs the launches the scheduler packed
+// into it (server lock not held while issuing).
+static void issuer_loop(msrep_server *s, size_t ci) {
+  cudaSetDevice(s->cfg.device);
+  Context &c = s->ctx[ci];
+  std::unique_lock<std::mutex> lk(s->mu);
+  for (;;) {
+    s->cv_issue.wait(lk, [&] { return c.pending || s->stop_issuers; });
+    if (!c.pending) return;  // stopping, nothing left to issue
     lk.unlock();
     const auto h0 = Clock::now();
-    msrep_status st = launch_context(s, *c, ritem, rtiles);
+    msrep_status st = launch_context(s, c, c.ritem, c.rtiles);
     const double host = std::chrono::duration<double, std::micro>(Clock::now() - h0).count();
     lk.lock();
+    c.pending = false;
     s->host_us.push_back(host);
-    if (st == MSREP_OK) c->in_flight = true;  // only now may its event be polled
+    if (st == MSREP_OK) c.in_flight = true;  // only now may its event be polled
     if (st != MSREP_OK) {
       // fail the requests of this launch; the context stays usable
-      cudaStreamSynchronize(c->stream);
+      cudaStreamSynchronize(c.stream);
       const std::string why = msrep_last_error();
-      for (auto &r : c->reqs) {
+      for (auto &r : c.reqs) {
         r->status = st;
         r->error = why;
         r->done = true;
         s->mats[r->matrix].refs--;
       }
-      c->reqs.clear();
-      c->busy = false;
+      c.reqs.clear();
+      c.busy = false;
       if (--s->inflight == 0)
         s->busy_s += std::chrono::duration<double>(Clock::now() - s->busy_since).count();
       s->cv_done.notify_all();
+      s->cv_work.notify_all();
     }
   }
 }
@@ -488,6 +516,7 @@ msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **ou
   s->resident = per_ctx * cfg->contexts;
   msrep_server *raw = s.release();
   raw->scheduler = std::thread(scheduler_loop, raw);
+  for (size_t ci = 0; ci < raw->ctx.size(); ++ci) raw->issuers.emplace_back(issuer_loop, raw, ci);
   raw->completer = std::thread(completion_loop, raw);
   *out = raw;
   return ok();
@@ -667,6 +696,55 @@ msrep_status msrep_serve_wait(msrep_server *s, uint64_t req_id, int64_t timeout_
   return ok();
 }
 
+msrep_status msrep_serve_replay(msrep_server *s, int64_t count, const double *t_us,
+                                const int64_t *matrix_id, const int32_t *k,
+                                const float *const *x, float *const *y, const int64_t *reuse,
+                                double reset_after_us, int64_t *late, double *max_lag_us) {
+  if (!s || count < 0 || (count > 0 && (!t_us || !matrix_id || !k || !x || !y || !reuse)) ||
+      !late || !max_lag_us)
+    return fail(MSREP_ERR_INVALID_ARG, "NULL argument or negative count");
+  for (int64_t i = 0; i < count; ++i)
+    if (reuse[i] >= i || (i > 0 && t_us[i] < t_us[i - 1]))
+      return fail(MSREP_ERR_INVALID_ARG,
+                  "arrival times must not decrease and reuse[i] must be < i (request %lld)",
+                  (long long)i);
+  std::vector<uint64_t> ids(static_cast<size_t>(count), 0);
+  std::vector<char> collected(static_cast<size_t>(count), 0);
+  *late = 0;
+  *max_lag_us = 0.0;
+  bool reset_done = reset_after_us < 0;
+  msrep_status status = MSREP_OK;
+  const auto t0 = Clock::now();
+  auto since = [&] { return std::chrono::duration<double, std::micro>(Clock::now() - t0).count(); };
+  for (int64_t i = 0; i < count && status == MSREP_OK; ++i) {
+    // the request that last used this request's buffers must be done
+    const int64_t d = reuse[i];
+    if (d >= 0 && !collected[d]) {
+      status = msrep_serve_wait(s, ids[d], -1);
+      collected[d] = 1;
+      if (status != MSREP_OK) break;
+    }
+    while (since() < t_us[i]) {
+    }
+    if (!reset_done && since() >= reset_after_us) {
+      msrep_serve_counters tmp;
+      msrep_serve_stats(s, &tmp, 1);
+      reset_done = true;
+    }
+    const double lag = since() - t_us[i];
+    if (lag > 100.0) ++*late;
+    *max_lag_us = std::max(*max_lag_us, lag);
+    status = msrep_serve_submit(s, matrix_id[i], k[i], x[i], y[i], &ids[i]);
+  }
+  for (int64_t i = 0; i < count; ++i)
+    if (ids[i] && !collected[i]) {
+      const msrep_status w = msrep_serve_wait(s, ids[i], -1);
+      if (status == MSREP_OK) status = w;
+    }
+  if (status != MSREP_OK) return status;
+  return ok();
+}
+
 msrep_status msrep_serve_stats(msrep_server *s, msrep_serve_counters *o, int32_t reset) {
   if (!s || !o) return fail(MSREP_ERR_INVALID_ARG, "NULL argument");
   std::lock_guard<std::mutex> lk(s->mu);
@@ -728,6 +806,14 @@ msrep_status msrep_serve_destroy(msrep_server *s) {
     s->cv_work.notify_all();
   }
   if (s->scheduler.joinable()) s->scheduler.join();
+  {
+    // every packed launch is issued before the issuing threads stop
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop_issuers = true;
+    s->cv_issue.notify_all();
+  }
+  for (auto &t : s->issuers)
+    if (t.joinable()) t.join();
   if (s->completer.joinable()) s->completer.join();
   for (auto &c : s->ctx) free_context(c);
   for (auto &kv : s->mats) cudaFree(kv.second.mem);

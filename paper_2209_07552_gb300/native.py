@@ -151,6 +151,9 @@ SIGNATURES = {
     "msrep_serve_stats": (ctypes.c_int, [_vp, ctypes.POINTER(c_msrep_serve_counters),
                                          ctypes.c_int32]),
     "msrep_serve_destroy": (ctypes.c_int, [_vp]),
+    "msrep_serve_replay": (ctypes.c_int, [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp,
+                                          ctypes.c_double, ctypes.POINTER(ctypes.c_int64),
+                                          ctypes.POINTER(ctypes.c_double)]),
     "msrep_autotune": (ctypes.c_int, [ctypes.c_int32, _M, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_void_p), _vp, ctypes.c_int64,
                                       ctypes.POINTER(c_msrep_tune_table), _vp]),
@@ -616,6 +619,34 @@ class Server:
     def wait(self, t: ServeTicket, timeout_us: int = -1) -> np.ndarray:
         _check(lib().msrep_serve_wait(self.h, t.id, timeout_us))
         return t.result
+
+    def replay(self, t_us, mids, ks, xs, ys, reuse, reset_after_us=-1.0):
+        """Native open-loop driver (msrep_serve_replay): request i arrives
+        t_us[i] us after the call starts, names matrix mids[i] with ks[i]
+        vectors from the host array xs[i] into ys[i]; reuse[i] is the
+        earlier request whose y buffer request i reuses (-1: none).
+        Returns (late submissions, largest submission lag in us)."""
+        n = len(t_us)
+        t = np.ascontiguousarray(t_us, np.float64)
+        mi = np.ascontiguousarray(mids, np.int64)
+        kk = np.ascontiguousarray(ks, np.int32)
+        ru = np.ascontiguousarray(reuse, np.int64)
+        if not (len(mi) == len(kk) == len(ru) == len(xs) == len(ys) == n):
+            raise ValueError("replay: per-request arrays differ in length")
+        for i in range(n):
+            # the native driver reads and writes these buffers in place
+            m, nc = self.shapes.get(int(mi[i]), (0, 0))
+            for a, need in ((xs[i], int(kk[i]) * nc), (ys[i], int(kk[i]) * m)):
+                if a.dtype != np.float32 or not a.flags.c_contiguous or a.size < need:
+                    raise ValueError(f"replay: request {i} needs C-contiguous float32 "
+                                     f"buffers of {need} values")
+        xp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in xs])
+        yp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in ys])
+        late, lag = ctypes.c_int64(), ctypes.c_double()
+        _check(lib().msrep_serve_replay(self.h, n, t.ctypes.data, mi.ctypes.data, kk.ctypes.data,
+                                        xp, yp, ru.ctypes.data, float(reset_after_us),
+                                        ctypes.byref(late), ctypes.byref(lag)))
+        return late.value, lag.value
 
     def stats(self, reset: bool = False) -> dict:
         c = c_msrep_serve_counters()

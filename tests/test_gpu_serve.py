@@ -174,3 +174,47 @@ def test_serve_wait_timeout_then_complete():
         with pytest.raises(M.MsrepError) as e:
             S.wait(t, 0)
         assert e.value.status == 7        # collected already
+
+
+def test_serve_replay_driver():
+    """The native open-loop driver: requests submitted at their arrival
+    times from one native thread, some writing into the y buffer of an
+    earlier request for the same matrix (the driver waits for that request
+    first).  Every buffer ends up holding the result of its last request,
+    equal bit for bit to msrep_spmv of that request's columns; a reuse
+    index that does not point back is refused before anything is
+    submitted."""
+    import paper_2209_07552_gb300 as M
+    mats = _mats(seed=11)
+    g = I.rng(41, 2)
+    X = [g.uniform(-1, 1, (8, a.n)).astype(np.float32) for a in mats]
+    solo = [_solo(M, a, x) for a, x in zip(mats, X)]
+    with M.Server(budget_bytes=4 << 30, arena_bytes=16 << 20, contexts=2) as S:
+        ids = [S.register(a) for a in mats]
+        n = 60
+        t_us = np.cumsum(g.exponential(200.0, n))
+        pick = g.integers(0, len(mats), n)
+        ks = g.integers(1, 9, n).astype(np.int32)
+        bufs, ys, reuse, last = {}, [], np.full(n, -1, np.int64), {}
+        for i in range(n):
+            j = int(pick[i])
+            slot = i % 3 if i >= 30 else i          # later requests share 3 buffers a matrix
+            key = (j, slot)
+            if key not in bufs:
+                bufs[key] = np.full((8, mats[j].m), np.nan, np.float32)
+            ys.append(bufs[key])
+            reuse[i] = last.get(key, -1)
+            last[key] = i
+        xs = [X[int(pick[i])][:int(ks[i])] for i in range(n)]
+        late, lag = S.replay(t_us, [ids[int(p)] for p in pick], ks, xs, ys, reuse)
+        assert late >= 0 and lag >= 0.0
+        assert S.stats()["completed"] == n
+        for key, i in last.items():
+            j, k = key[0], int(ks[i])
+            assert np.array_equal(bufs[key][:k], solo[j][:k]), (key, i, k)
+        bad = reuse.copy()
+        bad[5] = 5
+        with pytest.raises(M.MsrepError) as e:
+            S.replay(t_us, [ids[int(p)] for p in pick], ks, xs, ys, bad)
+        assert e.value.status == 1        # MSREP_ERR_INVALID_ARG
+        assert S.stats()["completed"] == n
