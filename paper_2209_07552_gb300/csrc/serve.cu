@@ -106,6 +106,7 @@ struct msrep_server {
   std::condition_variable cv_work;   // scheduler: new request or free context
   std::condition_variable cv_done;   // waiters
   std::condition_variable cv_issue;  // issuing threads: a context was packed
+  std::condition_variable cv_flight; // completion thread: a launch was issued, or stopping
   std::map<int64_t, msrep::Resident> mats;
   std::deque<std::shared_ptr<msrep::Request>> queue;
   std::unordered_map<uint64_t, std::shared_ptr<msrep::Request>> reqs;
@@ -363,6 +364,7 @@ static void issuer_loop(msrep_server *s, size_t ci) {
     c.pending = false;
     s->host_us.push_back(host);
     if (st == MSREP_OK) c.in_flight = true;  // only now may its event be polled
+    s->cv_flight.notify_all();
     if (st != MSREP_OK) {
       // fail the requests of this launch; the context stays usable
       cudaStreamSynchronize(c.stream);
@@ -383,15 +385,26 @@ static void issuer_loop(msrep_server *s, size_t ci) {
   }
 }
 
+// Completion thread.  With nothing issued it sleeps on cv_flight; while
+// any launch is in flight it polls the contexts' events back to back
+// (yielding between sweeps): a timed sleep between polls would add the
+// kernel's timer slack, tens of microseconds, to every request.
 static void completion_loop(msrep_server *s) {
   cudaSetDevice(s->cfg.device);
   for (;;) {
-    bool any = false, stop = false;
     {
-      std::lock_guard<std::mutex> lk(s->mu);
-      stop = s->stop && s->queue.empty();
-      for (auto &c : s->ctx) any |= c.busy;
-      if (stop && !any) return;
+      std::unique_lock<std::mutex> lk(s->mu);
+      bool any = false;
+      s->cv_flight.wait(lk, [&] {
+        bool flying = false;
+        any = false;
+        for (auto &c : s->ctx) {
+          any |= c.busy;
+          flying |= c.busy && c.in_flight;
+        }
+        return flying || (s->stop && s->queue.empty() && !any);
+      });
+      if (s->stop && s->queue.empty() && !any) return;
     }
     bool progressed = false;
     for (auto &c : s->ctx) {
@@ -442,7 +455,7 @@ static void completion_loop(msrep_server *s) {
       s->cv_done.notify_all();
       s->cv_work.notify_all();
     }
-    if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    if (!progressed) std::this_thread::yield();
   }
 }
 
@@ -804,6 +817,7 @@ msrep_status msrep_serve_destroy(msrep_server *s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop = true;
     s->cv_work.notify_all();
+    s->cv_flight.notify_all();
   }
   if (s->scheduler.joinable()) s->scheduler.join();
   {
@@ -811,6 +825,7 @@ msrep_status msrep_serve_destroy(msrep_server *s) {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stop_issuers = true;
     s->cv_issue.notify_all();
+    s->cv_flight.notify_all();
   }
   for (auto &t : s->issuers)
     if (t.joinable()) t.join();
