@@ -39,15 +39,22 @@ msrep_status launch_batched(const BatchItem *items, const int64_t *toff, int cou
                             double beta, unsigned flags, cudaStream_t st,
                             int cta_threads = 256, int max_tile = 1024);
 
-// Batched k-vector form (FP32 values and vectors): item j carries k_j <= 8
-// vectors, xin[j] = its k_j x vectors of n_j values each (device),
-// xt[j] = device space for n_j * kBatchWidth values (filled here with the
-// interleaved x), ys[j] = its k_j y vectors of m_j values.  Tiles numbered
-// by toff as for launch_batched; head, tail: total_tiles * kBatchWidth
-// doubles each.  y = A x for every vector (alpha 1, beta 0).  Asynchronous.
-msrep_status launch_batched_k(const BatchItem *items, const int64_t *toff, int count,
-                              int64_t total_tiles, const void *const *xin, void *const *xt,
-                              void *const *ys, double *head, double *tail, unsigned flags,
-                              cudaStream_t st);
+// Batched k-vector form (FP32 values and vectors): item j carries
+// 2 <= k_j <= 8 vectors, xin[j] = its k_j x vectors of n_j values each
+// (device), xt[j] = device space for n_j * kBatchWidth values (filled here
+// with the x interleaved by width spmm_width(k_j)), ys[j] = its k_j y
+// vectors of m_j values.  Tiles numbered by toff as for launch_batched;
+// uoff (count+1 entries, device) numbers the block work units, item j
+// having batched_k_units(tiles_j, k_j) of them, total_units in all; head,
+// tail: total_tiles * kBatchWidth doubles each.  y = A x for every vector
+// (alpha 1, beta 0).  Asynchronous.
+msrep_status launch_batched_k(const BatchItem *items, const int64_t *toff, const int64_t *uoff,
+                              int count, int64_t total_tiles, int64_t total_units,
+                              const void *const *xin, void *const *xt, void *const *ys,
+                              double *head, double *tail, unsigned flags, cudaStream_t st);
+
+// block work units of an item of `tiles` tiles and k vectors in the
+// batched k-vector kernel
+int64_t batched_k_units(int64_t tiles, int k);
 
 }  // namespace msrep

@@ -136,9 +136,10 @@ static size_t dir_size(int32_t max_items) {
          2 * align256(sizeof(void *) * max_items);
 }
 
-// k-vector directory: items | toff | xin | xt | ys
+// k-vector directory: items | toff | uoff | xin | xt | ys
 static size_t dirk_size(int32_t max_items) {
-  return align256(sizeof(BatchItem) * max_items) + align256(sizeof(int64_t) * (max_items + 1)) +
+  return align256(sizeof(BatchItem) * max_items) +
+         2 * align256(sizeof(int64_t) * (max_items + 1)) +
          3 * align256(sizeof(void *) * max_items);
 }
 
@@ -187,13 +188,15 @@ static msrep_status launch_context(msrep_server *s, Context &c,
   size_t ok_ = align256(sizeof(BatchItem) * N);
   int64_t *toffk = reinterpret_cast<int64_t *>(kp + ok_);
   ok_ += align256(sizeof(int64_t) * (N + 1));
+  int64_t *uoffk = reinterpret_cast<int64_t *>(kp + ok_);
+  ok_ += align256(sizeof(int64_t) * (N + 1));
   const void **xin = reinterpret_cast<const void **>(kp + ok_);
   ok_ += align256(sizeof(void *) * N);
   void **xtp = reinterpret_cast<void **>(kp + ok_);
   ok_ += align256(sizeof(void *) * N);
   void **ysk = reinterpret_cast<void **>(kp + ok_);
 
-  int64_t xo = 0, yo = 0, xto = 0, tt = 0, ttk = 0;
+  int64_t xo = 0, yo = 0, xto = 0, tt = 0, ttk = 0, utk = 0;
   int n1 = 0, nk = 0;
   c.y_off.clear();
   MSREP_CUDA_TRY(cudaEventRecord(c.begin_ev, c.stream));
@@ -219,7 +222,9 @@ static msrep_status launch_context(msrep_server *s, Context &c,
       itk[nk] = bi;
       itk[nk].k = r->k;
       toffk[nk] = ttk;
+      uoffk[nk] = utk;
       ttk += rtiles[i];
+      utk += batched_k_units(rtiles[i], r->k);
       xin[nk] = c.x_dev + xo;
       xtp[nk] = c.xt_dev + xto;
       ysk[nk] = c.y_dev + yo;
@@ -231,6 +236,7 @@ static msrep_status launch_context(msrep_server *s, Context &c,
   }
   toff[n1] = tt;
   toffk[nk] = ttk;
+  uoffk[nk] = utk;
   MSREP_CUDA_TRY(cudaEventRecord(c.k0_ev, c.stream));
   if (n1 > 0) {
     MSREP_CUDA_TRY(cudaMemcpyAsync(c.dir_dev, c.dir_pin, c.dir_bytes, cudaMemcpyHostToDevice, c.stream));
@@ -251,13 +257,15 @@ static msrep_status launch_context(msrep_server *s, Context &c,
     size_t q = align256(sizeof(BatchItem) * N);
     const int64_t *dtoff = reinterpret_cast<const int64_t *>(dd + q);
     q += align256(sizeof(int64_t) * (N + 1));
+    const int64_t *duoff = reinterpret_cast<const int64_t *>(dd + q);
+    q += align256(sizeof(int64_t) * (N + 1));
     const void *const *dxin = reinterpret_cast<const void *const *>(dd + q);
     q += align256(sizeof(void *) * N);
     void *const *dxt = reinterpret_cast<void *const *>(dd + q);
     q += align256(sizeof(void *) * N);
     void *const *dys = reinterpret_cast<void *const *>(dd + q);
-    MSREP_TRY(launch_batched_k(reinterpret_cast<const BatchItem *>(dd), dtoff, nk, ttk, dxin, dxt,
-                               dys, c.head_k, c.tail_k, 0, c.stream));
+    MSREP_TRY(launch_batched_k(reinterpret_cast<const BatchItem *>(dd), dtoff, duoff, nk, ttk,
+                               utk, dxin, dxt, dys, c.head_k, c.tail_k, 0, c.stream));
   }
   MSREP_CUDA_TRY(cudaEventRecord(c.k1_ev, c.stream));
   for (size_t i = 0; i < c.reqs.size(); ++i) {

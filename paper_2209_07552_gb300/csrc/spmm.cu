@@ -18,12 +18,6 @@ namespace msrep {
 msrep_status check_matrix(const msrep_matrix *A);
 int32_t effective_tile(int32_t tile);
 
-constexpr int kKWarps = 8;
-constexpr int kKThreads = 32 * kKWarps;
-constexpr int kKMaxIPT = 32;  // row-pointer stage sized for the largest tile (1024)
-
-int spmm_width(int k) { return k <= 1 ? 1 : k <= 2 ? 2 : k <= 4 ? 4 : 8; }
-
 // xt[c * KP + j] = x[j * ldx + c] for j < k, 0 for k <= j < KP; a thread
 // per column: coalesced reads of each vector, one KP-wide write
 template <class X, int KP>
@@ -44,23 +38,15 @@ __global__ void interleave_x(const X *x, int64_t ldx, int k, int64_t n, X *xt) {
 }
 
 template <class Pol, int KP>
-__global__ void __launch_bounds__(kKThreads, 2) csr_spmm_direct(SpmmArgs<Pol, KP> a,
-                                                                const int32_t *n_tiles,
-                                                                int64_t nnz) {
-  __shared__ int32_t s_rp[kKWarps][32 * kKMaxIPT + 8];
-  extern __shared__ __align__(16) unsigned char s_stage[];
+__global__ void __launch_bounds__(kKvThreads) csr_spmm_direct(SpmmArgs<Pol, KP> a,
+                                                              const int32_t *n_tiles,
+                                                              int64_t nnz) {
+  using Sh = KvShape<typename Pol::X, KP>;
+  __shared__ KvSmem<typename Pol::Acc, Sh::G> sm;
   grid_dependency_wait();
-  const int T = *n_tiles, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char *stage = s_stage + threadIdx.x * SpmmStage<Pol, KP>::LANE;
-  for (int b = blockIdx.x * kKWarps + wid; b < T; b += gridDim.x * kKWarps) {
-    const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
-    const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
-    const int32_t rend = min(r1 + 2, a.m + 1);
-    for (int32_t r = r0 + lane; r < rend; r += 32) s_rp[wid][r - r0] = __ldg(a.row_ptr + r);
-    __syncwarp();
-    csr_tile_compute_k<Pol, KP>(a, b, r0, k0, r1, k1, s_rp[wid], nnz, stage);
-    __syncwarp();
-  }
+  const int T = *n_tiles, ts = threadIdx.x / Sh::GT;
+  for (int b = blockIdx.x * Sh::G + ts; b < T; b += gridDim.x * Sh::G)
+    kv_tile<Pol, KP, Sh::G>(a, b, nnz, sm, ts);
 }
 
 template <class X, int KP>
@@ -90,7 +76,7 @@ static msrep_status blocks_of(K kern, size_t dyn, int want, int *nb) {
   MSREP_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(dyn)));
   MSREP_TRY(set_min_carveout(reinterpret_cast<const void *>(kern), dyn, want));
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, kKThreads, dyn) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, kern, kKvThreads, dyn) != cudaSuccess ||
       *nb < 1)
     *nb = 1;
   cache[key] = *nb;
@@ -149,15 +135,16 @@ static msrep_status run_spmm(const msrep_matrix *A, const msrep_partition *p, in
   a.tile_k = reinterpret_cast<const int32_t *>(plan + L.off_k);
   a.head = head;
   a.tail = tail;
+  a.hs = KP;
   a.m = A->m;
   a.comp_mode = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
   const int32_t *n_tiles = reinterpret_cast<const int32_t *>(plan + L.off_toff) + p->np;
   int nb = 1;
-  constexpr size_t dyn = size_t(kKWarps) * SpmmStage<Pol, KP>::WARP;
-  MSREP_TRY(blocks_of(csr_spmm_direct<Pol, KP>, dyn, 2, &nb));
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.tmax, kKWarps),
+  MSREP_TRY(blocks_of(csr_spmm_direct<Pol, KP>, 0, 2, &nb));
+  constexpr int G = KvShape<X, KP>::G;
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.tmax, G),
                                                              int64_t(nb) * sm_count()));
-  MSREP_TRY(launch_dependent(csr_spmm_direct<Pol, KP>, grid, kKThreads, st, dyn, a, n_tiles,
+  MSREP_TRY(launch_dependent(csr_spmm_direct<Pol, KP>, grid, kKvThreads, st, 0, a, n_tiles,
                              A->nnz));
   CsrTileView v{a.tile_row, a.tile_k, A->ptr, n_tiles};
   const int64_t fg = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.tmax, 256), 4 * sm_count()));
@@ -196,55 +183,75 @@ __device__ __forceinline__ int owner_item_k(const int64_t *toff, int count, int6
   return lo;
 }
 
+// one block work unit of an item: tile u * G + ts by tile group ts
+template <class Pol, int KP>
+__device__ __forceinline__ void batched_unit(const BatchItem &it, int64_t base, int T, int u,
+                                             const void *xt, void *y, double *head,
+                                             double *tail, unsigned comp_mode,
+                                             KvSmem<typename Pol::Acc, 8> &sm) {
+  using Sh = KvShape<typename Pol::X, KP>;
+  const int ts = threadIdx.x / Sh::GT, b = u * Sh::G + ts;
+  if (b >= T) return;  // uniform over the tile group
+  SpmmArgs<Pol, KP> a;
+  a.row_ptr = it.row_ptr;
+  a.col_idx = it.col_idx;
+  a.val = static_cast<const typename Pol::V *>(it.val);
+  a.xt = static_cast<const typename Pol::X *>(xt);
+  a.y = static_cast<typename Pol::X *>(y);
+  a.ldy = it.m;
+  a.k = it.k;
+  a.alpha = 1.0;
+  a.beta = 0.0;
+  a.finish = kFinishCopy;
+  a.tile_row = it.tile_row;
+  a.tile_k = it.tile_k;
+  a.head = head + base * kBatchWidth;
+  a.tail = tail + base * kBatchWidth;
+  a.hs = kBatchWidth;
+  a.m = it.m;
+  a.comp_mode = comp_mode;
+  kv_tile<Pol, KP, 8>(a, b, it.nnz, sm, ts);
+}
+
+// Items of 2..8 vectors; item j's x interleaved with width KP_j =
+// spmm_width(k_j) and its tiles cut into uoff[j+1] - uoff[j] block work
+// units of KvShape<float, KP_j>::G tiles, one unit per block at a time.
+// Tile groups run ahead of each other within a layout; where the layout
+// (KP) changes from one unit to the next the block synchronises, because
+// the two layouts share shared-memory slots differently.
 template <class Pol>
-__global__ void __launch_bounds__(kKThreads, 2) batched_spmm(const BatchItem *items,
-                                                             const int64_t *toff, int count,
-                                                             const void *const *xs,
-                                                             void *const *ys, double *head,
-                                                             double *tail, unsigned comp_mode) {
-  constexpr int KP = kBatchWidth;
-  __shared__ int32_t s_rp[kKWarps][32 * kKMaxIPT + 8];
-  extern __shared__ __align__(16) unsigned char s_stage[];
+__global__ void __launch_bounds__(kKvThreads) batched_spmm(const BatchItem *items,
+                                                           const int64_t *toff,
+                                                           const int64_t *uoff, int count,
+                                                           const void *const *xs,
+                                                           void *const *ys, double *head,
+                                                           double *tail, unsigned comp_mode) {
+  __shared__ KvSmem<typename Pol::Acc, 8> sm;
   grid_dependency_wait();
-  unsigned char *stage = s_stage + threadIdx.x * SpmmStage<Pol, KP>::LANE;
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t total = __ldg(toff + count);
-  int j = 0;
-  for (int64_t g = int64_t(blockIdx.x) * kKWarps + wid; g < total;
-       g += int64_t(gridDim.x) * kKWarps) {
+  const int64_t total = __ldg(uoff + count);
+  int j = 0, prev_kp = 0;
+  for (int64_t g = blockIdx.x; g < total; g += gridDim.x) {
     int step = 0;
-    while (step < 4 && j + 1 < count && __ldg(toff + j + 1) <= g) {
+    while (step < 4 && j + 1 < count && __ldg(uoff + j + 1) <= g) {
       ++j;
       ++step;
     }
-    if (step == 4) j = owner_item_k(toff, count, g);
+    if (step == 4) j = owner_item_k(uoff, count, g);
     const BatchItem it = items[j];
     const int64_t base = __ldg(toff + j);
-    const int b = static_cast<int>(g - base);
-    SpmmArgs<Pol, KP> a;
-    a.row_ptr = it.row_ptr;
-    a.col_idx = it.col_idx;
-    a.val = static_cast<const typename Pol::V *>(it.val);
-    a.xt = static_cast<const typename Pol::X *>(xs[j]);
-    a.y = static_cast<typename Pol::X *>(ys[j]);
-    a.ldy = it.m;
-    a.k = it.k;
-    a.alpha = 1.0;
-    a.beta = 0.0;
-    a.finish = kFinishCopy;
-    a.tile_row = it.tile_row;
-    a.tile_k = it.tile_k;
-    a.head = head + base * KP;
-    a.tail = tail + base * KP;
-    a.m = it.m;
-    a.comp_mode = comp_mode;
-    const int32_t r0 = __ldg(a.tile_row + b), k0 = __ldg(a.tile_k + b);
-    const int32_t r1 = __ldg(a.tile_row + b + 1), k1 = __ldg(a.tile_k + b + 1);
-    const int32_t rend = min(r1 + 2, a.m + 1);
-    for (int32_t r = r0 + lane; r < rend; r += 32) s_rp[wid][r - r0] = __ldg(a.row_ptr + r);
-    __syncwarp();
-    csr_tile_compute_k<Pol, KP>(a, b, r0, k0, r1, k1, s_rp[wid], it.nnz, stage);
-    __syncwarp();
+    const int T = static_cast<int>(__ldg(toff + j + 1) - base);
+    const int u = static_cast<int>(g - __ldg(uoff + j));
+    const int kp = spmm_width(it.k);
+    if (kp != prev_kp) {
+      __syncthreads();
+      prev_kp = kp;
+    }
+    if (kp == 2)
+      batched_unit<Pol, 2>(it, base, T, u, xs[j], ys[j], head, tail, comp_mode, sm);
+    else if (kp == 4)
+      batched_unit<Pol, 4>(it, base, T, u, xs[j], ys[j], head, tail, comp_mode, sm);
+    else
+      batched_unit<Pol, 8>(it, base, T, u, xs[j], ys[j], head, tail, comp_mode, sm);
   }
 }
 
@@ -272,7 +279,8 @@ __global__ void batched_fixup_k(const BatchItem *items, const int64_t *toff, int
   }
 }
 
-// blockIdx.y = item (grid-stride), blocks along x share the item's columns
+// blockIdx.y = item (grid-stride), blocks along x share the item's
+// columns; item j is interleaved with width spmm_width(k_j)
 template <class X>
 __global__ void interleave_batch(const BatchItem *items, int count, const void *const *xin,
                                  void *const *xt) {
@@ -280,16 +288,30 @@ __global__ void interleave_batch(const BatchItem *items, int count, const void *
     const BatchItem it = items[j];
     const X *x = static_cast<const X *>(xin[j]);
     X *o = static_cast<X *>(xt[j]);
+    const int kp = spmm_width(it.k);
     for (int64_t c = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; c < it.n;
-         c += int64_t(gridDim.x) * blockDim.x)
-      interleave_column<X, kBatchWidth>(x, it.n, it.k, c, o);
+         c += int64_t(gridDim.x) * blockDim.x) {
+      if (kp == 2)
+        interleave_column<X, 2>(x, it.n, it.k, c, o);
+      else if (kp == 4)
+        interleave_column<X, 4>(x, it.n, it.k, c, o);
+      else
+        interleave_column<X, 8>(x, it.n, it.k, c, o);
+    }
   }
 }
 
-msrep_status launch_batched_k(const BatchItem *items, const int64_t *toff, int count,
-                              int64_t total_tiles, const void *const *xin, void *const *xt,
-                              void *const *ys, double *head, double *tail, unsigned flags,
-                              cudaStream_t st) {
+int64_t batched_k_units(int64_t tiles, int k) {
+  const int kp = spmm_width(k);
+  const int g = kp == 2 ? KvShape<float, 2>::G : kp == 4 ? KvShape<float, 4>::G
+                                                         : KvShape<float, 8>::G;
+  return (tiles + g - 1) / g;
+}
+
+msrep_status launch_batched_k(const BatchItem *items, const int64_t *toff, const int64_t *uoff,
+                              int count, int64_t total_tiles, int64_t total_units,
+                              const void *const *xin, void *const *xt, void *const *ys,
+                              double *head, double *tail, unsigned flags, cudaStream_t st) {
   if (count == 0) return MSREP_OK;
   const int sms = sm_count();
   interleave_batch<float><<<dim3(64, std::min(count, 1024)), 256, 0, st>>>(items, count, xin, xt);
@@ -297,12 +319,11 @@ msrep_status launch_batched_k(const BatchItem *items, const int64_t *toff, int c
   if (total_tiles == 0) return MSREP_OK;
   const unsigned comp = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
   int nb = 1;
-  constexpr size_t dyn = size_t(kKWarps) * SpmmStage<PolF32<float>, kBatchWidth>::WARP;
-  MSREP_TRY(blocks_of(batched_spmm<PolF32<float>>, dyn, 2, &nb));
-  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(total_tiles, kKWarps),
-                                                             int64_t(nb) * sms));
-  MSREP_TRY(launch_dependent(batched_spmm<PolF32<float>>, grid, kKThreads, st, dyn, items, toff,
-                             count, static_cast<const void *const *>(xt), ys, head, tail, comp));
+  MSREP_TRY(blocks_of(batched_spmm<PolF32<float>>, 0, 2, &nb));
+  const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(total_units, int64_t(nb) * sms));
+  MSREP_TRY(launch_dependent(batched_spmm<PolF32<float>>, grid, kKvThreads, st, 0, items, toff,
+                             uoff, count, static_cast<const void *const *>(xt), ys, head, tail,
+                             comp));
   const int64_t fg = std::max<int64_t>(1, std::min<int64_t>(ceil_div(total_tiles, 256), 4 * sms));
   MSREP_TRY(launch_dependent(batched_fixup_k<float>, fg, 256, st, 0, items, toff, count, ys,
                              static_cast<const double *>(head), static_cast<const double *>(tail)));
