@@ -63,6 +63,10 @@ struct Request {
   float *y;
   Clock::time_point t_submit;
   bool x_pinned = false, y_pinned = false;  // page-locked: DMA directly
+  // page-locked and mapped: the device address of x / y, which the launch's
+  // copy kernels read and write directly (no per-request copy)
+  const float *x_map = nullptr;
+  float *y_map = nullptr;
   bool done = false;
   msrep_status status = MSREP_OK;
   std::string error;  // why the request failed, when it did
@@ -76,16 +80,15 @@ struct Context {
   float *x_dev = nullptr, *y_dev = nullptr;    // arenas
   float *x_pin = nullptr, *y_pin = nullptr;    // pinned staging
   int64_t arena_floats = 0;
-  char *dir_dev = nullptr;                     // items | toff | xs | ys
+  // the launch directory (LaunchDir), built in dir_pin and copied to dir_dev
+  char *dir_dev = nullptr;
   char *dir_pin = nullptr;
   size_t dir_bytes = 0;
   double *head = nullptr, *tail = nullptr;
   int64_t max_tiles = 0;
-  // k-vector requests: interleaved x arena, directory, partials (x8)
+  // k-vector requests: interleaved x arena, partials (x8)
   float *xt_dev = nullptr;
   int64_t xt_floats = 0;
-  char *dirk_dev = nullptr, *dirk_pin = nullptr;
-  size_t dirk_bytes = 0;
   double *head_k = nullptr, *tail_k = nullptr;
   bool busy = false;      // packed by the scheduler (launching or in flight)
   bool pending = false;   // packed, waiting for its issuing thread
@@ -131,16 +134,38 @@ struct msrep_server {
 
 namespace msrep {
 
-static size_t dir_size(int32_t max_items) {
-  return align256(sizeof(BatchItem) * max_items) + align256(sizeof(int64_t) * (max_items + 1)) +
-         2 * align256(sizeof(void *) * max_items);
+// one copy of a launch's copy lists: n floats from src to dst, both
+// device-accessible (the arenas, or mapped page-locked caller buffers)
+struct CopyItem {
+  const float *src;
+  float *dst;
+  int64_t n;
+};
+
+// The copy lists of a launch: blockIdx.y walks the items, the blocks along
+// x share an item's floats (16-byte accesses where both ends allow).
+__global__ void serve_copy(const CopyItem *items, int count) {
+  for (int j = blockIdx.y; j < count; j += gridDim.y) {
+    const CopyItem c = items[j];
+    const bool vec = ((reinterpret_cast<uintptr_t>(c.src) | reinterpret_cast<uintptr_t>(c.dst)) & 15) == 0;
+    const int64_t t0 = blockIdx.x * int64_t(blockDim.x) + threadIdx.x, step = int64_t(gridDim.x) * blockDim.x;
+    int64_t done = 0;
+    if (vec) {
+      const int64_t n4 = c.n / 4;
+      const float4 *s4 = reinterpret_cast<const float4 *>(c.src);
+      float4 *d4 = reinterpret_cast<float4 *>(c.dst);
+      for (int64_t i = t0; i < n4; i += step) d4[i] = s4[i];
+      done = 4 * n4;
+    }
+    for (int64_t i = done + t0; i < c.n; i += step) c.dst[i] = c.src[i];
+  }
 }
 
-// k-vector directory: items | toff | uoff | xin | xt | ys
-static size_t dirk_size(int32_t max_items) {
-  return align256(sizeof(BatchItem) * max_items) +
-         2 * align256(sizeof(int64_t) * (max_items + 1)) +
-         3 * align256(sizeof(void *) * max_items);
+static msrep_status launch_copies(const CopyItem *items, int count, cudaStream_t st) {
+  if (count == 0) return MSREP_OK;
+  serve_copy<<<dim3(32, std::min(count, 1024)), 256, 0, st>>>(items, count);
+  MSREP_CUDA_TRY(cudaGetLastError());
+  return MSREP_OK;
 }
 
 static void free_context(Context &c) {
@@ -151,10 +176,8 @@ static void free_context(Context &c) {
   cudaFree(c.head);
   cudaFree(c.tail);
   cudaFree(c.xt_dev);
-  cudaFree(c.dirk_dev);
   cudaFree(c.head_k);
   cudaFree(c.tail_k);
-  cudaFreeHost(c.dirk_pin);
   cudaFreeHost(c.x_pin);
   cudaFreeHost(c.y_pin);
   cudaFreeHost(c.dir_pin);
@@ -166,46 +189,83 @@ static void free_context(Context &c) {
   c = Context{};
 }
 
-// Launch the requests in c.reqs (scheduler thread, server lock NOT held
-// while copying; the matrices they name are pinned by their refs).  ritem /
-// rtiles: each request's matrix and its tile count.
+// Per-launch directory, laid out for the launch's R requests (so that one
+// copy of about 250 bytes a request carries it): the SpMV items (one-vector
+// requests) with their tile offsets and x / y pointers, the copy lists
+// (x in, y out), and the k-vector items with tile and unit offsets and
+// their x / interleaved-x / y pointers.
+struct LaunchDir {
+  size_t items, toff, xs, ys, cin, cout, itk, toffk, uoffk, xin, xtp, ysk, bytes;
+  explicit LaunchDir(size_t R) {
+    size_t o = 0;
+    auto take = [&o](size_t b) {
+      const size_t at = o;
+      o = (o + b + 15) & ~size_t(15);
+      return at;
+    };
+    items = take(sizeof(BatchItem) * R);
+    toff = take(sizeof(int64_t) * (R + 1));
+    xs = take(sizeof(void *) * R);
+    ys = take(sizeof(void *) * R);
+    cin = take(sizeof(CopyItem) * R);
+    cout = take(sizeof(CopyItem) * R);
+    itk = take(sizeof(BatchItem) * R);
+    toffk = take(sizeof(int64_t) * (R + 1));
+    uoffk = take(sizeof(int64_t) * (R + 1));
+    xin = take(sizeof(void *) * R);
+    xtp = take(sizeof(void *) * R);
+    ysk = take(sizeof(void *) * R);
+    bytes = o;
+  }
+};
+
+static size_t dir_size(int32_t max_items) { return LaunchDir(size_t(max_items)).bytes; }
+
+// Launch the requests in c.reqs (the context's issuing thread, server lock
+// NOT held; the matrices they name are pinned by their refs).  ritem /
+// rtiles: each request's matrix and its tile count.  Mapped page-locked x
+// and y are read and written by the launch's kernels directly: x of a
+// one-vector request is copied into the arena by one copy kernel (the
+// SpMV gathers it at random), x of a k-vector request is read by the
+// interleaving kernel itself, and every mapped y is written by one copy
+// kernel at the end.  Other buffers take one DMA copy each (staged through
+// the pinned arenas when pageable).
 static msrep_status launch_context(msrep_server *s, Context &c,
                                    const std::vector<BatchItem> &ritem,
                                    const std::vector<int64_t> &rtiles) {
-  const int N = s->cfg.max_items;
-  // SpMV directory (requests with one vector, one item per vector)
+  const size_t R = c.reqs.size();
+  const LaunchDir L(R);
+  if (L.bytes > c.dir_bytes) return fail(MSREP_ERR_INVALID_ARG, "launch directory too large");
   char *dp = c.dir_pin;
-  BatchItem *it = reinterpret_cast<BatchItem *>(dp);
-  size_t o = align256(sizeof(BatchItem) * N);
-  int64_t *toff = reinterpret_cast<int64_t *>(dp + o);
-  o += align256(sizeof(int64_t) * (N + 1));
-  const void **xs = reinterpret_cast<const void **>(dp + o);
-  o += align256(sizeof(void *) * N);
-  void **ys = reinterpret_cast<void **>(dp + o);
-  // k-vector directory
-  char *kp = c.dirk_pin;
-  BatchItem *itk = reinterpret_cast<BatchItem *>(kp);
-  size_t ok_ = align256(sizeof(BatchItem) * N);
-  int64_t *toffk = reinterpret_cast<int64_t *>(kp + ok_);
-  ok_ += align256(sizeof(int64_t) * (N + 1));
-  int64_t *uoffk = reinterpret_cast<int64_t *>(kp + ok_);
-  ok_ += align256(sizeof(int64_t) * (N + 1));
-  const void **xin = reinterpret_cast<const void **>(kp + ok_);
-  ok_ += align256(sizeof(void *) * N);
-  void **xtp = reinterpret_cast<void **>(kp + ok_);
-  ok_ += align256(sizeof(void *) * N);
-  void **ysk = reinterpret_cast<void **>(kp + ok_);
+  BatchItem *it = reinterpret_cast<BatchItem *>(dp + L.items);
+  int64_t *toff = reinterpret_cast<int64_t *>(dp + L.toff);
+  const void **xs = reinterpret_cast<const void **>(dp + L.xs);
+  void **ys = reinterpret_cast<void **>(dp + L.ys);
+  CopyItem *cin = reinterpret_cast<CopyItem *>(dp + L.cin);
+  CopyItem *cout = reinterpret_cast<CopyItem *>(dp + L.cout);
+  BatchItem *itk = reinterpret_cast<BatchItem *>(dp + L.itk);
+  int64_t *toffk = reinterpret_cast<int64_t *>(dp + L.toffk);
+  int64_t *uoffk = reinterpret_cast<int64_t *>(dp + L.uoffk);
+  const void **xin = reinterpret_cast<const void **>(dp + L.xin);
+  void **xtp = reinterpret_cast<void **>(dp + L.xtp);
+  void **ysk = reinterpret_cast<void **>(dp + L.ysk);
 
   int64_t xo = 0, yo = 0, xto = 0, tt = 0, ttk = 0, utk = 0;
-  int n1 = 0, nk = 0;
+  int n1 = 0, nk = 0, nci = 0, nco = 0;
   c.y_off.clear();
   MSREP_CUDA_TRY(cudaEventRecord(c.begin_ev, c.stream));
-  for (size_t i = 0; i < c.reqs.size(); ++i) {
+  for (size_t i = 0; i < R; ++i) {
     const auto &r = c.reqs[i];
     const BatchItem &bi = ritem[i];
     c.y_off.push_back(yo);
-    const size_t xb = sizeof(float) * size_t(bi.n) * r->k;
-    if (r->x_pinned) {
+    const int64_t nx = int64_t(bi.n) * r->k;
+    const size_t xb = sizeof(float) * size_t(nx);
+    const float *xsrc = c.x_dev + xo;  // where the kernels read this request's x
+    if (r->x_map && r->k > 1) {
+      xsrc = r->x_map;
+    } else if (r->x_map) {
+      cin[nci++] = CopyItem{r->x_map, c.x_dev + xo, nx};
+    } else if (r->x_pinned) {
       MSREP_CUDA_TRY(cudaMemcpyAsync(c.x_dev + xo, r->x, xb, cudaMemcpyHostToDevice, c.stream));
     } else {
       std::memcpy(c.x_pin + xo, r->x, xb);
@@ -215,7 +275,7 @@ static msrep_status launch_context(msrep_server *s, Context &c,
       it[n1] = bi;
       toff[n1] = tt;
       tt += rtiles[i];
-      xs[n1] = c.x_dev + xo;
+      xs[n1] = xsrc;
       ys[n1] = c.y_dev + yo;
       ++n1;
     } else {
@@ -225,52 +285,43 @@ static msrep_status launch_context(msrep_server *s, Context &c,
       uoffk[nk] = utk;
       ttk += rtiles[i];
       utk += batched_k_units(rtiles[i], r->k);
-      xin[nk] = c.x_dev + xo;
+      xin[nk] = xsrc;
       xtp[nk] = c.xt_dev + xto;
       ysk[nk] = c.y_dev + yo;
       xto += int64_t(bi.n) * kBatchWidth;
       ++nk;
     }
-    xo += int64_t(bi.n) * r->k;
+    if (r->y_map) cout[nco++] = CopyItem{c.y_dev + yo, r->y_map, int64_t(bi.m) * r->k};
+    xo += nx;
     yo += int64_t(bi.m) * r->k;
   }
   toff[n1] = tt;
   toffk[nk] = ttk;
   uoffk[nk] = utk;
+  const char *dd = c.dir_dev;
+  MSREP_CUDA_TRY(cudaMemcpyAsync(c.dir_dev, c.dir_pin, L.bytes, cudaMemcpyHostToDevice, c.stream));
+  MSREP_TRY(launch_copies(reinterpret_cast<const CopyItem *>(dd + L.cin), nci, c.stream));
   MSREP_CUDA_TRY(cudaEventRecord(c.k0_ev, c.stream));
-  if (n1 > 0) {
-    MSREP_CUDA_TRY(cudaMemcpyAsync(c.dir_dev, c.dir_pin, c.dir_bytes, cudaMemcpyHostToDevice, c.stream));
-    const char *dd = c.dir_dev;
-    size_t q = align256(sizeof(BatchItem) * N);
-    const int64_t *dtoff = reinterpret_cast<const int64_t *>(dd + q);
-    q += align256(sizeof(int64_t) * (N + 1));
-    const void *const *dxs = reinterpret_cast<const void *const *>(dd + q);
-    q += align256(sizeof(void *) * N);
-    void *const *dys = reinterpret_cast<void *const *>(dd + q);
-    MSREP_TRY(launch_batched(reinterpret_cast<const BatchItem *>(dd), dtoff, n1, tt, MSREP_F32,
-                             dxs, dys, c.head, c.tail, 1.0, 0.0, 0, c.stream));
-  }
-  if (nk > 0) {
-    MSREP_CUDA_TRY(cudaMemcpyAsync(c.dirk_dev, c.dirk_pin, c.dirk_bytes, cudaMemcpyHostToDevice,
-                                   c.stream));
-    const char *dd = c.dirk_dev;
-    size_t q = align256(sizeof(BatchItem) * N);
-    const int64_t *dtoff = reinterpret_cast<const int64_t *>(dd + q);
-    q += align256(sizeof(int64_t) * (N + 1));
-    const int64_t *duoff = reinterpret_cast<const int64_t *>(dd + q);
-    q += align256(sizeof(int64_t) * (N + 1));
-    const void *const *dxin = reinterpret_cast<const void *const *>(dd + q);
-    q += align256(sizeof(void *) * N);
-    void *const *dxt = reinterpret_cast<void *const *>(dd + q);
-    q += align256(sizeof(void *) * N);
-    void *const *dys = reinterpret_cast<void *const *>(dd + q);
-    MSREP_TRY(launch_batched_k(reinterpret_cast<const BatchItem *>(dd), dtoff, duoff, nk, ttk,
-                               utk, dxin, dxt, dys, c.head_k, c.tail_k, 0, c.stream));
-  }
+  if (n1 > 0)
+    MSREP_TRY(launch_batched(reinterpret_cast<const BatchItem *>(dd + L.items),
+                             reinterpret_cast<const int64_t *>(dd + L.toff), n1, tt, MSREP_F32,
+                             reinterpret_cast<const void *const *>(dd + L.xs),
+                             reinterpret_cast<void *const *>(dd + L.ys), c.head, c.tail, 1.0, 0.0,
+                             0, c.stream));
+  if (nk > 0)
+    MSREP_TRY(launch_batched_k(reinterpret_cast<const BatchItem *>(dd + L.itk),
+                               reinterpret_cast<const int64_t *>(dd + L.toffk),
+                               reinterpret_cast<const int64_t *>(dd + L.uoffk), nk, ttk, utk,
+                               reinterpret_cast<const void *const *>(dd + L.xin),
+                               reinterpret_cast<void *const *>(dd + L.xtp),
+                               reinterpret_cast<void *const *>(dd + L.ysk), c.head_k, c.tail_k, 0,
+                               c.stream));
   MSREP_CUDA_TRY(cudaEventRecord(c.k1_ev, c.stream));
-  for (size_t i = 0; i < c.reqs.size(); ++i) {
+  MSREP_TRY(launch_copies(reinterpret_cast<const CopyItem *>(dd + L.cout), nco, c.stream));
+  for (size_t i = 0; i < R; ++i) {
     const auto &r = c.reqs[i];
-    const int64_t ylen = (i + 1 < c.reqs.size() ? c.y_off[i + 1] : yo) - c.y_off[i];
+    if (r->y_map) continue;
+    const int64_t ylen = (i + 1 < R ? c.y_off[i + 1] : yo) - c.y_off[i];
     float *dst = r->y_pinned ? r->y : c.y_pin + c.y_off[i];
     MSREP_CUDA_TRY(cudaMemcpyAsync(dst, c.y_dev + c.y_off[i], sizeof(float) * ylen,
                                    cudaMemcpyDeviceToHost, c.stream));
@@ -495,7 +546,7 @@ msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **ou
   // the x of a request with two vectors); directories; partials of both
   // kernels
   const int64_t per_ctx = 2 * align256(cfg->arena_bytes) + 4 * align256(cfg->arena_bytes) +
-                          int64_t(dir_size(cfg->max_items)) + int64_t(dirk_size(cfg->max_items)) +
+                          int64_t(dir_size(cfg->max_items)) +
                           2 * int64_t(align256(sizeof(double) * cfg->max_tiles)) +
                           2 * int64_t(align256(sizeof(double) * cfg->max_tiles * kBatchWidth));
   if (per_ctx * cfg->contexts > cfg->budget_bytes)
@@ -508,7 +559,6 @@ msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **ou
     c.arena_floats = cfg->arena_bytes / int64_t(sizeof(float));
     c.max_tiles = cfg->max_tiles;
     c.dir_bytes = dir_size(cfg->max_items);
-    c.dirk_bytes = dirk_size(cfg->max_items);
     c.xt_floats = 4 * cfg->arena_bytes / int64_t(sizeof(float));
     bool okc = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking) == cudaSuccess &&
                cudaEventCreate(&c.done_ev) == cudaSuccess &&
@@ -524,10 +574,9 @@ msrep_status msrep_serve_create(const msrep_serve_config *cfg, msrep_server **ou
                cudaMallocHost(&c.y_pin, cfg->arena_bytes) == cudaSuccess &&
                cudaMallocHost(&c.dir_pin, c.dir_bytes) == cudaSuccess &&
                cudaMalloc(&c.xt_dev, sizeof(float) * c.xt_floats) == cudaSuccess &&
-               cudaMalloc(&c.dirk_dev, c.dirk_bytes) == cudaSuccess &&
                cudaMalloc(&c.head_k, sizeof(double) * cfg->max_tiles * kBatchWidth) == cudaSuccess &&
                cudaMalloc(&c.tail_k, sizeof(double) * cfg->max_tiles * kBatchWidth) == cudaSuccess &&
-               cudaMallocHost(&c.dirk_pin, c.dirk_bytes) == cudaSuccess;
+               true;
     if (!okc) {
       for (auto &cc : s->ctx) free_context(cc);
       cudaGetLastError();
@@ -675,10 +724,20 @@ msrep_status msrep_serve_submit(msrep_server *s, int64_t id, int32_t k, const fl
   r->y = y;
   r->t_submit = Clock::now();
   {
-    // page-locked caller buffers are copied by DMA without a staging copy
-    cudaPointerAttributes at;
-    r->x_pinned = cudaPointerGetAttributes(&at, x) == cudaSuccess && at.type == cudaMemoryTypeHost;
-    r->y_pinned = cudaPointerGetAttributes(&at, y) == cudaSuccess && at.type == cudaMemoryTypeHost;
+    // page-locked caller buffers are copied by DMA without a staging copy,
+    // and read / written by the launch's kernels directly when they are
+    // mapped at the same address (unified addressing), the only mapping
+    // used here
+    auto mapped = [](const void *p, bool &pinned) -> const void * {
+      cudaPointerAttributes at;
+      pinned = cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost;
+      if (!pinned || !at.devicePointer || !at.hostPointer) return nullptr;
+      const void *d = static_cast<const char *>(at.devicePointer) +
+                      (static_cast<const char *>(p) - static_cast<const char *>(at.hostPointer));
+      return d == p ? p : nullptr;
+    };
+    r->x_map = static_cast<const float *>(mapped(x, r->x_pinned));
+    r->y_map = static_cast<float *>(const_cast<void *>(mapped(y, r->y_pinned)));
     cudaGetLastError();
   }
   std::lock_guard<std::mutex> lk(s->mu);

@@ -218,3 +218,33 @@ def test_serve_replay_driver():
             S.replay(t_us, [ids[int(p)] for p in pick], ks, xs, ys, bad)
         assert e.value.status == 1        # MSREP_ERR_INVALID_ARG
         assert S.stats()["completed"] == n
+
+
+def test_serve_mapped_page_locked_buffers():
+    """Page-locked x and y are read and written by the launch's kernels
+    directly (one-vector x through the copy kernel, k-vector x by the
+    interleaving kernel, y by the copy-out kernel); mixed in one stream with
+    pageable buffers, every result equals msrep_spmv bit for bit."""
+    import paper_2209_07552_gb300 as M
+    mats = _mats(seed=13)
+    g = I.rng(43, 1)
+    X = [g.uniform(-1, 1, (8, a.n)).astype(np.float32) for a in mats]
+    solo = [_solo(M, a, x) for a, x in zip(mats, X)]
+    with M.Server(budget_bytes=4 << 30, arena_bytes=16 << 20, contexts=2) as S:
+        ids = [S.register(a) for a in mats]
+        pending = []
+        for rep in range(3):
+            for j, (mid, a) in enumerate(zip(ids, mats)):
+                for k in (1, 2, 3, 8):
+                    pinned = (rep + j + k) % 2 == 0
+                    if pinned:
+                        xb = M.native.pinned_empty((k, a.n))
+                        xb[:] = X[j][:k]
+                        yb = M.native.pinned_empty((k * a.m,))
+                        yb[:] = np.nan
+                    else:
+                        xb, yb = X[j][:k].copy(), None
+                    pending.append((j, k, xb, S.submit(mid, xb, yb)))
+        for j, k, xb, t in pending:
+            y = S.wait(t).reshape(k, -1)
+            assert np.array_equal(y, solo[j][:k]), (j, k)
