@@ -545,8 +545,8 @@ __global__ void __launch_bounds__(kThreads, 4) coo_scatter(ScatterArgs<Pol> a) {
     for (int64_t base = warp * 32 * B; base < a.nnz; base += nwarps * 32 * B) {
       int32_t r[B];
       LV v[B];
-      double xv[B];
-      typename Pol::X xr[B];
+      [[maybe_unused]] double xv[B];            // FP64: x as loaded
+      [[maybe_unused]] typename Pol::X xr[B];   // low precision: x to widen
       // loads first; low-precision values and x are widened to FP64
       // (integer operations, widen) after all of them are issued
 #pragma unroll

@@ -450,6 +450,32 @@ __device__ __forceinline__ void coo_tile_range(const CooArgs<Pol> &a, int b, int
   k1 = static_cast<int32_t>(s + (int64_t(g + 1) * L) / a.G);
 }
 
+// In-tile length of the run of row rv around nonzero j of a row-sorted
+// COO tile [k0, k1), or 0 when two probes 128 positions either side of j
+// both miss rv (the run is then shorter than 256).  Out of line: a lane
+// calls it for a few runs at most, and inlined at every call site it made
+// the low-precision COO kernel wait on instruction fetch.
+static __device__ __noinline__ int64_t coo_run_length(const int32_t *row_idx, int64_t k0,
+                                                      int64_t k1, int32_t rv, int64_t j) {
+  const int64_t pa = max(k0, j - 128), pb = min(k1 - 1, j + 128);
+  const bool reach_a = pa < j && __ldg(row_idx + pa) == rv;
+  const bool reach_b = pb > j && __ldg(row_idx + pb) == rv;
+  if (!reach_a && !reach_b) return 0;
+  int64_t lo = k0, hi = j;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(row_idx + mid) < rv) lo = mid + 1; else hi = mid;
+  }
+  const int64_t st = lo;
+  lo = j;
+  hi = k1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (__ldg(row_idx + mid) <= rv) lo = mid + 1; else hi = mid;
+  }
+  return lo - st;
+}
+
 template <class Pol, class Src>
 __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, int32_t k0,
                                                  int32_t k1, Seg<int32_t> row,
@@ -479,34 +505,17 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
   // compensation predicate of the run of row rv that contains nonzero j:
   // split if it touches a tile end that the row crosses (rows are sorted,
   // so it touches the tile's start iff rv is the tile's first row), long if
-  // its length inside the tile exceeds 256.  Two probes 128 positions
-  // either side of j settle most runs: when neither holds rv, the run lies
-  // strictly between them and is shorter than 256; only otherwise is its
-  // extent bisected in row_idx.  (A row that crosses the tile is split
-  // anyway; inside the tile, its in-tile length is its full length.)
+  // its length inside the tile exceeds 256 (coo_run_length; a split run is
+  // caught first, so the length test alone decides the rest).  A row that
+  // crosses the tile is split anyway; inside the tile, its in-tile length
+  // is its full length.
   auto run_comp = [&](int32_t rv, int64_t j) -> bool {
     if (!Pol::kLow) return false;
     if (a.comp_mode & (MSREP_COMP_ALL | MSREP_COMP_NONE))
       return want_comp(a.comp_mode, 0, false);
     const bool split = (rv == first_row && flag) || (rv == last_row && cont);
     if (split) return true;
-    const int64_t pa = max(int64_t(k0), j - 128), pb = min(int64_t(k1) - 1, j + 128);
-    const bool reach_a = pa < j && __ldg(a.row_idx + pa) == rv;
-    const bool reach_b = pb > j && __ldg(a.row_idx + pb) == rv;
-    if (!reach_a && !reach_b) return false;
-    int64_t lo = k0, hi = j;
-    while (lo < hi) {
-      int64_t mid = (lo + hi) >> 1;
-      if (__ldg(a.row_idx + mid) < rv) lo = mid + 1; else hi = mid;
-    }
-    const int64_t st = lo;
-    lo = j;
-    hi = k1;
-    while (lo < hi) {
-      int64_t mid = (lo + hi) >> 1;
-      if (__ldg(a.row_idx + mid) <= rv) lo = mid + 1; else hi = mid;
-    }
-    return want_comp(a.comp_mode, lo - st, (st == k0 && flag) || (lo == k1 && cont));
+    return coo_run_length(a.row_idx, k0, k1, rv, j) > 256;
   };
 
   // A lane whose range holds at most 256 nonzeros needs the predicate for
