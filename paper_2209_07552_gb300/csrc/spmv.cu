@@ -545,35 +545,45 @@ __global__ void __launch_bounds__(kThreads, 4) coo_scatter(ScatterArgs<Pol> a) {
     for (int64_t base = warp * 32 * B; base < a.nnz; base += nwarps * 32 * B) {
       int32_t r[B];
       LV v[B];
-      [[maybe_unused]] double xv[B];            // FP64: x as loaded
-      [[maybe_unused]] typename Pol::X xr[B];   // low precision: x to widen
-      // loads first; low-precision values and x are widened to FP64
-      // (integer operations, widen) after all of them are issued
+      if constexpr (Pol::kLow &&
+                    std::is_same<std::decay_t<decltype(sink)>, DirectSink>::value) {
+        // loads first; values and x are widened to FP64 (integer
+        // operations, widen) after all of them are issued (direct scatter
+        // only, as in the CSC walk)
+        typename Pol::X xr[B];
 #pragma unroll
-      for (int u = 0; u < B; ++u) {
-        const int64_t k = base + 32 * u + lane;
-        const bool in = k < a.nnz;
-        r[u] = in ? ld_stream(a.row_idx + k) : 0;
-        v[u] = in ? LV(ld_stream(a.val + k)) : LV(0);
-        if constexpr (Pol::kLow)
+        for (int u = 0; u < B; ++u) {
+          const int64_t k = base + 32 * u + lane;
+          const bool in = k < a.nnz;
+          r[u] = in ? ld_stream(a.row_idx + k) : 0;
+          v[u] = in ? LV(ld_stream(a.val + k)) : LV(0);
           xr[u] = in ? load_x(a.x, ld_stream(a.col_idx + k)) : typename Pol::X(0);
-        else
-          xv[u] = in ? double(load_x(a.x, ld_stream(a.col_idx + k))) : 0.0;
-      }
-#pragma unroll
-      for (int u = 0; u < B; ++u) {
-        if (base + 32 * u >= a.nnz) break;  // warp-uniform
-        double xw, vw;
-        if constexpr (Pol::kLow) {
-          xw = widen(xr[u]);
-          vw = widen(v[u]);
-        } else {
-          xw = xv[u];
-          vw = double(v[u]);
         }
-        const double xs = a.scaled ? __dmul_rn(xw, a.scale) : xw;
-        const double prod = __dmul_rn(vw, xs);
-        if (base + 32 * u + lane < a.nnz) sink.add(r[u], prod);
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          if (base + 32 * u >= a.nnz) break;  // warp-uniform
+          const double xw = widen(xr[u]);
+          const double xs = a.scaled ? __dmul_rn(xw, a.scale) : xw;
+          const double prod = __dmul_rn(widen(v[u]), xs);
+          if (base + 32 * u + lane < a.nnz) sink.add(r[u], prod);
+        }
+      } else {
+        double xv[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          const int64_t k = base + 32 * u + lane;
+          const bool in = k < a.nnz;
+          r[u] = in ? ld_stream(a.row_idx + k) : 0;
+          v[u] = in ? LV(ld_stream(a.val + k)) : LV(0);
+          xv[u] = in ? double(load_x(a.x, ld_stream(a.col_idx + k))) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+          if (base + 32 * u >= a.nnz) break;  // warp-uniform
+          const double xs = a.scaled ? __dmul_rn(xv[u], a.scale) : xv[u];
+          const double prod = __dmul_rn(double(v[u]), xs);
+          if (base + 32 * u + lane < a.nnz) sink.add(r[u], prod);
+        }
       }
     }
   };
