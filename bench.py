@@ -604,21 +604,24 @@ def main_kernel_us(M, call, reps, skip=3):
 
 def access_floor_us(M, A, x, reps):
     """Time of msrep_access_floor over the matrix's own index and value
-    arrays: a gather of x per nonzero (CSR; COO also streams its row index)
-    or an atomic add per nonzero (CSC, the faster of scattering to y's rows
-    and to the permuted accumulator).  None when a vector length is not a
-    power of two."""
+    arrays: a gather of x per nonzero (CSR; COO also streams its row index),
+    the faster of eight consecutive nonzeros a lane and lane-interleaved
+    steps, or an atomic add per nonzero (CSC, the faster of scattering to
+    y's rows and to the permuted accumulator); every mode's time is kept.
+    None when a vector length is not a power of two."""
     import torch
     if A.fmt == M.MSREP_CSC:
         n_vec, modes, idx2 = A.m, (2, 3), None
     else:
-        n_vec, modes = A.n, ((1,) if A.fmt == M.MSREP_COO else (0,))
+        # eight consecutive nonzeros a lane, and lane-interleaved steps
+        n_vec, modes = A.n, ((1, 5) if A.fmt == M.MSREP_COO else (0, 4))
         idx2 = A.idx2
     if n_vec & (n_vec - 1):
         return None
     vec = x if A.fmt != M.MSREP_CSC else torch.zeros(n_vec, dtype=torch.float64, device=x.device)
     sink = torch.zeros(1, dtype=torch.float64, device=x.device)
     best = None
+    by_mode = {}
     for mode in modes:
         for _ in range(2):
             M.native.msrep_access_floor(mode, A.idx, A.val, vec, idx2=idx2, sink=sink)
@@ -629,9 +632,10 @@ def access_floor_us(M, A, x, reps):
         e1.record()
         torch.cuda.synchronize()
         us = 1e3 * e0.elapsed_time(e1) / reps
+        by_mode[str(mode)] = us
         if best is None or us < best[0]:
             best = (us, mode)
-    return {"floor_us": best[0], "floor_mode": best[1]}
+    return {"floor_us": best[0], "floor_mode": best[1], "floor_us_by_mode": by_mode}
 
 
 def run_e2e(M, pairs, args, dev):

@@ -547,11 +547,13 @@ msrep_status msrep_device_status(void *stream, int *status);
 msrep_status msrep_wait_selftest(int64_t max_cycles, int32_t *gave_up, void *stream);
 
 /* Measurement aid (no counterpart in the paper): the access-pattern floor
- * of an SpMV.  One kernel that streams idx (and, mode 1, idx2) and val once
- * and, per nonzero, gathers vec[idx] (modes 0, 1: CSR, COO) or atomically
- * adds val into vec[idx] (mode 2) or into vec[slot(idx)] (mode 3: the
- * permuted accumulator of msrep_spmv's CSC path, slot(r) = r * 0x9E3779B1
- * mod vec_len), with no row logic.  Its time is what any SpMV kernel over
+ * of an SpMV.  One kernel that streams idx (and, modes 1 and 5, idx2) and
+ * val once and, per nonzero, gathers vec[idx] (modes 0, 1: CSR, COO, eight
+ * consecutive nonzeros a lane; modes 4, 5: the same, lane-interleaved, each
+ * warp instruction covering 32 consecutive nonzeros) or atomically adds val
+ * into vec[idx] (mode 2) or into vec[slot(idx)] (mode 3: the permuted
+ * accumulator of msrep_spmv's CSC path, slot(r) = r * 0x9E3779B1 mod
+ * vec_len), with no row logic.  Its time is what any SpMV kernel over
  * the same arrays pays for its gathers or scatters.  nnz elements; idx,
  * idx2, val 32-byte aligned device arrays; vec: vec_len doubles, vec_len a
  * power of two (every index is reduced modulo vec_len, so any idx is in

@@ -63,6 +63,42 @@ __global__ void __launch_bounds__(256) access_floor(const int32_t *__restrict__ 
   if (MODE <= 1 && (acc == 1.2345e-300 || other == 0x7fffabcd)) sink[0] = acc;
 }
 
+// Lane-interleaved layout (MODE 4: gather, 5: gather plus COO's row-index
+// stream): step u of a warp takes nonzeros base + 32 u + lane, so every
+// load and every gather instruction covers 32 consecutive nonzeros (coalesced
+// 4- and 8-byte loads; for a banded matrix the 32 gathers fall on a few
+// lines of x).  Eight steps are loaded ahead.
+template <int MODE>
+__global__ void __launch_bounds__(256) access_floor_lanes(const int32_t *__restrict__ idx,
+                                                         const int32_t *__restrict__ idx2,
+                                                         const double *__restrict__ val,
+                                                         const double *vec, int64_t nnz,
+                                                         uint32_t mask, double *sink) {
+  constexpr int B = 8;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  double acc = 0.0;
+  int32_t other = 0;
+  for (int64_t base = warp * 32 * B; base < nnz; base += nwarps * 32 * B) {
+    int32_t c[B];
+    double v[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int64_t k = base + 32 * u + lane;
+      const bool in = k < nnz;
+      c[u] = in ? ld_stream(idx + k) : 0;
+      v[u] = in ? ld_stream(val + k) : 0.0;
+      if (MODE == 5 && in) other ^= ld_stream(idx2 + k);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (base + 32 * u + lane < nnz)
+        acc = __fma_rn(v[u], __ldg(vec + (static_cast<uint32_t>(c[u]) & mask)), acc);
+  }
+  if (acc == 1.2345e-300 || other == 0x7fffabcd) sink[0] = acc;
+}
+
 // Self-test of the bounded device wait (msrep_wait_selftest): one thread
 // initialises an mbarrier that expects two arrivals, arrives once and issues
 // no copy, so the barrier's phase can never complete; the bounded wait must
@@ -101,9 +137,9 @@ extern "C" msrep_status msrep_wait_selftest(int64_t max_cycles, int32_t *gave_up
 extern "C" msrep_status msrep_access_floor(int32_t mode, const int32_t *idx, const int32_t *idx2,
                                            const double *val, double *vec, int64_t nnz,
                                            int64_t vec_len, double *sink, void *stream) {
-  if (mode < 0 || mode > 3) return fail(MSREP_ERR_INVALID_ARG, "mode %d outside 0..3", mode);
+  if (mode < 0 || mode > 5) return fail(MSREP_ERR_INVALID_ARG, "mode %d outside 0..5", mode);
   if (nnz < 0 || vec_len < 1 || !sink || (nnz > 0 && (!idx || !val || !vec)) ||
-      (mode == 1 && nnz > 0 && !idx2))
+      ((mode == 1 || mode == 5) && nnz > 0 && !idx2))
     return fail(MSREP_ERR_INVALID_ARG, "bad arrays or sizes");
   if ((reinterpret_cast<uintptr_t>(idx) | reinterpret_cast<uintptr_t>(idx2) |
        reinterpret_cast<uintptr_t>(val)) & 31)
@@ -117,7 +153,9 @@ extern "C" msrep_status msrep_access_floor(int32_t mode, const int32_t *idx, con
     case 0: access_floor<0><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
     case 1: access_floor<1><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
     case 2: access_floor<2><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
-    default: access_floor<3><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
+    case 3: access_floor<3><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
+    case 4: access_floor_lanes<4><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
+    default: access_floor_lanes<5><<<grid, 256, 0, st>>>(idx, idx2, val, vec, nnz, mask, sink); break;
   }
   MSREP_CUDA_TRY(cudaGetLastError());
   return ok();

@@ -391,7 +391,8 @@ def msrep_spmv(A: DeviceMatrix, part: DevicePartition, alpha: float, x,
 def msrep_access_floor(mode: int, idx, val, vec, idx2=None, sink=None, stream=None):
     """The access-pattern floor kernel (see include/msrep.h): mode 0 gather,
     1 gather plus a second index stream, 2 scatter-add, 3 scatter-add to the
-    permuted slot.  vec.numel() must be a power of two."""
+    permuted slot, 4 and 5 as 0 and 1 with lane-interleaved steps.
+    vec.numel() must be a power of two."""
     import torch
     if sink is None:
         sink = torch.zeros(1, dtype=torch.float64, device=vec.device)

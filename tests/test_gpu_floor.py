@@ -37,7 +37,16 @@ def test_gather_modes_run_and_reject_bad_lengths():
     x = torch.ones(1024, dtype=torch.float64, device="cuda")
     M.native.msrep_access_floor(0, idx, val, x)
     M.native.msrep_access_floor(1, idx, val, x, idx2=idx)
+    # lane-interleaved modes, also on a ragged length (not a multiple of 256)
+    M.native.msrep_access_floor(4, idx, val, x)
+    M.native.msrep_access_floor(5, idx, val, x, idx2=idx)
+    M.native.msrep_access_floor(4, idx[:4000], val[:4000], x)
+    M.native.msrep_access_floor(5, idx[:4000], val[:4000], x, idx2=idx[:4000])
     torch.cuda.synchronize()
+    for bad in (-1, 6):
+        with pytest.raises(M.MsrepError) as e:
+            M.native.msrep_access_floor(bad, idx, val, x, idx2=idx)
+        assert e.value.status == 1
     with pytest.raises(M.MsrepError) as e:
         M.native.msrep_access_floor(0, idx, val, torch.ones(1000, dtype=torch.float64,
                                                             device="cuda"))
