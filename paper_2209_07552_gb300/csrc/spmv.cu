@@ -101,6 +101,8 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) csr_direct(CsrArgs<Pol> 
                                                        int64_t nnz) {
   grid_dependency_wait();
   __shared__ int32_t s_rp[kWarps][32 * IPT + 8];
+  // per-row compensation flags of the low-precision form
+  __shared__ uint8_t s_cf[Pol::kLow ? kWarps : 1][Pol::kLow ? 32 * IPT + 8 : 1];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TileWalk tw = tile_walk(*n_tiles, kWarps, a.part_toff);
   const int T = tw.end, stride = tw.step;
@@ -128,7 +130,8 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) csr_direct(CsrArgs<Pol> 
     __syncwarp();
     if (b + stride < T) fetch(b + stride);
     csr_tile_compute<Pol>(a, b, cr0, ck0, cr1, ck1, s_rp[wid], Seg<int32_t>{a.col_idx, 0},
-                          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{});
+                          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{},
+                          Pol::kLow ? s_cf[wid] : nullptr);
     __syncwarp();
   }
 }

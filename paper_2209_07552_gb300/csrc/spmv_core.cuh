@@ -307,12 +307,16 @@ __device__ __forceinline__ void write_row(const CsrArgs<Pol> &a, int32_t row,
 // One merge-path tile b = rows [r0, r1] x nonzeros [k0, k1), processed by
 // one warp.  rp[j] = row_ptr[r0 + j] for j = 0..r1-r0, and also j = r1-r0+1
 // when r1 < m; rp must be in shared memory (it is searched).
+// cf (low-precision form, optional): this warp's nrows + 1 bytes of shared
+// memory for the tile's per-row compensation flags, filled once here by all
+// lanes; the row-finishing path, which the lanes of a warp reach at
+// different steps, then reads one byte instead of recomputing the predicate.
 template <class Pol, class Src>
 __device__ __forceinline__ void csr_tile_compute(const CsrArgs<Pol> &a, int b, int32_t r0,
                                                  int32_t k0, int32_t r1, int32_t k1,
                                                  const int32_t *rp, Seg<int32_t> col,
                                                  Seg<typename Pol::V> val, int64_t nnz,
-                                                 Src src) {
+                                                 Src src, uint8_t *cf = nullptr) {
   using Acc = typename Pol::Acc;
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
@@ -331,11 +335,18 @@ __device__ __forceinline__ void csr_tile_compute(const CsrArgs<Pol> &a, int b, i
   // compensation predicate (low-precision form only)
   int32_t re_last = 0;
   if (Pol::kLow) re_last = (r1 < a.m) ? rp[nrows + 1] : k1;
-  auto row_comp = [&](int rr) -> bool {
-    if (!Pol::kLow) return false;
+  auto row_comp_of = [&](int rr) -> bool {
     int64_t st = rr == 0 ? int64_t(rs0) : int64_t(s_end[rr - 1]);
     int64_t en = rr < nrows ? int64_t(s_end[rr]) : int64_t(re_last);
     return want_comp(a.comp_mode, en - st, (rr == 0 && flag) || rr == nrows);
+  };
+  if (Pol::kLow && cf) {
+    for (int rr = lane; rr <= nrows; rr += 32) cf[rr] = row_comp_of(rr);
+    __syncwarp();
+  }
+  auto row_comp = [&](int rr) -> bool {
+    if (!Pol::kLow) return false;
+    return cf ? cf[rr] != 0 : row_comp_of(rr);
   };
 
   Acc acc = Pol::zero(), first_acc = Pol::zero();
