@@ -248,3 +248,22 @@ def test_serve_mapped_page_locked_buffers():
         for j, k, xb, t in pending:
             y = S.wait(t).reshape(k, -1)
             assert np.array_equal(y, solo[j][:k]), (j, k)
+
+
+def test_serve_full_size_rmat(rmat_full):
+    """The served R-MAT of the bench (2^20 rows, 2^24 nonzeros) at each
+    width, through mapped page-locked buffers: every column equals
+    msrep_spmv of that x bit for bit."""
+    import paper_2209_07552_gb300 as M
+    a = rmat_full
+    g = I.rng(45, 3)
+    X = g.uniform(-1, 1, (8, a.n)).astype(np.float32)
+    solo = _solo(M, a, X)
+    with M.Server(budget_bytes=8 << 30, arena_bytes=64 << 20, contexts=2) as S:
+        mid = S.register(a)
+        for k in (1, 2, 3, 8):
+            xb = M.native.pinned_empty((k, a.n))
+            xb[:] = X[:k]
+            yb = M.native.pinned_empty((k * a.m,))
+            y = S.wait(S.submit(mid, xb, yb)).reshape(k, -1)
+            assert np.array_equal(y, solo[:k]), k

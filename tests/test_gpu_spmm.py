@@ -191,3 +191,37 @@ def test_empty_matrix_and_empty_rows(k):
     M.msrep_spmm(B, bpart, 1.0, torch.from_numpy(X).cuda(), 0.0, Yb)
     want = O.spmm_csr(b.m, b.row_ptr, b.col_idx, b.val, X.T.copy()).T
     assert np.array_equal(Yb.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("k", [2, 4, 8])
+def test_full_size_rmat_columns_equal_spmv(k, rmat_full):
+    """The bench's k-vector case at full size (R-MAT 2^20, 2^24 nonzeros,
+    FP32, P = 2368, default tile): every column equals msrep_spmv of that
+    x bit for bit, for each width the kernel has (KP 2, 4 with one thread
+    per lane, 8 with two), and the spot rows match the FP64 oracle's dot
+    products within the binary32 row bound ((L + 2) u (|A||x|)_r + u |y_r|,
+    recursive summation)."""
+    import torch
+
+    import paper_2209_07552_gb300 as M
+    a = rmat_full
+    A, part = _setup(a, "f32", 2368)
+    g = I.rng(77, k)
+    X = torch.from_numpy(g.uniform(-1, 1, (k, a.n)).astype(np.float32)).cuda()
+    Y = torch.empty((k, a.m), dtype=torch.float32, device="cuda")
+    M.msrep_spmm(A, part, 1.0, X, 0.0, Y)
+    ws = M.alloc_workspace(A, part)
+    y = torch.empty(a.m, dtype=torch.float32, device="cuda")
+    stored = I.CSR(a.m, a.n, a.row_ptr, a.col_idx, a.val.astype(np.float32).astype(np.float64))
+    rows = np.concatenate([np.arange(16), g.integers(0, a.m, 200)])   # hub rows and a sample
+    for v in range(k):
+        M.msrep_spmv(A, part, 1.0, X[v], 0.0, y, workspace=ws)
+        assert torch.equal(Y[v], y), v
+        xv = X[v].cpu().numpy().astype(np.float64)
+        got = Y[v].cpu().numpy()
+        for r in rows:
+            s, e = stored.row_ptr[r], stored.row_ptr[r + 1]
+            want = float(np.dot(stored.val[s:e], xv[stored.col_idx[s:e]]))
+            bound = (e - s + 2) * 2.0**-24 * float(np.dot(np.abs(stored.val[s:e]),
+                                                           np.abs(xv[stored.col_idx[s:e]])))
+            assert abs(float(got[r]) - want) <= bound + 2.0**-24 * abs(want), (v, r)
