@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <cstdarg>
+#include <map>
 #include <mutex>
 #include <string>
 
@@ -669,6 +670,44 @@ __global__ void warm_clear(const int32_t *hot, uint32_t *p, int64_t n) {
     p[i] = 0u;
 }
 
+// A second stream of this host thread on the current device, with a fork
+// and a join event: the frequent-row search depends on nothing else a
+// partitioning call computes, so it runs beside the metadata and tile-plan
+// chain.  The caller's stream still orders the whole call: the side stream
+// waits for a fork event recorded on it and the caller's stream waits for
+// the join event (a stream capture sees one fork and one join).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static msrep_status side_stream(SideStream **out) {
+  static thread_local std::map<int, SideStream> per_device;
+  int dev = 0;
+  MSREP_CUDA_TRY(cudaGetDevice(&dev));
+  SideStream &ss = per_device[dev];
+  if (!ss.s) {
+    MSREP_CUDA_TRY(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+    MSREP_CUDA_TRY(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming));
+    MSREP_CUDA_TRY(cudaEventCreateWithFlags(&ss.join, cudaEventDisableTiming));
+  }
+  *out = &ss;
+  return MSREP_OK;
+}
+
+static msrep_status fork_side(cudaStream_t st, SideStream **ss) {
+  MSREP_TRY(side_stream(ss));
+  MSREP_CUDA_TRY(cudaEventRecord((*ss)->fork, st));
+  MSREP_CUDA_TRY(cudaStreamWaitEvent((*ss)->s, (*ss)->fork, 0));
+  return MSREP_OK;
+}
+
+static msrep_status join_side(cudaStream_t st, SideStream *ss) {
+  MSREP_CUDA_TRY(cudaEventRecord(ss->join, ss->s));
+  MSREP_CUDA_TRY(cudaStreamWaitEvent(st, ss->join, 0));
+  return MSREP_OK;
+}
+
 // Hub rows, then the frequent-row table, of a scatter (CSC, or COO sorted by
 // column or in no order): hot, warm and the search scratch (key, cnt) are
 // in the plan.
@@ -833,6 +872,15 @@ static msrep_status partition_compressed(const msrep_matrix *A,
   if ((flags & MSREP_PART_MERGE_PATH) && (flags & MSREP_PART_ROW_BLOCK))
     return fail(MSREP_ERR_INVALID_ARG,
                 "MSREP_PART_MERGE_PATH and MSREP_PART_ROW_BLOCK exclude each other");
+  // CSC: the frequent-row search beside the rest
+  SideStream *side = nullptr;
+  if (plan && A->fmt == MSREP_CSC) {
+    MSREP_TRY(fork_side(st, &side));
+    int32_t *wtab = reinterpret_cast<int32_t *>(plan + L.off_wtab);
+    MSREP_TRY(find_frequent_rows(A->idx, A->nnz, reinterpret_cast<int32_t *>(plan + L.off_hot),
+                                 reinterpret_cast<unsigned long long *>(plan + L.off_warm), wtab,
+                                 wtab + kWarmTab, side->s));
+  }
   MSREP_TRY(launch_dependent(
       part_meta_compressed, blocks, threads, st, 0, A->ptr, n_major, A->nnz, p->np, p->start_idx,
       p->end_idx, p->start_major, p->end_major, p->start_flag, D, R,
@@ -865,13 +913,8 @@ static msrep_status partition_compressed(const msrep_matrix *A,
     MSREP_TRY(launch_dependent(plan_scan, 1, 1024, st, 0, D, p->np, tile, toff));
     MSREP_TRY(launch_dependent(plan_tiles, p->np, 128, st, 0, A->ptr, n_major, A->nnz, p->np, D,
                                R, toff, trow, tk));
-    if (A->fmt == MSREP_CSC) {
-      int32_t *wtab = reinterpret_cast<int32_t *>(plan + L.off_wtab);
-      MSREP_TRY(find_frequent_rows(A->idx, A->nnz, reinterpret_cast<int32_t *>(plan + L.off_hot),
-                                   reinterpret_cast<unsigned long long *>(plan + L.off_warm), wtab,
-                                   wtab + kWarmTab, st));
-    }
   }
+  if (side) MSREP_TRY(join_side(st, side));
   return ok();
 }
 
@@ -949,6 +992,16 @@ msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
   if (flags & MSREP_VALIDATE) MSREP_TRY(run_validation(A, st));
   // the major index: rows (sorted by row), columns (sorted by column)
   const int32_t *major = A->fmt == MSREP_COO_BY_COL ? A->idx : A->idx2;
+  // scatter orders: the frequent-row search beside the metadata
+  SideStream *side = nullptr;
+  if (scatter && p->plan) {
+    MSREP_TRY(fork_side(st, &side));
+    char *plan = static_cast<char *>(p->plan);
+    int32_t *wtab = reinterpret_cast<int32_t *>(plan + kScatterTabOff);
+    MSREP_TRY(find_frequent_rows(A->idx2, A->nnz, reinterpret_cast<int32_t *>(plan),
+                                 reinterpret_cast<unsigned long long *>(plan + kScatterWarmOff), wtab,
+                                 wtab + kWarmTab, side->s));
+  }
   const int threads = 256;
   const int blocks = static_cast<int>(ceil_div(p->np, threads));
   if (A->fmt == MSREP_COO_UNSORTED)
@@ -970,13 +1023,7 @@ msrep_status msrep_partition_coo(const msrep_matrix *A, msrep_partition *p,
       MSREP_TRY(launch_dependent(local_fill_coo<false>, grid, 256, st, 0, major, A->nnz, p->np,
                                  p->start_idx, p->start_major, p->local));
   }
-  if (scatter && p->plan) {
-    char *plan = static_cast<char *>(p->plan);
-    int32_t *wtab = reinterpret_cast<int32_t *>(plan + kScatterTabOff);
-    MSREP_TRY(find_frequent_rows(A->idx2, A->nnz, reinterpret_cast<int32_t *>(plan),
-                                 reinterpret_cast<unsigned long long *>(plan + kScatterWarmOff), wtab,
-                                 wtab + kWarmTab, st));
-  }
+  if (side) MSREP_TRY(join_side(st, side));
   return ok();
 }
 
