@@ -232,12 +232,31 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) coo_direct(CooArgs<Pol> 
   // the next tile's range is loaded while the current one is processed
   int32_t k0 = 0, k1 = 0;
   if (b < T) coo_tile_range(a, b, k0, k1);
-  for (; b < T; b += stride) {
-    const int32_t ck0 = k0, ck1 = k1;
-    if (b + stride < T) coo_tile_range(a, b + stride, k0, k1);
-    coo_tile_compute<Pol>(a, b, ck0, ck1, Seg<int32_t>{a.row_idx, 0}, Seg<int32_t>{a.col_idx, 0},
-                          Seg<typename Pol::V>{a.val, 0}, GlobalSrc{});
-    __syncwarp();
+  auto walk = [&](auto copy) {
+    for (; b < T; b += stride) {
+      const int32_t ck0 = k0, ck1 = k1;
+      if (b + stride < T) coo_tile_range(a, b + stride, k0, k1);
+      coo_tile_compute<Pol, GlobalSrc, decltype(copy)::value>(
+          a, b, ck0, ck1, Seg<int32_t>{a.row_idx, 0}, Seg<int32_t>{a.col_idx, 0},
+          Seg<typename Pol::V>{a.val, 0}, GlobalSrc{});
+      __syncwarp();
+    }
+  };
+  // the low-precision form specialises the common alpha = 1, beta = 0
+  if constexpr (Pol::kLow) {
+    if (a.finish == kFinishCopy)
+      walk(std::true_type{});
+    else
+      walk(std::false_type{});
+  } else {
+    for (; b < T; b += stride) {
+      const int32_t ck0 = k0, ck1 = k1;
+      if (b + stride < T) coo_tile_range(a, b + stride, k0, k1);
+      coo_tile_compute<Pol>(a, b, ck0, ck1, Seg<int32_t>{a.row_idx, 0},
+                            Seg<int32_t>{a.col_idx, 0}, Seg<typename Pol::V>{a.val, 0},
+                            GlobalSrc{});
+      __syncwarp();
+    }
   }
 }
 

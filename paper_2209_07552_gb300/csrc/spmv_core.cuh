@@ -439,17 +439,6 @@ struct CooArgs {
   bool per_part;  // one block per partition (tiles i*G .. i*G+G-1)
 };
 
-template <class Pol>
-__device__ __forceinline__ void coo_write_row(const CooArgs<Pol> &a, int32_t row,
-                                              typename Pol::Acc v) {
-  a.y[row] = Pol::finish(v, a.finish, a.alpha, a.beta, a.y + row);
-}
-
-template <class Pol>
-__device__ __forceinline__ void coo_write_empty(const CooArgs<Pol> &a, int32_t row) {
-  a.y[row] = Pol::finish(Pol::zero(), a.finish, a.alpha, a.beta, a.y + row);
-}
-
 // nonzero range of COO tile b: sub-range g of partition i (Alg. 2's split
 // applied inside the partition)
 template <class Pol>
@@ -487,7 +476,11 @@ static __device__ __noinline__ int64_t coo_run_length(const int32_t *row_idx, in
   return lo - st;
 }
 
-template <class Pol, class Src>
+// kCopy: the caller knows that alpha = 1 and beta = 0, so every row is
+// finished by the copy mode (compile-time: the finishing code shrinks to
+// that case, which keeps the low-precision kernel's loop in the
+// instruction cache).
+template <class Pol, class Src, bool kCopy = false>
 __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, int32_t k0,
                                                  int32_t k1, Seg<int32_t> row,
                                                  Seg<int32_t> col, Seg<typename Pol::V> val,
@@ -495,6 +488,13 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
   using Acc = typename Pol::Acc;
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
+  const int fin = kCopy ? int(kFinishCopy) : a.finish;
+  auto write_row = [&](int32_t row, Acc v) {
+    a.y[row] = Pol::finish(v, fin, a.alpha, a.beta, a.y + row);
+  };
+  auto write_empty = [&](int32_t row) {
+    a.y[row] = Pol::finish(Pol::zero(), fin, a.alpha, a.beta, a.y + row);
+  };
   if (lane == 0) {
     a.head[b] = 0.0;
     a.tail[b] = 0.0;
@@ -508,7 +508,7 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
   const bool cont = next_row == last_row;
 
   if (k0 == 0)
-    for (int32_t rr = lane; rr < first_row; rr += 32) coo_write_empty(a, rr);
+    for (int32_t rr = lane; rr < first_row; rr += 32) write_empty(rr);
 
   const LaneRange lr = lane_range(k0, k1, lane);
   const int64_t ka = lr.ka, kb = lr.kb;
@@ -558,7 +558,7 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
       first_r = cur;
       first_acc = acc;
     } else {
-      coo_write_row(a, cur, acc);
+      write_row(cur, acc);
     }
     acc = Pol::zero();
   };
@@ -587,7 +587,7 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
       if (u >= ulo && u <= uhi && rw[u] != cur) {
         if (cur >= 0) {
           emit();
-          for (int32_t rr = cur + 1; rr < rw[u]; ++rr) coo_write_empty(a, rr);
+          for (int32_t rr = cur + 1; rr < rw[u]; ++rr) write_empty(rr);
         }
         cur = rw[u];
         comp = comp_of(cur, g8 + u);
@@ -602,7 +602,7 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
     if (nxt != cur) {
       emit();
       if (kb < k1)
-        for (int32_t rr = cur + 1; rr < nxt; ++rr) coo_write_empty(a, rr);
+        for (int32_t rr = cur + 1; rr < nxt; ++rr) write_empty(rr);
     }
   }
 
@@ -613,7 +613,7 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
     if (first_r == first_row && flag)
       a.head[b] = Pol::to_f64(tot);
     else
-      coo_write_row(a, first_r, tot);
+      write_row(first_r, tot);
   }
   if (lane == 31 && cont) {
     if (last_row == first_row && flag)
@@ -623,7 +623,7 @@ __device__ __forceinline__ void coo_tile_compute(const CooArgs<Pol> &a, int b, i
   }
   // empty rows between this tile's last row and the next tile's first row
   if (!cont)
-    for (int32_t rr = last_row + 1 + lane; rr < next_row; rr += 32) coo_write_empty(a, rr);
+    for (int32_t rr = last_row + 1 + lane; rr < next_row; rr += 32) write_empty(rr);
 }
 
 // ---------------------------------------------------------------------------
