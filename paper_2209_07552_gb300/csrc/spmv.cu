@@ -584,9 +584,9 @@ __global__ void __launch_bounds__(kThreads, 4) coo_scatter(ScatterArgs<Pol> a) {
 #pragma unroll
         for (int u = 0; u < B; ++u) {
           if (base + 32 * u >= a.nnz) break;  // warp-uniform
-          const double xw = widen(xr[u]);
-          const double xs = a.scaled ? __dmul_rn(xw, a.scale) : xw;
-          const double prod = __dmul_rn(widen(v[u]), xs);
+          // the low-precision form applies alpha in its finishing pass
+          // (a.scaled is false), so no scaling multiply here
+          const double prod = __dmul_rn(widen(v[u]), widen(xr[u]));
           if (base + 32 * u + lane < a.nnz) sink.add(r[u], prod);
         }
       } else {

@@ -796,7 +796,12 @@ __device__ __forceinline__ void csc_tile_compute(const CscArgs<Pol> &a, int32_t 
         } while (cend <= e);
         xc = xat(c);
       }
-      const double prod = __dmul_rn(double(v[u]), in ? xc : 0.0);
+      double vw;
+      if constexpr (Pol::kLow)
+        vw = widen(v[u]);  // integer widening: off the FP64 pipe
+      else
+        vw = double(v[u]);
+      const double prod = __dmul_rn(vw, in ? xc : 0.0);
       if (in) sink.add(rw[u], prod);
     }
   }
@@ -879,9 +884,9 @@ __device__ __forceinline__ void csc_tile_interleaved(const CscArgs<Pol> &a, int3
 #pragma unroll
       for (int u = 0; u < B; ++u) {
         if (i0 + 32 * u >= len) break;  // warp-uniform
-        const double xw = widen(xr[u]);
-        const double xs = a.scaled ? __dmul_rn(xw, a.scale) : xw;
-        const double prod = __dmul_rn(widen(v[u]), xs);
+        // the low-precision form applies alpha in its finishing pass
+        // (a.scaled is false), so no scaling multiply here
+        const double prod = __dmul_rn(widen(v[u]), widen(xr[u]));
         if (i0 + 32 * u + lane < len) sink.add(rw[u], prod);
       }
     } else {
@@ -897,7 +902,8 @@ __device__ __forceinline__ void csc_tile_interleaved(const CscArgs<Pol> &a, int3
 #pragma unroll
       for (int u = 0; u < B; ++u) {
         if (i0 + 32 * u >= len) break;  // warp-uniform
-        const double xs = a.scaled ? __dmul_rn(xv[u], a.scale) : xv[u];
+        double xs = xv[u];
+        if constexpr (!Pol::kLow) xs = a.scaled ? __dmul_rn(xv[u], a.scale) : xv[u];
         const double prod = __dmul_rn(widen(v[u]), xs);
         if (i0 + 32 * u + lane < len) sink.add(rw[u], prod);
       }
