@@ -121,19 +121,28 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) csr_direct(CsrArgs<Pol> 
     p1 = r0 + 32 + lane < rend ? __ldg(a.row_ptr + r0 + 32 + lane) : 0;
   };
   if (b < T) fetch(b);
-  for (; b < T; b += stride) {
-    const int32_t cr0 = r0, ck0 = k0, cr1 = r1, ck1 = k1;
-    const int32_t rend = min(cr1 + 2, a.m + 1);
-    if (cr0 + lane < rend) s_rp[wid][lane] = p0;
-    if (cr0 + 32 + lane < rend) s_rp[wid][32 + lane] = p1;
-    for (int32_t r = cr0 + 64 + lane; r < rend; r += 32) s_rp[wid][r - cr0] = __ldg(a.row_ptr + r);
-    __syncwarp();
-    if (b + stride < T) fetch(b + stride);
-    csr_tile_compute<Pol>(a, b, cr0, ck0, cr1, ck1, s_rp[wid], Seg<int32_t>{a.col_idx, 0},
-                          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{},
-                          Pol::kLow ? s_cf[wid] : nullptr);
-    __syncwarp();
-  }
+  auto walk = [&](auto copy) {
+    for (; b < T; b += stride) {
+      const int32_t cr0 = r0, ck0 = k0, cr1 = r1, ck1 = k1;
+      const int32_t rend = min(cr1 + 2, a.m + 1);
+      if (cr0 + lane < rend) s_rp[wid][lane] = p0;
+      if (cr0 + 32 + lane < rend) s_rp[wid][32 + lane] = p1;
+      for (int32_t r = cr0 + 64 + lane; r < rend; r += 32)
+        s_rp[wid][r - cr0] = __ldg(a.row_ptr + r);
+      __syncwarp();
+      if (b + stride < T) fetch(b + stride);
+      csr_tile_compute<Pol, GlobalSrc, decltype(copy)::value>(
+          a, b, cr0, ck0, cr1, ck1, s_rp[wid], Seg<int32_t>{a.col_idx, 0},
+          Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{}, Pol::kLow ? s_cf[wid] : nullptr);
+      __syncwarp();
+    }
+  };
+  // alpha = 1, beta = 0 (the usual call) finishes rows by a copy, decided
+  // at compile time so that no other finishing mode is issued beside it
+  if (a.finish == kFinishCopy)
+    walk(std::true_type{});
+  else
+    walk(std::false_type{});
 }
 
 template <class Pol, int IPT>
@@ -242,22 +251,11 @@ __global__ void __launch_bounds__(kThreads, MSREP_MINB) coo_direct(CooArgs<Pol> 
       __syncwarp();
     }
   };
-  // the low-precision form specialises the common alpha = 1, beta = 0
-  if constexpr (Pol::kLow) {
-    if (a.finish == kFinishCopy)
-      walk(std::true_type{});
-    else
-      walk(std::false_type{});
-  } else {
-    for (; b < T; b += stride) {
-      const int32_t ck0 = k0, ck1 = k1;
-      if (b + stride < T) coo_tile_range(a, b + stride, k0, k1);
-      coo_tile_compute<Pol>(a, b, ck0, ck1, Seg<int32_t>{a.row_idx, 0},
-                            Seg<int32_t>{a.col_idx, 0}, Seg<typename Pol::V>{a.val, 0},
-                            GlobalSrc{});
-      __syncwarp();
-    }
-  }
+  // the common alpha = 1, beta = 0 specialised at compile time
+  if (a.finish == kFinishCopy)
+    walk(std::true_type{});
+  else
+    walk(std::false_type{});
 }
 
 template <class Pol, int IPT>

@@ -311,7 +311,9 @@ __device__ __forceinline__ void write_row(const CsrArgs<Pol> &a, int32_t row,
 // memory for the tile's per-row compensation flags, filled once here by all
 // lanes; the row-finishing path, which the lanes of a warp reach at
 // different steps, then reads one byte instead of recomputing the predicate.
-template <class Pol, class Src>
+// kCopy: the caller knows that alpha = 1 and beta = 0 (every row finished
+// by the copy mode, decided at compile time).
+template <class Pol, class Src, bool kCopy = false>
 __device__ __forceinline__ void csr_tile_compute(const CsrArgs<Pol> &a, int b, int32_t r0,
                                                  int32_t k0, int32_t r1, int32_t k1,
                                                  const int32_t *rp, Seg<int32_t> col,
@@ -320,6 +322,10 @@ __device__ __forceinline__ void csr_tile_compute(const CsrArgs<Pol> &a, int b, i
   using Acc = typename Pol::Acc;
   using LV = typename LoadT<typename Pol::V>::type;
   const int lane = threadIdx.x & 31;
+  const int fin = kCopy ? int(kFinishCopy) : a.finish;
+  auto write_row_k = [&](int32_t row, Acc v) {
+    a.y[row] = Pol::finish(v, fin, a.alpha, a.beta, a.y + row);
+  };
   const int nrows = r1 - r0;
   const int32_t rs0 = rp[0];
   const int32_t *s_end = rp + 1;  // s_end[i]: end of row r0 + i
@@ -360,7 +366,7 @@ __device__ __forceinline__ void csr_tile_compute(const CsrArgs<Pol> &a, int b, i
         first_r = r;
         first_acc = acc;
       } else {
-        write_row(a, r0 + r, acc);
+        write_row_k(r0 + r, acc);
       }
       acc = Pol::zero();
       ++r;
@@ -403,7 +409,7 @@ __device__ __forceinline__ void csr_tile_compute(const CsrArgs<Pol> &a, int b, i
     if (first_r == 0 && flag)
       a.head[b] = Pol::to_f64(tot);
     else
-      write_row(a, r0 + first_r, tot);
+      write_row_k(r0 + first_r, tot);
   }
   if (lane == 31) {
     if (nrows == 0) {
