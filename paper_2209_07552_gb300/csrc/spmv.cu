@@ -401,9 +401,14 @@ __global__ void __launch_bounds__(kThreads, 4) csc_direct(CscArgs<Pol> a, const 
       const double xv = double(load_x(a.x, g));
       return a.scaled ? __dmul_rn(xv, a.scale) : xv;
     };
-    if (csc_tile_max_col(c0, k0, c1, k1, a.n, s_cp) <= kColumnWalkMax)
-      csc_tile_interleaved<Pol>(a, c0, k0, c1, k1, s_cp, sink, s_col);
-    else
+    if (csc_tile_max_col(c0, k0, c1, k1, a.n, s_cp) <= kColumnWalkMax) {
+      // FP64 with alpha = 1: the walk without its scaling multiply
+      if (Pol::kLow || a.scaled)
+        csc_tile_interleaved<Pol>(a, c0, k0, c1, k1, s_cp, sink, s_col);
+      else
+        csc_tile_interleaved<Pol, std::decay_t<decltype(sink)>, !Pol::kLow>(
+            a, c0, k0, c1, k1, s_cp, sink, s_col);
+    } else
       csc_tile_compute<Pol>(a, c0, k0, c1, k1, s_cp, xat, Seg<int32_t>{a.row_idx, 0},
                             Seg<typename Pol::V>{a.val, 0}, nnz, GlobalSrc{}, sink);
     __syncwarp();

@@ -853,7 +853,9 @@ __device__ __forceinline__ int csc_tile_max_col(int32_t c0, int32_t k0, int32_t 
 // csc_tile_max_col).  Low-precision values and x are widened to FP64 with
 // integer operations (widen).  Seven steps are loaded ahead (eight spill registers
 // at four resident blocks; four keep too few loads in flight).
-template <class Pol, class Sink>
+// kUnscaled: the caller knows a.scaled is false (alpha = 1 on the FP64
+// path), so the scaling multiply is left out at compile time.
+template <class Pol, class Sink, bool kUnscaled = false>
 __device__ __forceinline__ void csc_tile_interleaved(const CscArgs<Pol> &a, int32_t c0,
                                                      int32_t k0, int32_t c1, int32_t k1,
                                                      const int32_t *cp, const Sink &sink,
@@ -909,7 +911,7 @@ __device__ __forceinline__ void csc_tile_interleaved(const CscArgs<Pol> &a, int3
       for (int u = 0; u < B; ++u) {
         if (i0 + 32 * u >= len) break;  // warp-uniform
         double xs = xv[u];
-        if constexpr (!Pol::kLow) xs = a.scaled ? __dmul_rn(xv[u], a.scale) : xv[u];
+        if constexpr (!Pol::kLow && !kUnscaled) xs = a.scaled ? __dmul_rn(xv[u], a.scale) : xv[u];
         const double prod = __dmul_rn(widen(v[u]), xs);
         if (i0 + 32 * u + lane < len) sink.add(rw[u], prod);
       }
