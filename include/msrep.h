@@ -447,10 +447,11 @@ msrep_status msrep_serve_unregister(msrep_server *s, int64_t matrix_id);
 
 /* Queues y_v = A x_v for v = 0..k-1 (x_host: k vectors of n floats, one
  * after the other; y_host: k vectors of m floats); both host buffers stay
- * owned by the caller and must live until the request completes; page-
- * locked buffers (cudaMallocHost / cudaHostRegister) are transferred by DMA
- * directly, others through the server's staging buffers.  Does not
- * block.  The request joins a launch as soon as a context and arena space
+ * owned by the caller and must live until the request completes.  Page-
+ * locked buffers (cudaMallocHost / cudaHostRegister) mapped at their own
+ * address (unified addressing) are read and written by the launch's kernels
+ * directly; other page-locked buffers are transferred by DMA, pageable ones
+ * through the server's staging buffers.  Does not block.  The request joins a launch as soon as a context and arena space
  * are free (continuous batching).  Errors: NOT_FOUND, INVALID_ARG (k out
  * of range), SHUTDOWN. */
 msrep_status msrep_serve_submit(msrep_server *s, int64_t matrix_id, int32_t k,
