@@ -45,8 +45,14 @@ __global__ void __launch_bounds__(kKvThreads) csr_spmm_direct(SpmmArgs<Pol, KP> 
   __shared__ KvSmem<typename Pol::Acc, Sh::G> sm;
   grid_dependency_wait();
   const int T = *n_tiles, ts = threadIdx.x / Sh::GT;
-  for (int b = blockIdx.x * Sh::G + ts; b < T; b += gridDim.x * Sh::G)
-    kv_tile<Pol, KP, Sh::G>(a, b, nnz, sm, ts);
+  // alpha = 1, beta = 0 finishes rows by a copy, chosen at compile time
+  if (a.finish == kFinishCopy) {
+    for (int b = blockIdx.x * Sh::G + ts; b < T; b += gridDim.x * Sh::G)
+      kv_tile<Pol, KP, Sh::G, true>(a, b, nnz, sm, ts);
+  } else {
+    for (int b = blockIdx.x * Sh::G + ts; b < T; b += gridDim.x * Sh::G)
+      kv_tile<Pol, KP, Sh::G>(a, b, nnz, sm, ts);
+  }
 }
 
 template <class X, int KP>

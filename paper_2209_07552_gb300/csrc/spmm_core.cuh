@@ -99,12 +99,13 @@ __device__ __forceinline__ void ldx(const double *p, double (&o)[VPT]) {
   }
 }
 
-template <class Pol, int KP>
+// kCopy: alpha = 1, beta = 0 known at compile time (the copy finish)
+template <class Pol, int KP, bool kCopy = false>
 __device__ __forceinline__ void spmm_write_row(const SpmmArgs<Pol, KP> &a, int v, int32_t row,
                                                typename Pol::Acc acc) {
   if (v < a.k) {
     typename Pol::X *yp = a.y + v * a.ldy + row;
-    *yp = Pol::finish(acc, a.finish, a.alpha, a.beta, yp);
+    *yp = Pol::finish(acc, kCopy ? int(kFinishCopy) : a.finish, a.alpha, a.beta, yp);
   }
 }
 
@@ -122,7 +123,7 @@ __device__ __forceinline__ void group_sync(int ts) {
 // of them call it).  Shared memory used: rp[ts] and the partial rows
 // ts*TPV*4 .. ts*TPV*4 + KP - 1, so groups never touch each other's
 // slots and synchronise only among themselves.
-template <class Pol, int KP, int GS>
+template <class Pol, int KP, int GS, bool kCopy = false>
 __device__ __forceinline__ void kv_tile(const SpmmArgs<Pol, KP> &a, int b, int64_t nnz,
                                         KvSmem<typename Pol::Acc, GS> &sm, int ts) {
   using Acc = typename Pol::Acc;
@@ -176,7 +177,7 @@ __device__ __forceinline__ void kv_tile(const SpmmArgs<Pol, KP> &a, int b, int64
           for (int j = 0; j < VPT; ++j) first_acc[j] = acc[j];
         } else {
 #pragma unroll
-          for (int j = 0; j < VPT; ++j) spmm_write_row(a, v0 + j, r0 + r, acc[j]);
+          for (int j = 0; j < VPT; ++j) spmm_write_row<Pol, KP, kCopy>(a, v0 + j, r0 + r, acc[j]);
         }
 #pragma unroll
         for (int j = 0; j < VPT; ++j) acc[j] = Pol::zero();
@@ -259,7 +260,7 @@ __device__ __forceinline__ void kv_tile(const SpmmArgs<Pol, KP> &a, int b, int64
       if (first_r == 0 && flag)
         a.head[int64_t(b) * a.hs + v0 + j] = Pol::to_f64(tot);
       else
-        spmm_write_row(a, v0 + j, r0 + first_r, tot);
+        spmm_write_row<Pol, KP, kCopy>(a, v0 + j, r0 + first_r, tot);
     }
   }
   // the next tile of this group rewrites rp only after every thread of
