@@ -773,10 +773,13 @@ def run_serving(M, args, dev):
     cfg = dict(arena_bytes=256 << 20, contexts=args.serve_contexts, max_items=512,
                device=dev.index or 0)
     # Page-locked y buffers for every matrix, carved from one slab allocated
-    # up front (16 per matrix, each large enough for 8 vectors):
-    # allocating page-locked memory while submitting takes milliseconds (and
-    # can wait on the device), which bunched submissions and inflated p99.
-    per = 24
+    # up front (48 per matrix, each large enough for 8 vectors): the load
+    # driver waits for the request that last used a buffer before reusing
+    # it, so the pool must outlast the slowest request (48 buffers a matrix
+    # are reused about every 160 ms at 20,000 requests/s over 66 matrices);
+    # with fewer, one slow request stalled the open-loop driver and the
+    # stall bunched the following submissions.
+    per = 48
     sizes = [8 * a.m for a in mats]
     slab = M.native.pinned_empty((per * sum(sizes),))
     pools, o = [], 0
