@@ -803,7 +803,7 @@ def serve_once(M, mats, X, budget, cfg, args, seed, all_pools):
     library's native driver (msrep_serve_replay), which submits each
     request at its arrival time from one native thread; request i writes
     into the next of its matrix's page-locked y buffers and, before that,
-    the driver waits for the request that last used that buffer."""
+    the replay waits for the request that last used that buffer."""
     S = M.Server(budget_bytes=budget, **cfg)
     ids = []
     for j, a in enumerate(mats):
