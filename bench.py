@@ -501,6 +501,7 @@ def run_ours(args):
     serving = run_serving(M, args, dev) if args.serve_seconds > 0 else None
     p_sweep = run_p_sweep(M, pairs, args) if not args.skip_p_sweep else None
     coo_orders = run_coo_orders(M, args, dev, kern, peak) if not args.skip_coo_orders else None
+    stream_tma = run_stream_tma(M, pairs, kern, peak) if not args.skip_stream_tma else None
     imbalance = run_imbalance(M, args, dev) if not args.skip_imbalance else None
 
     # low-precision form on every (matrix, format) pair
@@ -528,6 +529,8 @@ def run_ours(args):
         line["p_sweep"] = p_sweep
     if imbalance:
         line["imbalance"] = imbalance
+    if stream_tma:
+        line["stream_tma"] = stream_tma
     if prec:
         line["precision"] = prec
     if batched:
@@ -1024,6 +1027,43 @@ def run_coo_orders(M, args, dev, kern, peak):
     return out
 
 
+def run_stream_tma(M, pairs, kern, peak, reps=20):
+    """The bulk-copy (TMA) staging variant (MSREP_STREAM_TMA) of each main
+    kernel of the step, on the step's own problems: main-kernel time beside
+    the direct-load kernel's, and its result against the direct kernel's
+    (bit-equal for CSR and COO, normwise for CSC, whose atomic adds land in
+    another order)."""
+    import torch
+    out = {}
+    for (name, fmt, A, part, x, y, ws, nnz, nb) in pairs:
+        key = f"{name}/{fmt}"
+        M.msrep_spmv(A, part, 1.0, x, 0.0, y, workspace=ws)
+        y_direct = y.clone()
+        for _ in range(3):
+            M.msrep_spmv(A, part, 1.0, x, 0.0, y, flags=M.MSREP_STREAM_TMA, workspace=ws)
+        torch.cuda.synchronize()
+        if fmt == "csc":
+            check = {"normwise_vs_direct": float(torch.linalg.norm(y - y_direct)
+                                                 / torch.linalg.norm(y_direct))}
+        else:
+            check = {"bit_equal_to_direct": bool(torch.equal(y, y_direct))}
+        k_us = main_kernel_us(M, lambda: M.msrep_spmv(A, part, 1.0, x, 0.0, y,
+                                                       flags=M.MSREP_STREAM_TMA, workspace=ws),
+                              reps)
+        d_us = kern[key]["kernel_us"]
+        out[key] = {"kernel_us": k_us, "direct_kernel_us": d_us, "stream_over_direct": k_us / d_us,
+                    "gbs": nb / (k_us * 1e-6) / 1e9, "frac": nb / (k_us * 1e-6) / 1e9 / peak,
+                    **check}
+        del y_direct
+    # a bounded wait of the streaming kernels that gave up is reported here
+    try:
+        M.native.msrep_device_status()
+        out["waits_gave_up"] = False
+    except M.MsrepError:
+        out["waits_gave_up"] = True
+    return out
+
+
 def run_profile_case(args):
     """A short fixed case for ncu captures: partition the R-MAT matrix once,
     then `--reps` calls of msrep_spmv in one format and value type."""
@@ -1137,6 +1177,8 @@ def main():
                     help="skip the row-block imbalance experiment")
     ap.add_argument("--skip-coo-orders", action="store_true",
                     help="skip the column-sorted / unsorted COO leg")
+    ap.add_argument("--skip-stream-tma", action="store_true",
+                    help="skip the bulk-copy (TMA) staging variant's leg")
     ap.add_argument("--batched-count", type=int, default=512,
                     help="matrices in the batched-form measurement (0 = skip)")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
