@@ -146,7 +146,10 @@ static msrep_status run_spmm(const msrep_matrix *A, const msrep_partition *p, in
   a.comp_mode = flags & (MSREP_COMP_ALL | MSREP_COMP_NONE);
   const int32_t *n_tiles = reinterpret_cast<const int32_t *>(plan + L.off_toff) + p->np;
   int nb = 1;
-  MSREP_TRY(blocks_of(csr_spmm_direct<Pol, KP>, 0, 2, &nb));
+  // a tile's walk is a chain of dependent loads, so tiles in flight set the
+  // rate: the 1- and 2-vector layouts fit three blocks an SM in registers
+  // (R-MAT FP32, 2 vectors: 207 -> 174 us); the wider ones fit two
+  MSREP_TRY(blocks_of(csr_spmm_direct<Pol, KP>, 0, KP <= 2 ? 3 : 2, &nb));
   constexpr int G = KvShape<X, KP>::G;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ceil_div(L.tmax, G),
                                                              int64_t(nb) * sm_count()));
